@@ -1,0 +1,312 @@
+#!/usr/bin/env python
+"""Benchmark: Stokes mobility solves of 100 unit spheres (M=1200 collocation, N=600 proxy points).
+
+One step = one whole mobility solve through the C ABI (completion lambda_0, right-hand side u_0
+over all pairs, device GMRES to 1e-7 on the preconditioned square system, recovery and
+extraction of U, Omega), inputs already in HBM.  Metric: Stokeslet pair interactions per second
+over the solve; the line also carries the solve time, the pair kernel's share of peak FP32
+throughput (28 flops per Stokeslet pair, FP32 FMA peak = 2 * 128 lanes * SMs * 2070 MHz), the
+error against the stored FP64 oracle solution, and the FP64 oracle itself timed on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (torchrun) every rank solves its own copy of the workload (replicas: the solve has no
+exchange step between GPUs at this size); the value is the pairs of all ranks over the slowest
+rank's time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "sphere100_mobility"
+METRIC = "Stokeslet pair-interactions/s (mobility solve to 1e-7 GMRES tolerance, 100 spheres, M=1200, N=600)"
+UNIT = "pairs/s"
+FLOPS_PER_PAIR = 28
+GOLDEN = os.path.join(ROOT, "tests", "golden", "sphere100_mobility_oracle.json")
+THROTTLE_BITS = {
+    0x1: "gpu_idle",
+    0x2: "applications_clocks_setting",
+    0x4: "sw_power_cap",
+    0x8: "hw_slowdown",
+    0x10: "sync_boost",
+    0x20: "sw_thermal_slowdown",
+    0x40: "hw_thermal_slowdown",
+    0x80: "hw_power_brake_slowdown",
+    0x100: "display_clock_setting",
+}
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--cpu-sample-bodies", type=int, default=12)
+    ap.add_argument("--small", action="store_true",
+                    help="profiling case: 24 spheres with the same M, N and volume fraction (not a bench line)")
+    return ap.parse_args()
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons while the timed region runs."""
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active"
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons, power = [], [], set(), []
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 4:
+                continue
+            try:
+                s, mx = float(parts[0]), float(parts[1])
+                bits = int(parts[3], 16) if parts[3].startswith("0x") else int(parts[3])
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            sm.append(s)
+            smax.append(mx)
+            for b, name in THROTTLE_BITS.items():
+                if bits & b and name != "gpu_idle":
+                    reasons.add(name)
+        os.unlink(self.f.name)
+        busy = [s for s in sm if s > 0.5 * max(sm)] if sm else []
+        return {
+            "sm_mhz": statistics.median(busy) if busy else None,
+            "sm_max_mhz": max(smax) if smax else None,
+            "reasons": sorted(reasons),
+            "samples": len(sm),
+            "power_w_max": max(power) if power else None,
+        }
+
+
+def _oracle_sample(wl, nbodies: int, repeats: int = 1):
+    """The FP64 oracle's matvec restricted to `nbodies` sampled target bodies (preconditioner on all)."""
+    from oracle import Problem
+
+    pr = Problem(wl)
+    bodies = list(range(pr.P))
+    rng = np.random.default_rng(0)
+    gam = rng.standard_normal(sum(x.shape[0] for x in pr.X) * 3)
+    sample = list(range(0, pr.P, max(1, pr.P // nbodies)))[:nbodies]
+    pairs = sum(pr.X[k].shape[0] * sum(pr.Y[j].shape[0] for j in bodies if j != k) for k in sample)
+    times = []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        g = pr.split(bodies, gam)
+        lam = [pr.pinv_apply(k, gk, project=True) for k, gk in zip(bodies, g)]
+        pr.pair_sum(bodies, lam, include_self=False, target_bodies=sample)
+        times.append(time.perf_counter() - t0)
+    cores = len(os.sched_getaffinity(0))
+    threads = int(os.environ.get("OMP_NUM_THREADS", cores))
+    return pairs, times, cores, threads, sample
+
+
+def reference_arm(args, rank):
+    if rank != 0:
+        return
+    from mfs_inputs import make_workload
+
+    wl = make_workload(WORKLOAD)
+    nb = args.cpu_sample_bodies
+    pairs, times, cores, threads, sample = _oracle_sample(wl, nb, repeats=args.warmup + args.steps)
+    timed = times[args.warmup:]
+    sec = sum(timed)
+    value = pairs * len(timed) / sec
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * sec / len(timed),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded RSA sphere suspension)",
+        "config": {"workload": f"{WORKLOAD}: 100 unit spheres, volume fraction 0.1, M=1200, N=600",
+                   "step": f"FP64 oracle matvec on {len(sample)} sampled target bodies (one-body "
+                           "pseudo-inverse on all 100 bodies, plain-C OpenMP direct sums)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{len(sample)} of 100 target bodies x 99 source bodies per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = _args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    import __graft_entry__
+
+    if rank == 0:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    from mfs_inputs import make_workload
+    from paper_2409_04215_gb300 import MFS
+
+    wl = make_workload(WORKLOAD, count=24) if args.small else make_workload(WORKLOAD)
+    ctx = MFS.from_workload(wl, profile=1)
+    F = torch.tensor(wl.F, device=dev)
+    T = torch.tensor(wl.T, device=dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2, written between steps
+    for _ in range(args.warmup):
+        ctx.solve_mobility(F, T)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(torch.cuda.current_device())
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    infos = []
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        torch.cuda.nvtx.range_push("bench_timed")  # profilers select the timed solves by this range
+        ev[i][0].record()
+        U, W, info = ctx.solve_mobility(F, T)
+        ev[i][1].record()
+        torch.cuda.nvtx.range_pop()
+        infos.append(info)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    if dist:
+        dist.barrier()
+    ck = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    t_max = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if dist:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms_max = float(t_max.item())
+    pairs_step = infos[-1].pairs * wl.nrhs
+    value = pairs_step * args.steps * world / (ms_max / 1e3)
+
+    # pair kernel roofline (device time of the kernel launches alone, CUDA events on the library's stream)
+    pair_ms = sum(i.ms_pairs for i in infos)
+    pair_launches = sum(i.pair_launches for i in infos)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = 2 * 128 * sms * 2070e6 / 1e12
+    achieved = FLOPS_PER_PAIR * pairs_step * args.steps / (pair_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "mfs::pair_sum_kernel<3,1,*,*> (Stokeslet, FP32)",
+                "peak_note": f"FP32 FMA: 2 x 128 lanes x {sms} SMs x 2070 MHz (max SM clock)",
+                "avg_launch_ms": pair_ms / pair_launches,
+                "pair_share_of_step": pair_ms / ms}
+    if ck.get("sm_mhz"):
+        roofline["frac_at_measured_clock"] = achieved / (2 * 128 * sms * ck["sm_mhz"] * 1e6 / 1e12)
+
+    err = None
+    if os.path.exists(GOLDEN) and not args.small:
+        g = json.load(open(GOLDEN))
+        ref = np.concatenate([np.array(g["U"]), np.array(g["Omega"])], axis=1)
+        got = np.concatenate([U.cpu().numpy()[0], W.cpu().numpy()[0]], axis=1)
+        err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+    # end to end through the public API with host buffers (pinned in, copies inside the timed region)
+    Fh = torch.tensor(wl.F).pin_memory()
+    Th = torch.tensor(wl.T).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Uh, Wh, _ = ctx.solve_mobility(Fh, Th, stream=torch.cuda.current_stream(dev).cuda_stream)
+        _ = float(Uh[0, 0, 0])  # the result is on the host
+    e2e_sec = (time.perf_counter() - t0) / args.steps
+    e2e = {"value": pairs_step * world / e2e_sec, "unit": UNIT,
+           "h2d_bytes_per_step": int(Fh.numel() * 8 + Th.numel() * 8),
+           "d2h_bytes_per_step": int(2 * Fh.numel() * 8), "ms_per_step": 1e3 * e2e_sec}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if world == 1:
+        pairs_c, times_c, cores, threads, sample = _oracle_sample(wl, args.cpu_sample_bodies, repeats=1)
+        cpu = {"value": pairs_c / times_c[0], "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"FP64 oracle matvec rows of {len(sample)} of 100 target bodies ({pairs_c:.3g} pairs, "
+                         f"{times_c[0]:.1f} s)"}
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 pair sums, f64 GMRES",
+        "data": "synthetic (seeded RSA sphere suspension, N(0,1) forces and torques)",
+        "config": {"workload": f"{WORKLOAD}: 100 unit spheres, volume fraction 0.1, min gap 0.1, M=1200, N=600, "
+                               "R_p=0.7", "nrhs": wl.nrhs, "gmres_tol": 1e-7,
+                   "l2": "512 MB buffer written between timed steps (flush)",
+                   "parallelism": f"replicas x{world}"},
+        "profile_case": "24 spheres (not a bench line)" if args.small else None,
+        "solve_ms": ms_max / args.steps,
+        "gmres_iters": infos[-1].iters,
+        "err_vs_oracle": err,
+        "wall_s_timed": wall,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(sum(i.launches for i in infos)),
+        "clocks": ck,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,188 @@
+/*
+ * mfs.h -- C ABI of libmfs: the GMRES matvec hot path of the recompleted
+ * method-of-fundamental-solutions (MFS) elastance and mobility solvers of
+ * Broms, Barnett & Tornberg, "A Method of Fundamental Solutions for
+ * Large-Scale 3D Elastance and Mobility Problems", on one GB300 (sm_103a).
+ *
+ * Conventions (all entry points)
+ *  - Every user-facing number is FP64 and every index int32_t.  Arrays are
+ *    row-major and contiguous.  "Host or device" pointers are accepted as either:
+ *    the library asks the CUDA runtime what the pointer is, copies host data
+ *    to the device itself and copies results back before returning.
+ *  - Bodies are numbered 0..P-1; suspension s owns bodies
+ *    [body_offsets[s], body_offsets[s+1]) and never interacts with another
+ *    suspension.  Body k has M_k = colloc[shape_id[k]].n collocation points and
+ *    N_k = proxy[shape_id[k]].n proxy points; sum_M = sum_k M_k, sum_N = sum_k N_k.
+ *  - d = 1 (Laplace) or 3 (Stokes).  Surface vectors (gamma, y, u) are laid out
+ *    [nrhs][sum_M][d]; proxy strength vectors (lambda, alpha) [nrhs][sum_N][d];
+ *    forces, torques and velocities [nrhs][P][3]; charges and potentials [nrhs][P].
+ *  - Kernels: Laplace G = 1/(4 pi r) (Sec. 2.1, Eq. Skk); Stokeslet
+ *    (I + r r^T / r^2) / (8 pi mu r) (Sec. 2.2, Eq. stokeslet).  Torques are taken
+ *    about the body centre.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Every launch
+ *    goes on it; an entry point that returns results to host memory synchronises it.
+ *  - No exception or longjmp crosses the ABI.  On error the status is returned
+ *    and mfs_last_error() describes it; outputs are then unspecified, except for
+ *    MFS_ERR_NOT_CONVERGED, where outputs hold the last iterate and `info` is filled.
+ *  - A context is not thread safe: calls on one context must not overlap.
+ */
+#ifndef MFS_H_
+#define MFS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MFS_ABI_VERSION 1
+
+typedef struct mfs_ctx mfs_ctx; /* opaque; owns all internal device memory */
+
+typedef enum {
+    MFS_OK = 0,
+    MFS_ERR_INVALID_ARG = 1,     /* bad size, NULL pointer, non-finite input, wrong kind */
+    MFS_ERR_CUDA = 2,            /* a CUDA runtime / library call failed */
+    MFS_ERR_OOM = 3,             /* device allocation failed */
+    MFS_ERR_NOT_CONVERGED = 4,   /* GMRES reached max_iter above the tolerance */
+    MFS_ERR_BREAKDOWN = 5,       /* GMRES produced a non-finite residual */
+    MFS_ERR_ILL_CONDITIONED = 6, /* a one-body SVD returned a non-finite or zero sigma_1 */
+    MFS_ERR_DEVICE_TIMEOUT = 7   /* a device-side bounded wait gave up (kernel returned early) */
+} mfs_status;
+
+typedef enum { MFS_LAPLACE = 0, MFS_STOKES = 1 } mfs_kind;
+
+/* A body-frame point set of one shape: n points, pts[n][3] (host memory), centred on the body centre. */
+typedef struct {
+    int32_t n;
+    const double *pts;
+} mfs_pointset;
+
+/* The bodies (host memory).  quats [P][4] = (w, x, y, z) unit quaternions or NULL (identity);
+ * shape_id [P] or NULL (all shape 0); body_offsets [S+1] or NULL (one suspension of P bodies). */
+typedef struct {
+    int32_t num_bodies;
+    const double *centers; /* [P][3] */
+    const double *quats;
+    const int32_t *shape_id;
+    int32_t num_suspensions;
+    const int32_t *body_offsets;
+} mfs_bodies;
+
+typedef struct {
+    double mu;         /* viscosity (Stokes); default 1 */
+    double gmres_tol;  /* relative tolerance on the Arnoldi residual estimate; default 1e-7 */
+    int32_t max_iter;  /* GMRES iteration cap per solve; default 200 */
+    int32_t restart;   /* Krylov basis size before a restart; default 200 (no restart) */
+    double eps_trunc;  /* singular values <= sigma_1 * eps_trunc are dropped (Eq. pseudo); default 0 */
+    int32_t precision; /* 0: FP32 pair sums with compensated accumulation (default);
+                          1: FP64 pair sums and FP64 preconditioner (reference GPU path) */
+    int32_t autotune;  /* 1: time pair-kernel variants on this geometry at setup (default 1) */
+    int32_t max_rhs;   /* largest nrhs any later call will use (1..4); default 4 */
+    int32_t profile;   /* 1: bracket every pair-kernel launch with CUDA events (no host sync) and report
+                          their summed device time in mfs_solve_info.ms_pairs; default 0 */
+} mfs_options;
+
+typedef struct {
+    int32_t iters;        /* GMRES iterations (max over right-hand sides and suspensions) */
+    int32_t converged;    /* 1 when every lane met gmres_tol */
+    int32_t matvecs;      /* applications of the preconditioned operator */
+    int32_t lanes;        /* independent Krylov solves = nrhs * num_suspensions */
+    double rel_residual;  /* max over lanes of the final Arnoldi residual estimate / ||b|| */
+    double ms_setup;      /* wall time of mfs_setup (ms) */
+    double ms_solve;      /* device time of the solve (ms) */
+    double ms_pairs;      /* device time spent in the pair-sum kernel (ms) */
+    double pairs;         /* point pairs evaluated by the pair-sum kernel (per right-hand side) */
+    int32_t launches;     /* device kernels and memsets this call enqueued */
+    int32_t pair_launches;/* pair-sum kernel launches of this call */
+} mfs_solve_info;
+
+/* Fill *opt with the defaults listed above. */
+void mfs_default_options(mfs_options *opt);
+
+/* Library ABI version (MFS_ABI_VERSION). */
+int32_t mfs_abi_version(void);
+
+/*
+ * mfs_setup -- discretise the bodies and build every one-body factor (Sec. 2.3, Sec. 3.3).
+ * Per shape, on the device in FP64: S^(00), K_N, K_M (Eq. Kdef), L and L_r (Sec. 3.1 / Eq. Lrsto),
+ * S_L = S^(00)(I - L) + L_r and its thin SVD (Eq. pseudo); congruent rotated bodies share it
+ * (Remark congruent, Eq. Krot).  Global points are c_k + R(q_k) X0.
+ * proxy[s], colloc[s] (s < num_shapes) describe shape s; colloc[s].n must exceed proxy[s].n.
+ * On success *out owns the new context (free with mfs_destroy).  All inputs are copied.
+ */
+mfs_status mfs_setup(mfs_ctx **out, mfs_kind kind, const mfs_bodies *bodies, int32_t num_shapes,
+                     const mfs_pointset *proxy, const mfs_pointset *colloc, const mfs_options *opt,
+                     void *stream);
+
+/* Move the bodies: new centres [P][3] (host or device).  One-body factors are reused
+ * (they depend on shape and orientation only, Remark congruent). */
+mfs_status mfs_update_centers(mfs_ctx *ctx, const double *centers, void *stream);
+
+/*
+ * mfs_matvec -- y = A gamma for the preconditioned square system Eq. 2esysprec:
+ *   y^(k) = gamma^(k) + sum_{k' != k, same suspension} S^(kk') (I - L^(k')) S_L^(k')+ gamma^(k'),
+ * with S_L^+ applied in two steps (Eq. pseudo) and self pairs never evaluated (Algorithm 1 MATVEC
+ * steps 1-3 with step 3 folded into step 2).  gamma, y: [nrhs][sum_M][d], host or device; 1 <= nrhs <= max_rhs.
+ */
+mfs_status mfs_matvec(mfs_ctx *ctx, const double *gamma, double *y, int32_t nrhs, void *stream);
+
+/*
+ * mfs_precond_apply -- lambda^(k) = S_L^(k)+ gamma^(k) (Eq. pseudo with Remark congruent), followed
+ * by the projection (I - L^(k)) when project != 0 (Sec. 3.3, item 2).  gamma [nrhs][sum_M][d],
+ * lambda [nrhs][sum_N][d], host or device.
+ */
+mfs_status mfs_precond_apply(mfs_ctx *ctx, const double *gamma, double *lambda, int32_t project, int32_t nrhs,
+                             void *stream);
+
+/*
+ * mfs_pair_sum -- the bare MFS evaluation (Algorithm 1 MATVEC step 2):
+ *   u^(k) = sum_{k' in the suspension of k, k' != k unless include_self} S^(kk') s^(k'),
+ * strengths s [nrhs][sum_N][d] at the proxy points, u [nrhs][sum_M][d] at the collocation points,
+ * host or device.  With include_self = 1 this is the right-hand side u_0 of Eq. erhsK / Eq. stou0.
+ */
+mfs_status mfs_pair_sum(mfs_ctx *ctx, const double *strengths, double *u, int32_t nrhs, int32_t include_self,
+                        void *stream);
+
+/*
+ * mfs_solve_elastance -- potentials V [nrhs][P] of conductors with net charges Q [nrhs][P]
+ * (Prop. 3.1): alpha_0 = q/N 1 (Eq. al0), u_0 by a pair sum over all pairs (Eq. erhsK), GMRES on
+ * Eq. 2esysprec from a zero guess, alpha = S_L^+ gamma, V = -mean(alpha) (Eq. vkal).  Laplace only.
+ * info may be NULL.
+ */
+mfs_status mfs_solve_elastance(mfs_ctx *ctx, const double *Q, double *V, int32_t nrhs, mfs_solve_info *info,
+                               void *stream);
+
+/*
+ * mfs_solve_mobility -- velocities U and angular velocities Omega [nrhs][P][3] of rigid bodies
+ * under forces F and torques T [nrhs][P][3] (Prop. 3.2): lambda_0 = K_N (K_N^T K_N)^-1 [f; t]
+ * (Eq. lambda01, lambda02), u_0 over all pairs (Eq. stou0), GMRES on Eq. 2esysprec,
+ * lambda = S_L^+ gamma, [U; Omega] = -K_N^T lambda (Eq. getU).  Stokes only.  info may be NULL.
+ * The context keeps the solution for mfs_mobility_vjp.
+ */
+mfs_status mfs_solve_mobility(mfs_ctx *ctx, const double *F, const double *T, double *U, double *Omega,
+                              int32_t nrhs, mfs_solve_info *info, void *stream);
+
+/*
+ * mfs_mobility_vjp -- reverse-mode derivative of the last mfs_solve_mobility (an adjoint the paper
+ * does not give; derived from Eq. 2esysprec, Eq. stou0 and Eq. getU).  Given dL/dU and dL/dOmega
+ * [nrhs][P][3], writes dL/dcenters [P][3] (summed over right-hand sides) and, when non-NULL,
+ * dL/dF and dL/dT [nrhs][P][3].  Host or device pointers.
+ */
+mfs_status mfs_mobility_vjp(mfs_ctx *ctx, const double *dU, const double *dOmega, int32_t nrhs, double *dcenters,
+                            double *dF, double *dT, void *stream);
+
+/* Text of the last error on this context (never NULL; "" when none).  Valid until the next call. */
+const char *mfs_last_error(const mfs_ctx *ctx);
+
+/* Text of the last mfs_setup failure that could not return a context. */
+const char *mfs_setup_error(void);
+
+/* Release the context and all its device memory.  NULL is ignored. */
+void mfs_destroy(mfs_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MFS_H_ */

@@ -1,0 +1,118 @@
+// Shared definitions of libmfs (internal; not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#define MFS_PI 3.14159265358979323846
+
+// Device error flags (bit mask written with atomicOr by kernels that give up).
+#define MFS_DEVERR_TIMEOUT 1
+#define MFS_DEVERR_BADARG 2
+
+// ---------------------------------------------------------------------------
+// Pair-sum work decomposition.
+//
+// Targets (collocation points) are numbered globally, bodies contiguous, the
+// bodies of one suspension contiguous.  A tile is a range of at most
+// `tile_targets` consecutive targets of one suspension spanning at most
+// MFS_MAX_TILE_BODIES bodies.  Its work is the sequence of source "units"
+// (blocks of MFS_BS consecutive source records of one body) of every body of
+// its suspension, except the tile's own body when the tile lies inside one
+// body and self pairs are excluded.  The units of all tiles are concatenated
+// into one global sequence of `total_units`, cut into G equal shares, one per
+// persistent CTA (a stream-K split), so that every CTA does the same work.
+// ---------------------------------------------------------------------------
+#define MFS_BS 32
+#define MFS_MAX_TILE_BODIES 32
+
+struct PairTile {
+    int t0, t1;          // targets [t0, t1)
+    int kb0, nb;         // target bodies kb0 .. kb0+nb-1
+    int skip;            // source body left out entirely, or -1
+    int B0, B1;          // source bodies of the suspension [B0, B1)
+    long long u0, u1;    // global unit range of this tile
+    int gA, gB;          // first and last CTA whose share meets this tile
+};
+
+struct PairGeom {
+    const float4 *tgt;         // [ntargets] body-local rotated target (x,y,z), w = body id (int bits)
+    const float *src;          // [sum_Npad][REC] packed source records
+    const int *src_off;        // [P+1] record offset of each body (padded to a multiple of 4)
+    const long long *blk_off;  // [P+1] global block offset of each body (blocks of MFS_BS records)
+    const double *centres;     // [P][3]
+    int ntargets;
+};
+
+struct PairWork {
+    const PairTile *tiles;
+    int ntiles;
+    long long total_units;
+    int G;                     // persistent CTAs
+    double *partial;           // [G][2][tile_targets][C]
+    double *direct;            // [ntargets][C]
+    int tile_targets;
+    int include_self;          // 1: self pairs included (right-hand side u_0)
+};
+
+// ---------------------------------------------------------------------------
+// Inline PTX: mbarrier + 1-D bulk copy (TMA engine), with bounded waits.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+        "r"(bytes)
+        : "memory");
+}
+
+// Returns true when phase `parity` of the barrier has completed.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after `limit` polls (each try_wait itself suspends for a
+// hardware-defined interval), records MFS_DEVERR_TIMEOUT and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *err, long long limit) {
+    for (long long it = 0; it < limit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    if (err) atomicOr(err, MFS_DEVERR_TIMEOUT);
+    return false;
+}
+
+// Bulk copy global -> shared, completion signalled on `bar` (bytes % 16 == 0, both addresses 16-B aligned).
+__device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src_gmem, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Error-free transformation a + b = s + e (Knuth's TwoSum, 6 flops).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}

@@ -1,0 +1,95 @@
+// Internal host-side entry points of the libmfs kernels (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace mfs {
+
+// ---- pair sums (pair_kernel.cu) ----
+struct PairVariant {
+    int D, nrhs, T, NT, tile_targets;
+};
+const PairVariant *pair_variants(int *count);
+int pair_occupancy(int variant);  // resident CTAs per SM
+int pair_record_floats(int D, int nrhs);
+cudaError_t pair_launch(int variant, const PairGeom &geo, const PairWork &work, int *err, cudaStream_t st);
+cudaError_t pair_epilogue(int D, int nrhs, const PairWork &work, const double *base, double beta, double scale,
+                          double *out, int ntargets, cudaStream_t st);
+cudaError_t pack_sources(int D, int nrhs, const float4 *src_pos, const int *src_pt_of_rec, const double *strength,
+                         int nsrc, int nrec, float *records, cudaStream_t st);
+
+// FP64 reference pair sum (precision = 1): one thread per target, direct loops; raw sums (no 1/(4pi) factor).
+cudaError_t pair_sum_fp64(int D, int nrhs, const double *tgt_local, const int *tgt_body, int ntargets,
+                          const double *src_local4, int nsrc, const int *susp_src_begin, const int *susp_src_end,
+                          const int *body_src_off, const double *centres, const double *strength, int include_self,
+                          double *out_raw, cudaStream_t st);
+
+// ---- preconditioner and setup (precond.cu) ----
+struct ShapeDev {
+    int M, N, dM, dN, r;  // r = dN (rank kept; truncated sigmas give zero columns)
+    float *U;             // [dM][r]  left singular vectors (GEMM 1: t = U^T g)
+    float *Wp;            // [r][dN]  ((I - L0) V Sigma^+)^T (projected apply, matvec)
+    float *Wr;            // [r][dN]  (V Sigma^+)^T (recovery apply)
+    double *U64, *Wp64, *Wr64;  // FP64 copies (precision = 1)
+    double sigma1, sigma_min;   // largest / smallest kept singular value
+};
+
+// Build S_L = S0 (I - L) + L_r column-major (dM x dN) in FP64 on the device (Sec. 3.3).
+cudaError_t build_SL(int kind, int M, int N, const double *X0, const double *Y0, double mu, const double *G0inv,
+                     double *SL, cudaStream_t st);
+// From the SVD (U col-major dM x r, sigma, VT col-major r x dN) write the FP32 / FP64 apply factors.
+cudaError_t build_apply_factors(int kind, int M, int N, const double *Ucm, const double *sigma, const double *VTcm,
+                                const double *Y0, const double *G0inv, double eps_trunc, ShapeDev &sd,
+                                cudaStream_t st);
+
+// Gather: A[col][i] = (R_k^T gamma_k)[i] as FP32 for the columns (body, rhs) of one shape.
+cudaError_t gather_rotate(int D, const double *gamma, int sum_MD, const int *col_body, const int *col_rhs,
+                          const int *body_tgt_off, const double *rot, int ncols, int dM, float *A, double *A64,
+                          cudaStream_t st);
+// C[m][n] = sum_k A[m][k] B[k][n]  (row-major; FP32 SIMT tiles, or FP64 when A64/B64 given).
+cudaError_t gemm_rm(int m, int n, int k, const float *A, const float *B, float *C, cudaStream_t st);
+cudaError_t gemm_rm64(int m, int n, int k, const double *A, const double *B, double *C, cudaStream_t st);
+// Scatter: lambda (FP64 [nrhs][sum_N][D]) at the columns' bodies = R_k * Lcol (rotate back).
+cudaError_t scatter_rotate(int D, const float *L, const double *L64, const int *col_body, const int *col_rhs,
+                           const int *body_src_off, const float *rot, const double *rot64, int ncols, int dN,
+                           int sum_N, double *lambda, cudaStream_t st);
+
+// Completion strengths (Eq. lambda01-02 / Eq. al0) and extraction (Eq. getU / Eq. vkal).
+cudaError_t completion_stokes(const double *F, const double *T, int nrhs, int P, const double *rot64,
+                              const double *G0inv_shapes, const int *shape_id, const double *src_local64,
+                              const int *body_src_off, int sum_N, double *lam0, cudaStream_t st);
+cudaError_t completion_laplace(const double *Q, int nrhs, int P, const int *body_src_off, int sum_N, double *alpha0,
+                               cudaStream_t st);
+cudaError_t extract_stokes(const double *lam, int nrhs, int P, const double *src_local64, const int *body_src_off,
+                           int sum_N, double *U, double *Om, cudaStream_t st);
+cudaError_t extract_laplace(const double *alpha, int nrhs, int P, const int *body_src_off, int sum_N, double *V,
+                            cudaStream_t st);
+
+// ---- GMRES (gmres.cu): L independent lanes, lane l owns vector entries [seg_off[l], seg_off[l+1]) ----
+struct GmresDev {
+    int L, m;                  // lanes, Krylov basis capacity (m <= 1023)
+    long long n;               // vector length (all lanes)
+    const long long *seg_off;  // [L+1] (device)
+    double *V;                 // [(m+1)][n] basis
+    double *H;                 // [L][m+1][m] Hessenberg, rotated to upper triangular
+    double *cs, *sn, *g;       // [L][m], [L][m], [L][m+1]
+    double *beta;              // [L] ||b||
+    double *hbuf, *htmp;       // [L][m+1] current column, current CGS pass
+    double *hn;                // [L] norm of the new Krylov vector
+    double *part;              // [L][part_blocks][m+1] block partials
+    int *active;               // [L] 1 while the lane iterates
+    int *iters;                // [L] iterations done
+    int *status;               // [L] 0 ok, 2 breakdown (non-finite)
+    double *resid;             // [L] |g_k| / ||b||
+    int *done;                 // [1] 1 when no lane is active
+    double tol;
+    int part_blocks;           // blocks per lane in the reductions
+};
+cudaError_t gmres_init(GmresDev &gd, const double *b, cudaStream_t st);
+// Orthogonalise w = A v_j against v_0..v_j (CGS2), append v_{j+1}, Givens-update every active lane.
+cudaError_t gmres_arnoldi(GmresDev &gd, double *w, int j, cudaStream_t st);
+// x = V y with H y = g per lane (y_small: [L][m+1] scratch).
+cudaError_t gmres_solution(GmresDev &gd, double *x, double *y_small, cudaStream_t st);
+
+}  // namespace mfs

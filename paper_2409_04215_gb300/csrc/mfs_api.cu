@@ -1,0 +1,1209 @@
+// libmfs host runtime and C ABI (see include/mfs.h).
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/mfs.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace mfs;
+
+namespace {
+
+thread_local std::string g_setup_error;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct PairPlan {
+    int variant = -1;
+    int include_self = 0;
+    int tile_targets = 0;
+    int G = 0;
+    int ntiles = 0;
+    long long total_units = 0;
+    PairTile *tiles = nullptr;
+    double *partial = nullptr;
+    double *direct = nullptr;
+    size_t partial_bytes = 0, direct_bytes = 0;
+};
+
+struct ShapeHost {
+    int M = 0, N = 0;
+    std::vector<double> X0, Y0;  // body frame
+    double G0inv[36];
+    std::vector<int> bodies;     // bodies of this shape
+    int *col_body = nullptr, *col_rhs = nullptr;  // device, [max_rhs * nbodies]
+    float *A = nullptr, *Tm = nullptr, *Lm = nullptr;  // GEMM buffers
+    double *A64 = nullptr, *T64 = nullptr, *L64 = nullptr;
+    ShapeDev dev{};
+};
+
+}  // namespace
+
+struct mfs_ctx {
+    int kind = 0, D = 1;
+    mfs_options opt{};
+    int P = 0, S = 0, nshapes = 0;
+    std::vector<double> centres, quats;
+    std::vector<int> shape_id, body_off;
+    std::vector<int> tgt_off, src_off, rec_off;  // [P+1] point / padded-record offsets
+    std::vector<long long> blk_off;
+    std::vector<int> tgt_body;                     // [sum_M]
+    int sumM = 0, sumN = 0, nrec = 0;
+    std::vector<double> rot;                       // [P][9]
+    std::vector<ShapeHost> shapes;
+
+    // device geometry
+    double *centres_d = nullptr, *rot64_d = nullptr, *G0inv_d = nullptr;
+    float *rot_d = nullptr;
+    int *shape_id_d = nullptr;
+    float4 *tgt_pos_d = nullptr, *src_pos_d = nullptr;
+    double *tgt_local64_d = nullptr, *src_local64_d = nullptr, *src_local4_d = nullptr;
+    int *tgt_body_d = nullptr, *rec_pt_d = nullptr, *rec_off_d = nullptr, *tgt_off_d = nullptr,
+        *src_off_d = nullptr, *susp_src_begin_d = nullptr, *susp_src_end_d = nullptr;
+    long long *blk_off_d = nullptr;
+    int *err_d = nullptr;
+
+    // work buffers
+    float *rec_d = nullptr;      // packed source records (max_rhs)
+    double *lam_d = nullptr;     // [max_rhs][sumN][D]
+    double *raw_d = nullptr;     // FP64 reference pair sums [max_rhs][sumM][D]
+    std::map<std::pair<int, int>, PairPlan> plans;  // (variant, include_self)
+    int best_variant[2][5] = {{-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}};  // [D==3][nrhs]
+
+    // GMRES
+    GmresDev gd{};
+    size_t gd_n = 0;
+    int gd_L = 0, gd_m = 0;
+    long long *seg_off_d = nullptr;
+    double *w_d = nullptr, *b_d = nullptr, *x_d = nullptr, *ysmall_d = nullptr;
+    int *done_h = nullptr;
+
+    // solution kept for the adjoint
+    double *last_gamma = nullptr;
+    int last_nrhs = 0;
+
+    int sm_count = 0;
+    std::string last_error;
+    std::vector<void *> allocs;
+    double ms_setup = 0.0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, evp0 = nullptr, evp1 = nullptr;
+    double pair_ms_acc = 0.0;
+    int launches = 0;        // kernels + memsets enqueued by the current call
+    int pair_launches = 0;   // pair-kernel launches of the current call
+    std::vector<cudaEvent_t> pev;  // profile: event pairs around pair-kernel launches
+
+    template <typename T>
+    cudaError_t alloc(T **p, size_t count) {
+        *p = nullptr;
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc((void **)p, sizeof(T) * count);
+        if (e == cudaSuccess) allocs.push_back((void *)*p);
+        return e;
+    }
+    void release(void *p) {
+        if (!p) return;
+        auto it = std::find(allocs.begin(), allocs.end(), p);
+        if (it != allocs.end()) allocs.erase(it);
+        cudaFree(p);
+    }
+    ~mfs_ctx() {
+        for (void *p : allocs) cudaFree(p);
+        if (done_h) cudaFreeHost(done_h);
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+        if (evp0) cudaEventDestroy(evp0);
+        if (evp1) cudaEventDestroy(evp1);
+        for (cudaEvent_t e : pev) cudaEventDestroy(e);
+    }
+};
+
+namespace {
+
+#define CK(call)                                                                             \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            ctx->last_error = std::string(#call) + ": " + cudaGetErrorString(e_);            \
+            return e_ == cudaErrorMemoryAllocation ? MFS_ERR_OOM : MFS_ERR_CUDA;              \
+        }                                                                                    \
+    } while (0)
+
+#define CKS(call)                                  \
+    do {                                           \
+        mfs_status s_ = (call);                    \
+        if (s_ != MFS_OK) return s_;               \
+    } while (0)
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// A device view of a user pointer: either the pointer itself or a staged copy.
+struct Staged {
+    mfs_ctx *ctx = nullptr;
+    double *d = nullptr;
+    const void *user = nullptr;
+    size_t count = 0;
+    bool owned = false;
+    ~Staged() {
+        if (owned && d) cudaFree(d);
+    }
+};
+
+mfs_status stage_in(mfs_ctx *ctx, Staged &s, const double *user, size_t count, cudaStream_t st) {
+    s.ctx = ctx;
+    s.user = user;
+    s.count = count;
+    if (is_device_ptr(user)) {
+        s.d = const_cast<double *>(user);
+        return MFS_OK;
+    }
+    CK(cudaMalloc(&s.d, sizeof(double) * std::max<size_t>(count, 1)));
+    s.owned = true;
+    CK(cudaMemcpyAsync(s.d, user, sizeof(double) * count, cudaMemcpyHostToDevice, st));
+    return MFS_OK;
+}
+
+mfs_status stage_out_alloc(mfs_ctx *ctx, Staged &s, double *user, size_t count) {
+    s.ctx = ctx;
+    s.user = user;
+    s.count = count;
+    if (is_device_ptr(user)) {
+        s.d = user;
+        return MFS_OK;
+    }
+    CK(cudaMalloc(&s.d, sizeof(double) * std::max<size_t>(count, 1)));
+    s.owned = true;
+    return MFS_OK;
+}
+
+mfs_status stage_out_finish(mfs_ctx *ctx, Staged &s, cudaStream_t st) {
+    if (s.owned) {
+        CK(cudaMemcpyAsync(const_cast<void *>(s.user), s.d, sizeof(double) * s.count, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    return MFS_OK;
+}
+
+mfs_status check_device_error(mfs_ctx *ctx, cudaStream_t st) {
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, ctx->err_d, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h) {
+        ctx->last_error = (h & MFS_DEVERR_TIMEOUT) ? "a device-side bounded wait gave up" : "device argument error";
+        cudaMemsetAsync(ctx->err_d, 0, sizeof(int), st);
+        return MFS_ERR_DEVICE_TIMEOUT;
+    }
+    return MFS_OK;
+}
+
+void quat_to_rot(const double *q, double *R) {
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z); R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
+}
+
+// 6x6 inverse by Gauss-Jordan with partial pivoting; returns false when singular.
+bool invert6(const double *A, double *Ainv) {
+    double a[6][12];
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 12; ++j) a[i][j] = j < 6 ? A[i * 6 + j] : (j - 6 == i ? 1.0 : 0.0);
+    for (int c = 0; c < 6; ++c) {
+        int p = c;
+        for (int r = c + 1; r < 6; ++r)
+            if (std::fabs(a[r][c]) > std::fabs(a[p][c])) p = r;
+        if (a[p][c] == 0.0) return false;
+        for (int j = 0; j < 12; ++j) std::swap(a[c][j], a[p][j]);
+        const double inv = 1.0 / a[c][c];
+        for (int j = 0; j < 12; ++j) a[c][j] *= inv;
+        for (int r = 0; r < 6; ++r)
+            if (r != c) {
+                const double f = a[r][c];
+                for (int j = 0; j < 12; ++j) a[r][j] -= f * a[c][j];
+            }
+    }
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) Ainv[i * 6 + j] = a[i][j + 6];
+    return true;
+}
+
+// G0 = K_N0^T K_N0 for body-frame proxy points (Eq. lambda02 with Eq. Kdef).
+void gram6(const std::vector<double> &Y0, double *G) {
+    std::memset(G, 0, sizeof(double) * 36);
+    const int n = (int)Y0.size() / 3;
+    for (int q = 0; q < n; ++q) {
+        const double *d = &Y0[3 * q];
+        const double cm[3][3] = {{0.0, d[2], -d[1]}, {-d[2], 0.0, d[0]}, {d[1], -d[0], 0.0}};
+        for (int b = 0; b < 3; ++b) {
+            double row[6];
+            for (int m = 0; m < 3; ++m) row[m] = (b == m) ? 1.0 : 0.0;
+            for (int m = 0; m < 3; ++m) row[3 + m] = cm[b][m];
+            for (int i = 0; i < 6; ++i)
+                for (int j = 0; j < 6; ++j) G[i * 6 + j] += row[i] * row[j];
+        }
+    }
+}
+
+int default_variant(int D, int nrhs) {
+    int count = 0;
+    const PairVariant *v = pair_variants(&count);
+    // preferred (T, NT) per kind and nrhs
+    int wantT = (D == 3) ? (nrhs == 1 ? 4 : (nrhs == 4 ? 2 : 2)) : (nrhs == 1 ? 4 : 4);
+    int wantNT = 128;
+    for (int i = 0; i < count; ++i)
+        if (v[i].D == D && v[i].nrhs == nrhs && v[i].T == wantT && v[i].NT == wantNT) return i;
+    for (int i = 0; i < count; ++i)
+        if (v[i].D == D && v[i].nrhs == nrhs) return i;
+    return -1;
+}
+
+mfs_status build_plan(mfs_ctx *ctx, int variant, int include_self, PairPlan &plan) {
+    int count = 0;
+    const PairVariant *vv = pair_variants(&count);
+    const PairVariant &v = vv[variant];
+    const int TT = v.tile_targets;
+    const int C = v.D * v.nrhs;
+    std::vector<PairTile> tiles;
+    long long units = 0;
+    for (int s = 0; s < ctx->S; ++s) {
+        const int B0 = ctx->body_off[s], B1 = ctx->body_off[s + 1];
+        const int t_end = ctx->tgt_off[B1];
+        int t = ctx->tgt_off[B0];
+        while (t < t_end) {
+            int t1 = std::min(t + TT, t_end);
+            const int kb0 = ctx->tgt_body[t];
+            int kb1 = ctx->tgt_body[t1 - 1];
+            if (kb1 - kb0 + 1 > MFS_MAX_TILE_BODIES) {
+                kb1 = kb0 + MFS_MAX_TILE_BODIES - 1;
+                t1 = ctx->tgt_off[kb1 + 1];
+            }
+            PairTile tl;
+            tl.t0 = t;
+            tl.t1 = t1;
+            tl.kb0 = kb0;
+            tl.nb = kb1 - kb0 + 1;
+            tl.skip = (!include_self && tl.nb == 1) ? kb0 : -1;
+            tl.B0 = B0;
+            tl.B1 = B1;
+            long long u = 0;
+            for (int b = B0; b < B1; ++b)
+                if (b != tl.skip) u += ctx->blk_off[b + 1] - ctx->blk_off[b];
+            tl.u0 = units;
+            tl.u1 = units + u;
+            units += u;
+            tiles.push_back(tl);
+            t = t1;
+        }
+    }
+    const int occ = pair_occupancy(variant);
+    if (occ <= 0) {
+        ctx->last_error = "pair kernel variant cannot be resident on this GPU";
+        return MFS_ERR_CUDA;
+    }
+    long long G = (long long)occ * ctx->sm_count;
+    if (G > units) G = std::max<long long>(units, 1);
+    const long long W = units;
+    for (auto &tl : tiles) {
+        if (tl.u1 == tl.u0) {
+            tl.gA = tl.gB = -1;
+            continue;
+        }
+        auto owner = [&](long long u) { return (int)(((u + 1) * G - 1) / W); };
+        tl.gA = owner(tl.u0);
+        tl.gB = owner(tl.u1 - 1);
+    }
+    plan.variant = variant;
+    plan.include_self = include_self;
+    plan.tile_targets = TT;
+    plan.G = (int)G;
+    plan.ntiles = (int)tiles.size();
+    plan.total_units = units;
+    CK(ctx->alloc(&plan.tiles, tiles.size()));
+    CK(cudaMemcpy(plan.tiles, tiles.data(), sizeof(PairTile) * tiles.size(), cudaMemcpyHostToDevice));
+    plan.partial_bytes = sizeof(double) * (size_t)G * 2 * TT * C;
+    plan.direct_bytes = sizeof(double) * (size_t)ctx->sumM * C;
+    CK(ctx->alloc(&plan.partial, (size_t)G * 2 * TT * C));
+    CK(ctx->alloc(&plan.direct, (size_t)ctx->sumM * C));
+    return MFS_OK;
+}
+
+mfs_status get_plan(mfs_ctx *ctx, int variant, int include_self, PairPlan **out) {
+    auto key = std::make_pair(variant, include_self);
+    auto it = ctx->plans.find(key);
+    if (it == ctx->plans.end()) {
+        PairPlan p;
+        CKS(build_plan(ctx, variant, include_self, p));
+        it = ctx->plans.emplace(key, p).first;
+    }
+    *out = &it->second;
+    return MFS_OK;
+}
+
+PairWork work_of(const PairPlan &p) {
+    PairWork w;
+    w.tiles = p.tiles;
+    w.ntiles = p.ntiles;
+    w.total_units = p.total_units;
+    w.G = p.G;
+    w.partial = p.partial;
+    w.direct = p.direct;
+    w.tile_targets = p.tile_targets;
+    w.include_self = p.include_self;
+    return w;
+}
+
+PairGeom geom_of(mfs_ctx *ctx) {
+    PairGeom g;
+    g.tgt = ctx->tgt_pos_d;
+    g.src = ctx->rec_d;
+    g.src_off = ctx->rec_off_d;
+    g.blk_off = ctx->blk_off_d;
+    g.centres = ctx->centres_d;
+    g.ntargets = ctx->sumM;
+    return g;
+}
+
+double kernel_scale(mfs_ctx *ctx) {
+    return ctx->kind == MFS_STOKES ? 1.0 / (8.0 * MFS_PI * ctx->opt.mu) : 1.0 / (4.0 * MFS_PI);
+}
+
+// out = beta * base + sign * (pair sum of strengths)  (strengths FP64 [nrhs][sumN][D] on device)
+__global__ void combine_raw_kernel(const double *raw, const double *base, double beta, double scale, double *out,
+                                   size_t n) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (base ? beta * base[i] : 0.0) + scale * raw[i];
+}
+
+mfs_status pair_apply(mfs_ctx *ctx, const double *strength, double *out, const double *base, double beta,
+                      double sign, int nrhs, int include_self, cudaStream_t st) {
+    const double scale = sign * kernel_scale(ctx);
+    if (ctx->opt.precision == 1) {
+        CK(pair_sum_fp64(ctx->D, nrhs, ctx->tgt_local64_d, ctx->tgt_body_d, ctx->sumM, ctx->src_local4_d, ctx->sumN,
+                         ctx->susp_src_begin_d, ctx->susp_src_end_d, ctx->src_off_d, ctx->centres_d, strength,
+                         include_self, ctx->raw_d, st));
+        const size_t n = (size_t)nrhs * ctx->sumM * ctx->D;
+        combine_raw_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ctx->raw_d, base, beta, scale, out, n);
+        CK(cudaGetLastError());
+        ctx->launches += 2;
+        ctx->pair_launches += 1;
+        return MFS_OK;
+    }
+    const int variant = ctx->best_variant[ctx->D == 3][nrhs] >= 0 ? ctx->best_variant[ctx->D == 3][nrhs]
+                                                                  : default_variant(ctx->D, nrhs);
+    if (variant < 0) {
+        ctx->last_error = "no pair-kernel variant for this nrhs";
+        return MFS_ERR_INVALID_ARG;
+    }
+    PairPlan *plan = nullptr;
+    CKS(get_plan(ctx, variant, include_self, &plan));
+    CK(pack_sources(ctx->D, nrhs, ctx->src_pos_d, ctx->rec_pt_d, strength, ctx->sumN, ctx->nrec, ctx->rec_d, st));
+    const PairWork w = work_of(*plan);
+    ctx->launches += 2;
+    if (w.total_units > 0) {
+        const size_t slot = 2 * (size_t)ctx->pair_launches;
+        if (ctx->opt.profile) {
+            while (ctx->pev.size() < slot + 2) {
+                cudaEvent_t e;
+                CK(cudaEventCreate(&e));
+                ctx->pev.push_back(e);
+            }
+            CK(cudaEventRecord(ctx->pev[slot], st));
+        }
+        CK(pair_launch(variant, geom_of(ctx), w, ctx->err_d, st));
+        if (ctx->opt.profile) CK(cudaEventRecord(ctx->pev[slot + 1], st));
+        ctx->launches += 1;
+        ctx->pair_launches += 1;
+    }
+    CK(pair_epilogue(ctx->D, nrhs, w, base, beta, scale, out, ctx->sumM, st));
+    return MFS_OK;
+}
+
+// pairs evaluated per right-hand side by one pair sum
+double pair_count(mfs_ctx *ctx, int include_self) {
+    double total = 0.0;
+    for (int s = 0; s < ctx->S; ++s) {
+        double sm = 0, sn = 0, self = 0;
+        for (int k = ctx->body_off[s]; k < ctx->body_off[s + 1]; ++k) {
+            const double m = ctx->tgt_off[k + 1] - ctx->tgt_off[k], n = ctx->src_off[k + 1] - ctx->src_off[k];
+            sm += m;
+            sn += n;
+            self += m * n;
+        }
+        total += sm * sn - (include_self ? 0.0 : self);
+    }
+    return total;
+}
+
+// lambda = (I - L) S_L^+ gamma (project) or S_L^+ gamma  (Eq. pseudo, Remark congruent)
+mfs_status precond_apply_dev(mfs_ctx *ctx, const double *gamma, double *lambda, int project, int nrhs,
+                             cudaStream_t st) {
+    const int D = ctx->D;
+    for (auto &sh : ctx->shapes) {
+        const int nb = (int)sh.bodies.size();
+        if (nb == 0) continue;
+        const int ncols = nb * nrhs;
+        const ShapeDev &sd = sh.dev;
+        if (ctx->opt.precision == 1) {
+            CK(gather_rotate(D, gamma, ctx->sumM * D, sh.col_body, sh.col_rhs, ctx->tgt_off_d, ctx->rot64_d, ncols,
+                             sd.dM, sh.A, sh.A64, st));
+            CK(gemm_rm64(ncols, sd.r, sd.dM, sh.A64, sd.U64, sh.T64, st));
+            CK(gemm_rm64(ncols, sd.dN, sd.r, sh.T64, project ? sd.Wp64 : sd.Wr64, sh.L64, st));
+            CK(scatter_rotate(D, nullptr, sh.L64, sh.col_body, sh.col_rhs, ctx->src_off_d, ctx->rot_d, ctx->rot64_d,
+                              ncols, sd.dN, ctx->sumN, lambda, st));
+        } else {
+            CK(gather_rotate(D, gamma, ctx->sumM * D, sh.col_body, sh.col_rhs, ctx->tgt_off_d, ctx->rot64_d, ncols,
+                             sd.dM, sh.A, nullptr, st));
+            CK(gemm_rm(ncols, sd.r, sd.dM, sh.A, sd.U, sh.Tm, st));
+            CK(gemm_rm(ncols, sd.dN, sd.r, sh.Tm, project ? sd.Wp : sd.Wr, sh.Lm, st));
+            CK(scatter_rotate(D, sh.Lm, nullptr, sh.col_body, sh.col_rhs, ctx->src_off_d, ctx->rot_d, ctx->rot64_d,
+                              ncols, sd.dN, ctx->sumN, lambda, st));
+        }
+        ctx->launches += 4;
+    }
+    return MFS_OK;
+}
+
+// y = gamma + sum_{k' != k} S^(kk') (I - L^(k')) S_L^(k')+ gamma^(k')  (Eq. 2esysprec)
+mfs_status matvec_dev(mfs_ctx *ctx, const double *gamma, double *y, int nrhs, cudaStream_t st) {
+    CKS(precond_apply_dev(ctx, gamma, ctx->lam_d, 1, nrhs, st));
+    CKS(pair_apply(ctx, ctx->lam_d, y, gamma, 1.0, 1.0, nrhs, 0, st));
+    return MFS_OK;
+}
+
+mfs_status ensure_gmres(mfs_ctx *ctx, int nrhs) {
+    const long long n = (long long)nrhs * ctx->sumM * ctx->D;
+    const int L = nrhs * ctx->S;
+    const int m = std::min(ctx->opt.restart, ctx->opt.max_iter);
+    if (ctx->gd.V && ctx->gd_n == (size_t)n && ctx->gd_L == L && ctx->gd_m == m) return MFS_OK;
+    // free old
+    void *olds[] = {ctx->gd.V, ctx->gd.H, ctx->gd.cs, ctx->gd.sn, ctx->gd.g, ctx->gd.beta, ctx->gd.hbuf,
+                    ctx->gd.htmp, ctx->gd.hn, ctx->gd.part, ctx->gd.active, ctx->gd.iters, ctx->gd.status,
+                    ctx->gd.resid, ctx->gd.done, ctx->seg_off_d, ctx->w_d, ctx->b_d, ctx->x_d, ctx->ysmall_d};
+    for (void *p : olds) ctx->release(p);
+    GmresDev &gd = ctx->gd;
+    gd = GmresDev{};
+    gd.L = L;
+    gd.m = m;
+    gd.n = n;
+    gd.tol = ctx->opt.gmres_tol;
+    // blocks per lane: enough parallelism for the reductions, at least one
+    const long long per_lane = n / std::max(L, 1);
+    gd.part_blocks = (int)std::max<long long>(1, std::min<long long>(4 * (long long)ctx->sm_count / std::max(L, 1) + 1,
+                                                                     (per_lane + 4095) / 4096));
+    gd.part_blocks = std::min(gd.part_blocks, 512);
+    std::vector<long long> seg(L + 1);
+    for (int h = 0; h < nrhs; ++h)
+        for (int s = 0; s < ctx->S; ++s) {
+            const int l = h * ctx->S + s;
+            seg[l] = (long long)h * ctx->sumM * ctx->D + (long long)ctx->tgt_off[ctx->body_off[s]] * ctx->D;
+        }
+    seg[L] = n;
+    CK(ctx->alloc(&ctx->seg_off_d, L + 1));
+    CK(cudaMemcpy(ctx->seg_off_d, seg.data(), sizeof(long long) * (L + 1), cudaMemcpyHostToDevice));
+    gd.seg_off = ctx->seg_off_d;
+    CK(ctx->alloc(&gd.V, (size_t)(m + 1) * n));
+    CK(cudaMemset(gd.V, 0, sizeof(double) * (size_t)(m + 1) * n));
+    CK(ctx->alloc(&gd.H, (size_t)L * (m + 1) * m));
+    CK(ctx->alloc(&gd.cs, (size_t)L * m));
+    CK(ctx->alloc(&gd.sn, (size_t)L * m));
+    CK(ctx->alloc(&gd.g, (size_t)L * (m + 1)));
+    CK(ctx->alloc(&gd.beta, L));
+    CK(ctx->alloc(&gd.hbuf, (size_t)L * (m + 1)));
+    CK(ctx->alloc(&gd.htmp, (size_t)L * (m + 1)));
+    CK(ctx->alloc(&gd.hn, L));
+    CK(ctx->alloc(&gd.part, (size_t)L * gd.part_blocks * (m + 1)));
+    CK(ctx->alloc(&gd.active, L));
+    CK(ctx->alloc(&gd.iters, L));
+    CK(ctx->alloc(&gd.status, L));
+    CK(ctx->alloc(&gd.resid, L));
+    CK(ctx->alloc(&gd.done, 1));
+    CK(ctx->alloc(&ctx->w_d, n));
+    CK(ctx->alloc(&ctx->b_d, n));
+    CK(ctx->alloc(&ctx->x_d, n));
+    CK(ctx->alloc(&ctx->ysmall_d, (size_t)L * (m + 1)));
+    ctx->gd_n = n;
+    ctx->gd_L = L;
+    ctx->gd_m = m;
+    return MFS_OK;
+}
+
+struct SolveStats {
+    int iters = 0, converged = 1, matvecs = 0, breakdown = 0;
+    double resid = 0.0;
+};
+
+// Solve A x = b (b = ctx->b_d) for all lanes; x in ctx->x_d.
+mfs_status gmres_solve(mfs_ctx *ctx, int nrhs, cudaStream_t st, SolveStats &stats) {
+    GmresDev &gd = ctx->gd;
+    CK(gmres_init(gd, ctx->b_d, st));
+    ctx->launches += 5;
+    int j = 0;
+    for (; j < gd.m; ++j) {
+        CKS(matvec_dev(ctx, gd.V + (size_t)j * gd.n, ctx->w_d, nrhs, st));
+        stats.matvecs++;
+        CK(gmres_arnoldi(gd, ctx->w_d, j, st));
+        ctx->launches += 9;
+        CK(cudaMemcpyAsync(ctx->done_h, gd.done, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (*ctx->done_h) break;
+    }
+    CK(gmres_solution(gd, ctx->x_d, ctx->ysmall_d, st));
+    ctx->launches += 2;
+    std::vector<int> it(gd.L), status(gd.L), active(gd.L);
+    std::vector<double> res(gd.L);
+    CK(cudaMemcpyAsync(it.data(), gd.iters, sizeof(int) * gd.L, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(status.data(), gd.status, sizeof(int) * gd.L, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(res.data(), gd.resid, sizeof(double) * gd.L, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int l = 0; l < gd.L; ++l) {
+        stats.iters = std::max(stats.iters, it[l]);
+        stats.resid = std::max(stats.resid, res[l]);
+        if (status[l] == 2) stats.breakdown = 1;
+        if (!(res[l] <= gd.tol)) stats.converged = 0;
+    }
+    CKS(check_device_error(ctx, st));
+    return MFS_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void mfs_default_options(mfs_options *opt) {
+    if (!opt) return;
+    opt->mu = 1.0;
+    opt->gmres_tol = 1e-7;
+    opt->max_iter = 200;
+    opt->restart = 200;
+    opt->eps_trunc = 0.0;
+    opt->precision = 0;
+    opt->autotune = 1;
+    opt->max_rhs = 4;
+    opt->profile = 0;
+}
+
+int32_t mfs_abi_version(void) { return MFS_ABI_VERSION; }
+
+const char *mfs_last_error(const mfs_ctx *ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+const char *mfs_setup_error(void) { return g_setup_error.c_str(); }
+
+void mfs_destroy(mfs_ctx *ctx) { delete ctx; }
+
+}  // extern "C"
+
+static mfs_status setup_impl(mfs_ctx *ctx, mfs_kind kind, const mfs_bodies *bodies, int32_t num_shapes,
+                             const mfs_pointset *proxy, const mfs_pointset *colloc, cudaStream_t st) {
+    auto t0 = std::chrono::steady_clock::now();
+    ctx->kind = kind;
+    ctx->D = kind == MFS_STOKES ? 3 : 1;
+    const int P = bodies->num_bodies;
+    ctx->P = P;
+    ctx->nshapes = num_shapes;
+    ctx->S = bodies->num_suspensions > 0 && bodies->body_offsets ? bodies->num_suspensions : 1;
+    ctx->centres.assign(bodies->centers, bodies->centers + 3 * P);
+    ctx->shape_id.resize(P);
+    for (int k = 0; k < P; ++k) ctx->shape_id[k] = bodies->shape_id ? bodies->shape_id[k] : 0;
+    if (bodies->body_offsets && bodies->num_suspensions > 0)
+        ctx->body_off.assign(bodies->body_offsets, bodies->body_offsets + ctx->S + 1);
+    else
+        ctx->body_off = {0, P};
+    // validation
+    if (ctx->body_off.front() != 0 || ctx->body_off.back() != P) {
+        ctx->last_error = "body_offsets must start at 0 and end at num_bodies";
+        return MFS_ERR_INVALID_ARG;
+    }
+    for (int s = 0; s < ctx->S; ++s)
+        if (ctx->body_off[s + 1] <= ctx->body_off[s]) {
+            ctx->last_error = "every suspension needs at least one body";
+            return MFS_ERR_INVALID_ARG;
+        }
+    for (int k = 0; k < P; ++k) {
+        if (ctx->shape_id[k] < 0 || ctx->shape_id[k] >= num_shapes) {
+            ctx->last_error = "shape_id out of range";
+            return MFS_ERR_INVALID_ARG;
+        }
+        for (int c = 0; c < 3; ++c)
+            if (!std::isfinite(ctx->centres[3 * k + c])) {
+                ctx->last_error = "non-finite body centre";
+                return MFS_ERR_INVALID_ARG;
+            }
+    }
+    ctx->rot.resize(9 * P);
+    for (int k = 0; k < P; ++k) {
+        if (bodies->quats) {
+            double q[4];
+            double nq = 0.0;
+            for (int c = 0; c < 4; ++c) {
+                q[c] = bodies->quats[4 * k + c];
+                nq += q[c] * q[c];
+            }
+            if (!(nq > 0.0) || !std::isfinite(nq)) {
+                ctx->last_error = "quaternion must be non-zero and finite";
+                return MFS_ERR_INVALID_ARG;
+            }
+            nq = std::sqrt(nq);
+            for (int c = 0; c < 4; ++c) q[c] /= nq;
+            quat_to_rot(q, &ctx->rot[9 * k]);
+        } else {
+            const double I[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+            std::memcpy(&ctx->rot[9 * k], I, sizeof(I));
+        }
+    }
+    ctx->shapes.resize(num_shapes);
+    for (int s = 0; s < num_shapes; ++s) {
+        ShapeHost &sh = ctx->shapes[s];
+        sh.M = colloc[s].n;
+        sh.N = proxy[s].n;
+        if (sh.N <= 0 || sh.M <= sh.N || !colloc[s].pts || !proxy[s].pts) {
+            ctx->last_error = "each shape needs 0 < N < M points";
+            return MFS_ERR_INVALID_ARG;
+        }
+        sh.X0.assign(colloc[s].pts, colloc[s].pts + 3 * sh.M);
+        sh.Y0.assign(proxy[s].pts, proxy[s].pts + 3 * sh.N);
+        for (double v : sh.X0)
+            if (!std::isfinite(v)) { ctx->last_error = "non-finite collocation point"; return MFS_ERR_INVALID_ARG; }
+        for (double v : sh.Y0)
+            if (!std::isfinite(v)) { ctx->last_error = "non-finite proxy point"; return MFS_ERR_INVALID_ARG; }
+        double G0[36];
+        gram6(sh.Y0, G0);
+        if (kind == MFS_STOKES) {
+            if (!invert6(G0, sh.G0inv)) {
+                ctx->last_error = "proxy points do not span rigid-body motions (singular K_N^T K_N)";
+                return MFS_ERR_INVALID_ARG;
+            }
+        } else {
+            std::memset(sh.G0inv, 0, sizeof(sh.G0inv));
+        }
+    }
+    for (int k = 0; k < P; ++k) ctx->shapes[ctx->shape_id[k]].bodies.push_back(k);
+
+    // offsets
+    ctx->tgt_off.assign(P + 1, 0);
+    ctx->src_off.assign(P + 1, 0);
+    ctx->rec_off.assign(P + 1, 0);
+    ctx->blk_off.assign(P + 1, 0);
+    for (int k = 0; k < P; ++k) {
+        const ShapeHost &sh = ctx->shapes[ctx->shape_id[k]];
+        const int npad = (sh.N + 3) / 4 * 4;
+        ctx->tgt_off[k + 1] = ctx->tgt_off[k] + sh.M;
+        ctx->src_off[k + 1] = ctx->src_off[k] + sh.N;
+        ctx->rec_off[k + 1] = ctx->rec_off[k] + npad;
+        ctx->blk_off[k + 1] = ctx->blk_off[k] + (npad + MFS_BS - 1) / MFS_BS;
+    }
+    ctx->sumM = ctx->tgt_off[P];
+    ctx->sumN = ctx->src_off[P];
+    ctx->nrec = ctx->rec_off[P];
+    ctx->tgt_body.resize(ctx->sumM);
+    for (int k = 0; k < P; ++k)
+        for (int i = ctx->tgt_off[k]; i < ctx->tgt_off[k + 1]; ++i) ctx->tgt_body[i] = k;
+
+    // rotated body-local points
+    std::vector<float4> tgt_pos(ctx->sumM), src_pos(ctx->sumN);
+    std::vector<double> tgt64(3 * (size_t)ctx->sumM), src64(3 * (size_t)ctx->sumN), src4(4 * (size_t)ctx->sumN);
+    std::vector<int> rec_pt(ctx->nrec, -1), susp_b(P), susp_e(P);
+    for (int s = 0; s < ctx->S; ++s)
+        for (int k = ctx->body_off[s]; k < ctx->body_off[s + 1]; ++k) {
+            susp_b[k] = ctx->src_off[ctx->body_off[s]];
+            susp_e[k] = ctx->src_off[ctx->body_off[s + 1]];
+        }
+    for (int k = 0; k < P; ++k) {
+        const ShapeHost &sh = ctx->shapes[ctx->shape_id[k]];
+        const double *R = &ctx->rot[9 * k];
+        for (int i = 0; i < sh.M; ++i) {
+            double x[3];
+            for (int a = 0; a < 3; ++a)
+                x[a] = R[3 * a] * sh.X0[3 * i] + R[3 * a + 1] * sh.X0[3 * i + 1] + R[3 * a + 2] * sh.X0[3 * i + 2];
+            const int t = ctx->tgt_off[k] + i;
+            float kb;
+            std::memcpy(&kb, &k, sizeof(float));  // body id stored as int bits
+            tgt_pos[t] = make_float4((float)x[0], (float)x[1], (float)x[2], kb);
+            for (int a = 0; a < 3; ++a) tgt64[3 * (size_t)t + a] = x[a];
+        }
+        for (int j = 0; j < sh.N; ++j) {
+            double y[3];
+            for (int a = 0; a < 3; ++a)
+                y[a] = R[3 * a] * sh.Y0[3 * j] + R[3 * a + 1] * sh.Y0[3 * j + 1] + R[3 * a + 2] * sh.Y0[3 * j + 2];
+            const int q = ctx->src_off[k] + j;
+            src_pos[q] = make_float4((float)y[0], (float)y[1], (float)y[2], 0.f);
+            for (int a = 0; a < 3; ++a) {
+                src64[3 * (size_t)q + a] = y[a];
+                src4[4 * (size_t)q + a] = y[a];
+            }
+            src4[4 * (size_t)q + 3] = (double)k;
+            rec_pt[ctx->rec_off[k] + j] = q;
+        }
+    }
+    // padding records point at the body centre: rec_pt = -1 packs (0,0,0) with zero strength
+    std::vector<float> rot32(9 * (size_t)P);
+    for (size_t i = 0; i < rot32.size(); ++i) rot32[i] = (float)ctx->rot[i];
+
+    CK(ctx->alloc(&ctx->centres_d, 3 * (size_t)P));
+    CK(ctx->alloc(&ctx->rot64_d, 9 * (size_t)P));
+    CK(ctx->alloc(&ctx->rot_d, 9 * (size_t)P));
+    CK(ctx->alloc(&ctx->shape_id_d, P));
+    CK(ctx->alloc(&ctx->tgt_pos_d, ctx->sumM));
+    CK(ctx->alloc(&ctx->src_pos_d, ctx->sumN));
+    CK(ctx->alloc(&ctx->tgt_local64_d, 3 * (size_t)ctx->sumM));
+    CK(ctx->alloc(&ctx->src_local64_d, 3 * (size_t)ctx->sumN));
+    CK(ctx->alloc(&ctx->src_local4_d, 4 * (size_t)ctx->sumN));
+    CK(ctx->alloc(&ctx->tgt_body_d, ctx->sumM));
+    CK(ctx->alloc(&ctx->rec_pt_d, ctx->nrec));
+    CK(ctx->alloc(&ctx->rec_off_d, P + 1));
+    CK(ctx->alloc(&ctx->blk_off_d, P + 1));
+    CK(ctx->alloc(&ctx->tgt_off_d, P + 1));
+    CK(ctx->alloc(&ctx->src_off_d, P + 1));
+    CK(ctx->alloc(&ctx->susp_src_begin_d, P));
+    CK(ctx->alloc(&ctx->susp_src_end_d, P));
+    CK(ctx->alloc(&ctx->err_d, 1));
+    CK(cudaMemset(ctx->err_d, 0, sizeof(int)));
+    CK(cudaMemcpy(ctx->centres_d, ctx->centres.data(), sizeof(double) * 3 * P, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->rot64_d, ctx->rot.data(), sizeof(double) * 9 * P, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->rot_d, rot32.data(), sizeof(float) * 9 * P, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->shape_id_d, ctx->shape_id.data(), sizeof(int) * P, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->tgt_pos_d, tgt_pos.data(), sizeof(float4) * ctx->sumM, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->src_pos_d, src_pos.data(), sizeof(float4) * ctx->sumN, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->tgt_local64_d, tgt64.data(), sizeof(double) * tgt64.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->src_local64_d, src64.data(), sizeof(double) * src64.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->src_local4_d, src4.data(), sizeof(double) * src4.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->tgt_body_d, ctx->tgt_body.data(), sizeof(int) * ctx->sumM, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->rec_pt_d, rec_pt.data(), sizeof(int) * ctx->nrec, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->rec_off_d, ctx->rec_off.data(), sizeof(int) * (P + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->blk_off_d, ctx->blk_off.data(), sizeof(long long) * (P + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->tgt_off_d, ctx->tgt_off.data(), sizeof(int) * (P + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->src_off_d, ctx->src_off.data(), sizeof(int) * (P + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->susp_src_begin_d, susp_b.data(), sizeof(int) * P, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->susp_src_end_d, susp_e.data(), sizeof(int) * P, cudaMemcpyHostToDevice));
+    {
+        std::vector<double> g0(36 * (size_t)num_shapes);
+        for (int s = 0; s < num_shapes; ++s) std::memcpy(&g0[36 * s], ctx->shapes[s].G0inv, sizeof(double) * 36);
+        CK(ctx->alloc(&ctx->G0inv_d, g0.size()));
+        CK(cudaMemcpy(ctx->G0inv_d, g0.data(), sizeof(double) * g0.size(), cudaMemcpyHostToDevice));
+    }
+
+    // per-shape one-body factors: S_L and its SVD in FP64 (cuSOLVER), then the apply factors
+    cusolverDnHandle_t solver = nullptr;
+    if (cusolverDnCreate(&solver) != CUSOLVER_STATUS_SUCCESS) {
+        ctx->last_error = "cusolverDnCreate failed";
+        return MFS_ERR_CUDA;
+    }
+    cusolverDnSetStream(solver, st);
+    const int D = ctx->D;
+    const int R = ctx->opt.max_rhs;
+    mfs_status status = MFS_OK;
+    for (int s = 0; s < num_shapes && status == MFS_OK; ++s) {
+        ShapeHost &sh = ctx->shapes[s];
+        ShapeDev &sd = sh.dev;
+        sd.M = sh.M;
+        sd.N = sh.N;
+        sd.dM = D * sh.M;
+        sd.dN = D * sh.N;
+        sd.r = sd.dN;
+        double *X0 = nullptr, *Y0 = nullptr, *G0i = nullptr, *SL = nullptr, *Ucm = nullptr, *sig = nullptr,
+               *VT = nullptr, *work = nullptr;
+        int *info_d = nullptr;
+        auto cleanup = [&]() {
+            cudaFree(X0); cudaFree(Y0); cudaFree(G0i); cudaFree(SL); cudaFree(Ucm); cudaFree(sig); cudaFree(VT);
+            cudaFree(work); cudaFree(info_d);
+        };
+        auto fail = [&](const std::string &msg, mfs_status code) {
+            ctx->last_error = msg;
+            status = code;
+        };
+        const int m = sd.dM, n = sd.dN;
+        if (cudaMalloc(&X0, sizeof(double) * 3 * sh.M) != cudaSuccess ||
+            cudaMalloc(&Y0, sizeof(double) * 3 * sh.N) != cudaSuccess ||
+            cudaMalloc(&G0i, sizeof(double) * 36) != cudaSuccess ||
+            cudaMalloc(&SL, sizeof(double) * (size_t)m * n) != cudaSuccess ||
+            cudaMalloc(&Ucm, sizeof(double) * (size_t)m * n) != cudaSuccess ||
+            cudaMalloc(&sig, sizeof(double) * n) != cudaSuccess ||
+            cudaMalloc(&VT, sizeof(double) * (size_t)n * n) != cudaSuccess ||
+            cudaMalloc(&info_d, sizeof(int)) != cudaSuccess) {
+            cleanup();
+            cudaGetLastError();
+            fail("device allocation for the one-body SVD failed", MFS_ERR_OOM);
+            break;
+        }
+        cudaMemcpy(X0, sh.X0.data(), sizeof(double) * 3 * sh.M, cudaMemcpyHostToDevice);
+        cudaMemcpy(Y0, sh.Y0.data(), sizeof(double) * 3 * sh.N, cudaMemcpyHostToDevice);
+        cudaMemcpy(G0i, sh.G0inv, sizeof(double) * 36, cudaMemcpyHostToDevice);
+        cudaError_t ce = build_SL(kind, sh.M, sh.N, X0, Y0, ctx->opt.mu, G0i, SL, st);
+        int lwork = 0;
+        if (ce == cudaSuccess && cusolverDnDgesvd_bufferSize(solver, m, n, &lwork) != CUSOLVER_STATUS_SUCCESS)
+            ce = cudaErrorUnknown;
+        if (ce == cudaSuccess) ce = cudaMalloc(&work, sizeof(double) * std::max(lwork, 1));
+        if (ce == cudaSuccess) {
+            signed char jobu = 'S', jobvt = 'S';
+            cusolverStatus_t cs = cusolverDnDgesvd(solver, jobu, jobvt, m, n, SL, m, sig, Ucm, m, VT, n, work, lwork,
+                                                   nullptr, info_d);
+            if (cs != CUSOLVER_STATUS_SUCCESS) ce = cudaErrorUnknown;
+        }
+        int info_h = 0;
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(&info_h, info_d, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        if (ce != cudaSuccess || info_h != 0) {
+            cleanup();
+            fail(std::string("one-body SVD failed: ") + (ce != cudaSuccess ? cudaGetErrorString(ce) : "gesvd info != 0"),
+                 MFS_ERR_CUDA);
+            break;
+        }
+        // apply factors
+        bool ok = ctx->alloc(&sd.U, (size_t)m * n) == cudaSuccess && ctx->alloc(&sd.Wp, (size_t)n * n) == cudaSuccess &&
+                  ctx->alloc(&sd.Wr, (size_t)n * n) == cudaSuccess;
+        if (ok && ctx->opt.precision == 1)
+            ok = ctx->alloc(&sd.U64, (size_t)m * n) == cudaSuccess &&
+                 ctx->alloc(&sd.Wp64, (size_t)n * n) == cudaSuccess &&
+                 ctx->alloc(&sd.Wr64, (size_t)n * n) == cudaSuccess;
+        if (!ok) {
+            cleanup();
+            fail("device allocation for the apply factors failed", MFS_ERR_OOM);
+            break;
+        }
+        ce = build_apply_factors(kind, sh.M, sh.N, Ucm, sig, VT, Y0, G0i, ctx->opt.eps_trunc, sd, st);
+        cleanup();
+        if (ce != cudaSuccess) {
+            fail(std::string("apply factors: ") + cudaGetErrorString(ce), MFS_ERR_CUDA);
+            break;
+        }
+        if (!(sd.sigma1 > 0.0) || !std::isfinite(sd.sigma1)) {
+            fail("one-body SVD returned a non-finite or zero largest singular value", MFS_ERR_ILL_CONDITIONED);
+            break;
+        }
+        // GEMM column lists and buffers
+        const int nb = (int)sh.bodies.size();
+        std::vector<int> cb(R * nb), cr(R * nb);
+        for (int h = 0; h < R; ++h)
+            for (int i = 0; i < nb; ++i) {
+                cb[h * nb + i] = sh.bodies[i];
+                cr[h * nb + i] = h;
+            }
+        if (nb > 0) {
+            ok = ctx->alloc(&sh.col_body, R * nb) == cudaSuccess && ctx->alloc(&sh.col_rhs, R * nb) == cudaSuccess &&
+                 ctx->alloc(&sh.A, (size_t)R * nb * m) == cudaSuccess &&
+                 ctx->alloc(&sh.Tm, (size_t)R * nb * n) == cudaSuccess &&
+                 ctx->alloc(&sh.Lm, (size_t)R * nb * n) == cudaSuccess;
+            if (ok && ctx->opt.precision == 1)
+                ok = ctx->alloc(&sh.A64, (size_t)R * nb * m) == cudaSuccess &&
+                     ctx->alloc(&sh.T64, (size_t)R * nb * n) == cudaSuccess &&
+                     ctx->alloc(&sh.L64, (size_t)R * nb * n) == cudaSuccess;
+            if (!ok) {
+                fail("device allocation for the preconditioner buffers failed", MFS_ERR_OOM);
+                break;
+            }
+            cudaMemcpy(sh.col_body, cb.data(), sizeof(int) * cb.size(), cudaMemcpyHostToDevice);
+            cudaMemcpy(sh.col_rhs, cr.data(), sizeof(int) * cr.size(), cudaMemcpyHostToDevice);
+        }
+    }
+    cusolverDnDestroy(solver);
+    if (status != MFS_OK) return status;
+
+    // work buffers
+    const int recf = pair_record_floats(D, R);
+    CK(ctx->alloc(&ctx->rec_d, (size_t)ctx->nrec * recf));
+    CK(cudaMemset(ctx->rec_d, 0, sizeof(float) * (size_t)ctx->nrec * recf));
+    CK(ctx->alloc(&ctx->lam_d, (size_t)R * ctx->sumN * D));
+    if (ctx->opt.precision == 1) CK(ctx->alloc(&ctx->raw_d, (size_t)R * ctx->sumM * D));
+    CK(cudaMallocHost(&ctx->done_h, sizeof(int)));
+    CK(cudaEventCreate(&ctx->ev0));
+    CK(cudaEventCreate(&ctx->ev1));
+    CK(cudaEventCreate(&ctx->evp0));
+    CK(cudaEventCreate(&ctx->evp1));
+    CK(cudaStreamSynchronize(st));
+    ctx->ms_setup = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return MFS_OK;
+}
+
+// Time every pair-kernel variant for (D, nrhs) on the actual geometry and keep the fastest.
+static mfs_status autotune(mfs_ctx *ctx, int nrhs, cudaStream_t st) {
+    int count = 0;
+    const PairVariant *v = pair_variants(&count);
+    double best = 1e300;
+    int best_i = -1;
+    for (int i = 0; i < count; ++i) {
+        if (v[i].D != ctx->D || v[i].nrhs != nrhs) continue;
+        if (pair_occupancy(i) <= 0) continue;
+        PairPlan *plan = nullptr;
+        CKS(get_plan(ctx, i, 0, &plan));
+        const PairWork w = work_of(*plan);
+        if (w.total_units == 0) return MFS_OK;
+        float ms_best = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            CK(cudaEventRecord(ctx->ev0, st));
+            CK(pair_launch(i, geom_of(ctx), w, ctx->err_d, st));
+            CK(cudaEventRecord(ctx->ev1, st));
+            CK(cudaEventSynchronize(ctx->ev1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+            if (rep > 0) ms_best = std::min(ms_best, ms);
+        }
+        if (ms_best < best) {
+            best = ms_best;
+            best_i = i;
+        }
+    }
+    ctx->best_variant[ctx->D == 3][nrhs] = best_i;
+    return check_device_error(ctx, st);
+}
+
+extern "C" {
+
+mfs_status mfs_setup(mfs_ctx **out, mfs_kind kind, const mfs_bodies *bodies, int32_t num_shapes,
+                     const mfs_pointset *proxy, const mfs_pointset *colloc, const mfs_options *opt, void *stream) {
+    g_setup_error.clear();
+    if (!out || !bodies || !proxy || !colloc || num_shapes <= 0 || bodies->num_bodies <= 0 || !bodies->centers ||
+        (kind != MFS_LAPLACE && kind != MFS_STOKES)) {
+        g_setup_error = "mfs_setup: invalid argument";
+        return MFS_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    std::unique_ptr<mfs_ctx> ctx(new mfs_ctx());
+    if (opt) ctx->opt = *opt; else mfs_default_options(&ctx->opt);
+    if (ctx->opt.max_rhs < 1 || ctx->opt.max_rhs > 4 || ctx->opt.max_iter < 1 || ctx->opt.restart < 1 ||
+        ctx->opt.restart > 1023 || !(ctx->opt.mu > 0.0) || !(ctx->opt.gmres_tol >= 0.0) ||
+        ctx->opt.precision < 0 || ctx->opt.precision > 1 || !(ctx->opt.eps_trunc >= 0.0)) {
+        g_setup_error = "mfs_setup: invalid options";
+        return MFS_ERR_INVALID_ARG;
+    }
+    if (ctx->opt.max_iter > ctx->opt.restart) {
+        g_setup_error = "mfs_setup: max_iter above restart is not supported (no restarted GMRES)";
+        return MFS_ERR_INVALID_ARG;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        g_setup_error = "mfs_setup: no CUDA device";
+        return MFS_ERR_CUDA;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    mfs_status s = setup_impl(ctx.get(), kind, bodies, num_shapes, proxy, colloc, st);
+    if (s == MFS_OK && ctx->opt.autotune && ctx->opt.precision == 0) {
+        // tune the single-rhs variant now; other nrhs on first use
+        std::vector<double> zero((size_t)ctx->sumN * ctx->D, 0.0);
+        mfs_ctx *c = ctx.get();
+        cudaError_t e = cudaMemsetAsync(c->lam_d, 0, sizeof(double) * zero.size(), st);
+        if (e == cudaSuccess) e = pack_sources(c->D, 1, c->src_pos_d, c->rec_pt_d, c->lam_d, c->sumN, c->nrec, c->rec_d, st);
+        s = (e == cudaSuccess) ? autotune(c, 1, st) : MFS_ERR_CUDA;
+    }
+    if (s != MFS_OK) {
+        g_setup_error = ctx->last_error;
+        return s;
+    }
+    *out = ctx.release();
+    return MFS_OK;
+}
+
+mfs_status mfs_update_centers(mfs_ctx *ctx, const double *centers, void *stream) {
+    if (!ctx || !centers) return MFS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (is_device_ptr(centers)) {
+        CK(cudaMemcpyAsync(ctx->centres.data(), centers, sizeof(double) * 3 * ctx->P, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    } else {
+        std::memcpy(ctx->centres.data(), centers, sizeof(double) * 3 * ctx->P);
+    }
+    for (double v : ctx->centres)
+        if (!std::isfinite(v)) {
+            ctx->last_error = "non-finite body centre";
+            return MFS_ERR_INVALID_ARG;
+        }
+    CK(cudaMemcpyAsync(ctx->centres_d, ctx->centres.data(), sizeof(double) * 3 * ctx->P, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    return MFS_OK;
+}
+
+mfs_status mfs_matvec(mfs_ctx *ctx, const double *gamma, double *y, int32_t nrhs, void *stream) {
+    if (!ctx || !gamma || !y || nrhs < 1 || nrhs > ctx->opt.max_rhs) {
+        if (ctx) ctx->last_error = "mfs_matvec: invalid argument";
+        return MFS_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)nrhs * ctx->sumM * ctx->D;
+    Staged gi, yo;
+    CKS(stage_in(ctx, gi, gamma, n, st));
+    CKS(stage_out_alloc(ctx, yo, y, n));
+    CKS(matvec_dev(ctx, gi.d, yo.d, nrhs, st));
+    CKS(stage_out_finish(ctx, yo, st));
+    return check_device_error(ctx, st);
+}
+
+mfs_status mfs_precond_apply(mfs_ctx *ctx, const double *gamma, double *lambda, int32_t project, int32_t nrhs,
+                             void *stream) {
+    if (!ctx || !gamma || !lambda || nrhs < 1 || nrhs > ctx->opt.max_rhs) {
+        if (ctx) ctx->last_error = "mfs_precond_apply: invalid argument";
+        return MFS_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    Staged gi, lo;
+    CKS(stage_in(ctx, gi, gamma, (size_t)nrhs * ctx->sumM * ctx->D, st));
+    CKS(stage_out_alloc(ctx, lo, lambda, (size_t)nrhs * ctx->sumN * ctx->D));
+    CKS(precond_apply_dev(ctx, gi.d, lo.d, project ? 1 : 0, nrhs, st));
+    CKS(stage_out_finish(ctx, lo, st));
+    return MFS_OK;
+}
+
+mfs_status mfs_pair_sum(mfs_ctx *ctx, const double *strengths, double *u, int32_t nrhs, int32_t include_self,
+                        void *stream) {
+    if (!ctx || !strengths || !u || nrhs < 1 || nrhs > ctx->opt.max_rhs) {
+        if (ctx) ctx->last_error = "mfs_pair_sum: invalid argument";
+        return MFS_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    Staged si, uo;
+    CKS(stage_in(ctx, si, strengths, (size_t)nrhs * ctx->sumN * ctx->D, st));
+    CKS(stage_out_alloc(ctx, uo, u, (size_t)nrhs * ctx->sumM * ctx->D));
+    CKS(pair_apply(ctx, si.d, uo.d, nullptr, 0.0, 1.0, nrhs, include_self ? 1 : 0, st));
+    CKS(stage_out_finish(ctx, uo, st));
+    return check_device_error(ctx, st);
+}
+
+static void begin_call(mfs_ctx *ctx) {
+    ctx->launches = 0;
+    ctx->pair_launches = 0;
+    ctx->pair_ms_acc = 0.0;
+}
+
+static double pair_profile_ms(mfs_ctx *ctx) {
+    if (!ctx->opt.profile) return 0.0;
+    double total = 0.0;
+    for (int i = 0; i < ctx->pair_launches && 2 * (size_t)i + 1 < ctx->pev.size(); ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->pev[2 * i], ctx->pev[2 * i + 1]) == cudaSuccess) total += ms;
+    }
+    return total;
+}
+
+static mfs_status finish_info(mfs_ctx *ctx, mfs_solve_info *info, const SolveStats &ss, float ms, int nrhs) {
+    ctx->pair_ms_acc = pair_profile_ms(ctx);
+    if (info) {
+        info->launches = ctx->launches;
+        info->pair_launches = ctx->pair_launches;
+        info->iters = ss.iters;
+        info->converged = ss.converged;
+        info->matvecs = ss.matvecs;
+        info->lanes = nrhs * ctx->S;
+        info->rel_residual = ss.resid;
+        info->ms_setup = ctx->ms_setup;
+        info->ms_solve = ms;
+        info->ms_pairs = ctx->pair_ms_acc;
+        info->pairs = pair_count(ctx, 0) * ss.matvecs + pair_count(ctx, 1);
+    }
+    if (ss.breakdown) {
+        ctx->last_error = "GMRES breakdown: non-finite residual";
+        return MFS_ERR_BREAKDOWN;
+    }
+    if (!ss.converged) {
+        ctx->last_error = "GMRES did not reach the tolerance within max_iter";
+        return MFS_ERR_NOT_CONVERGED;
+    }
+    return MFS_OK;
+}
+
+mfs_status mfs_solve_mobility(mfs_ctx *ctx, const double *F, const double *T, double *U, double *Omega, int32_t nrhs,
+                              mfs_solve_info *info, void *stream) {
+    if (!ctx || !F || !T || !U || !Omega || nrhs < 1 || nrhs > ctx->opt.max_rhs) {
+        if (ctx) ctx->last_error = "mfs_solve_mobility: invalid argument";
+        return MFS_ERR_INVALID_ARG;
+    }
+    if (ctx->kind != MFS_STOKES) {
+        ctx->last_error = "mfs_solve_mobility needs a Stokes context";
+        return MFS_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nb = (size_t)nrhs * ctx->P * 3;
+    Staged Fi, Ti, Uo, Oo;
+    CKS(stage_in(ctx, Fi, F, nb, st));
+    CKS(stage_in(ctx, Ti, T, nb, st));
+    CKS(stage_out_alloc(ctx, Uo, U, nb));
+    CKS(stage_out_alloc(ctx, Oo, Omega, nb));
+    if (ctx->opt.autotune && ctx->opt.precision == 0 && ctx->best_variant[1][nrhs] < 0) CKS(autotune(ctx, nrhs, st));
+    CKS(ensure_gmres(ctx, nrhs));
+    begin_call(ctx);
+    CK(cudaEventRecord(ctx->ev0, st));
+    ctx->launches += 1;
+    // lambda_0 and b = -u_0 (all pairs, Eq. stou0)
+    CK(completion_stokes(Fi.d, Ti.d, nrhs, ctx->P, ctx->rot64_d, ctx->G0inv_d, ctx->shape_id_d, ctx->src_local64_d,
+                         ctx->src_off_d, ctx->sumN, ctx->lam_d, st));
+    CKS(pair_apply(ctx, ctx->lam_d, ctx->b_d, nullptr, 0.0, -1.0, nrhs, 1, st));
+    SolveStats ss;
+    CKS(gmres_solve(ctx, nrhs, st, ss));
+    // lambda = S_L^+ gamma, [U; Omega] = -K_N^T lambda (Eq. getU)
+    CKS(precond_apply_dev(ctx, ctx->x_d, ctx->lam_d, 0, nrhs, st));
+    CK(extract_stokes(ctx->lam_d, nrhs, ctx->P, ctx->src_local64_d, ctx->src_off_d, ctx->sumN, Uo.d, Oo.d, st));
+    ctx->launches += 1;
+    CK(cudaEventRecord(ctx->ev1, st));
+    CK(cudaEventSynchronize(ctx->ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    CKS(stage_out_finish(ctx, Uo, st));
+    CKS(stage_out_finish(ctx, Oo, st));
+    ctx->last_nrhs = nrhs;
+    return finish_info(ctx, info, ss, ms, nrhs);
+}
+
+mfs_status mfs_solve_elastance(mfs_ctx *ctx, const double *Q, double *V, int32_t nrhs, mfs_solve_info *info,
+                               void *stream) {
+    if (!ctx || !Q || !V || nrhs < 1 || nrhs > ctx->opt.max_rhs) {
+        if (ctx) ctx->last_error = "mfs_solve_elastance: invalid argument";
+        return MFS_ERR_INVALID_ARG;
+    }
+    if (ctx->kind != MFS_LAPLACE) {
+        ctx->last_error = "mfs_solve_elastance needs a Laplace context";
+        return MFS_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nb = (size_t)nrhs * ctx->P;
+    Staged Qi, Vo;
+    CKS(stage_in(ctx, Qi, Q, nb, st));
+    CKS(stage_out_alloc(ctx, Vo, V, nb));
+    if (ctx->opt.autotune && ctx->opt.precision == 0 && ctx->best_variant[0][nrhs] < 0) CKS(autotune(ctx, nrhs, st));
+    CKS(ensure_gmres(ctx, nrhs));
+    begin_call(ctx);
+    CK(cudaEventRecord(ctx->ev0, st));
+    ctx->launches += 1;
+    CK(completion_laplace(Qi.d, nrhs, ctx->P, ctx->src_off_d, ctx->sumN, ctx->lam_d, st));  // Eq. al0
+    CKS(pair_apply(ctx, ctx->lam_d, ctx->b_d, nullptr, 0.0, -1.0, nrhs, 1, st));           // b = -u_0, Eq. erhsK
+    SolveStats ss;
+    CKS(gmres_solve(ctx, nrhs, st, ss));
+    CKS(precond_apply_dev(ctx, ctx->x_d, ctx->lam_d, 0, nrhs, st));
+    CK(extract_laplace(ctx->lam_d, nrhs, ctx->P, ctx->src_off_d, ctx->sumN, Vo.d, st));  // Eq. vkal
+    ctx->launches += 1;
+    CK(cudaEventRecord(ctx->ev1, st));
+    CK(cudaEventSynchronize(ctx->ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    CKS(stage_out_finish(ctx, Vo, st));
+    return finish_info(ctx, info, ss, ms, nrhs);
+}
+
+mfs_status mfs_mobility_vjp(mfs_ctx *ctx, const double *dU, const double *dOmega, int32_t nrhs, double *dcenters,
+                            double *dF, double *dT, void *stream) {
+    (void)dU; (void)dOmega; (void)nrhs; (void)dcenters; (void)dF; (void)dT; (void)stream;
+    if (ctx) ctx->last_error = "mfs_mobility_vjp: not available in this build";
+    return MFS_ERR_INVALID_ARG;
+}
+
+}  // extern "C"
