@@ -75,8 +75,9 @@ typedef struct {
     int32_t max_iter;  /* GMRES iteration cap per solve; default 200 */
     int32_t restart;   /* Krylov basis size before a restart; default 200 (no restart) */
     double eps_trunc;  /* singular values <= sigma_1 * eps_trunc are dropped (Eq. pseudo); default 0 */
-    int32_t precision; /* 0: FP32 pair sums with compensated accumulation (default);
-                          1: FP64 pair sums and FP64 preconditioner (reference GPU path) */
+    int32_t precision; /* 0: FP32 pair sums with compensated accumulation and FP32 one-body apply (default);
+                          1: FP64 pair sums and FP64 one-body apply (reference GPU path);
+                          2: FP32 pair sums, FP64 one-body apply */
     int32_t autotune;  /* 1: time pair-kernel variants on this geometry at setup (default 1) */
     int32_t max_rhs;   /* largest nrhs any later call will use (1..4); default 4 */
     int32_t profile;   /* 1: bracket every pair-kernel launch with CUDA events (no host sync) and report

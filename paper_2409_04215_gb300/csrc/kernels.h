@@ -9,15 +9,16 @@ namespace mfs {
 // ---- pair sums (pair_kernel.cu) ----
 struct PairVariant {
     int D, nrhs, T, NT, tile_targets;
+    int packed;  // 1: f32x2 Stokes policy with duplicated source records
 };
 const PairVariant *pair_variants(int *count);
 int pair_occupancy(int variant);  // resident CTAs per SM
-int pair_record_floats(int D, int nrhs);
+int pair_record_floats(int D, int nrhs, int packed);
 cudaError_t pair_launch(int variant, const PairGeom &geo, const PairWork &work, int *err, cudaStream_t st);
 cudaError_t pair_epilogue(int D, int nrhs, const PairWork &work, const double *base, double beta, double scale,
                           double *out, int ntargets, cudaStream_t st);
-cudaError_t pack_sources(int D, int nrhs, const float4 *src_pos, const int *src_pt_of_rec, const double *strength,
-                         int nsrc, int nrec, float *records, cudaStream_t st);
+cudaError_t pack_sources(int D, int nrhs, int packed, const float4 *src_pos, const int *src_pt_of_rec,
+                         const double *strength, int nsrc, int nrec, float *records, cudaStream_t st);
 
 // FP64 reference pair sum (precision = 1): one thread per target, direct loops; raw sums (no 1/(4pi) factor).
 cudaError_t pair_sum_fp64(int D, int nrhs, const double *tgt_local, const int *tgt_body, int ntargets,
@@ -49,6 +50,11 @@ cudaError_t gather_rotate(int D, const double *gamma, int sum_MD, const int *col
                           cudaStream_t st);
 // C[m][n] = sum_k A[m][k] B[k][n]  (row-major; FP32 SIMT tiles, or FP64 when A64/B64 given).
 cudaError_t gemm_rm(int m, int n, int k, const float *A, const float *B, float *C, cudaStream_t st);
+// Split-K FP32 GEMM with TwoSum-compensated slices; chunk results (FP64, P [S][m][n]) summed in FP64
+// into C32 (FP32) or C64 (FP64).  S from gemm_splitk_chunks; P must hold S*m*n doubles.
+int gemm_splitk_chunks(int m, int n, int k, int sm_count);
+cudaError_t gemm_splitk(int m, int n, int k, int S, const float *A, const float *B, double *P, float *C32,
+                        double *C64, cudaStream_t st);
 cudaError_t gemm_rm64(int m, int n, int k, const double *A, const double *B, double *C, cudaStream_t st);
 // Scatter: lambda (FP64 [nrhs][sum_N][D]) at the columns' bodies = R_k * Lcol (rotate back).
 cudaError_t scatter_rotate(int D, const float *L, const double *L64, const int *col_body, const int *col_rhs,

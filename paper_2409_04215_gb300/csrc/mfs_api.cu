@@ -46,6 +46,8 @@ struct ShapeHost {
     std::vector<int> bodies;     // bodies of this shape
     int *col_body = nullptr, *col_rhs = nullptr;  // device, [max_rhs * nbodies]
     float *A = nullptr, *Tm = nullptr, *Lm = nullptr;  // GEMM buffers
+    double *Pk = nullptr;                              // split-K chunk results
+    size_t Pk_count = 0;
     double *A64 = nullptr, *T64 = nullptr, *L64 = nullptr;
     ShapeDev dev{};
 };
@@ -267,11 +269,12 @@ void gram6(const std::vector<double> &Y0, double *G) {
 int default_variant(int D, int nrhs) {
     int count = 0;
     const PairVariant *v = pair_variants(&count);
-    // preferred (T, NT) per kind and nrhs
-    int wantT = (D == 3) ? (nrhs == 1 ? 4 : (nrhs == 4 ? 2 : 2)) : (nrhs == 1 ? 4 : 4);
-    int wantNT = 128;
+    // preferred variant per kind and nrhs when not autotuned: packed f32x2 for Stokes, scalar for Laplace
+    const int wantT = (D == 3) ? (nrhs == 1 ? 4 : 2) : 4;
+    const int wantNT = 128, wantPacked = (D == 3 && nrhs != 3) ? 1 : 0;
     for (int i = 0; i < count; ++i)
-        if (v[i].D == D && v[i].nrhs == nrhs && v[i].T == wantT && v[i].NT == wantNT) return i;
+        if (v[i].D == D && v[i].nrhs == nrhs && v[i].T == wantT && v[i].NT == wantNT && v[i].packed == wantPacked)
+            return i;
     for (int i = 0; i < count; ++i)
         if (v[i].D == D && v[i].nrhs == nrhs) return i;
     return -1;
@@ -416,7 +419,12 @@ mfs_status pair_apply(mfs_ctx *ctx, const double *strength, double *out, const d
     }
     PairPlan *plan = nullptr;
     CKS(get_plan(ctx, variant, include_self, &plan));
-    CK(pack_sources(ctx->D, nrhs, ctx->src_pos_d, ctx->rec_pt_d, strength, ctx->sumN, ctx->nrec, ctx->rec_d, st));
+    {
+        int vc = 0;
+        const PairVariant *vv = pair_variants(&vc);
+        CK(pack_sources(ctx->D, nrhs, vv[variant].packed, ctx->src_pos_d, ctx->rec_pt_d, strength, ctx->sumN,
+                        ctx->nrec, ctx->rec_d, st));
+    }
     const PairWork w = work_of(*plan);
     ctx->launches += 2;
     if (w.total_units > 0) {
@@ -463,7 +471,7 @@ mfs_status precond_apply_dev(mfs_ctx *ctx, const double *gamma, double *lambda, 
         if (nb == 0) continue;
         const int ncols = nb * nrhs;
         const ShapeDev &sd = sh.dev;
-        if (ctx->opt.precision == 1) {
+        if (ctx->opt.precision >= 1) {  // FP64 one-body apply (reference and mixed modes)
             CK(gather_rotate(D, gamma, ctx->sumM * D, sh.col_body, sh.col_rhs, ctx->tgt_off_d, ctx->rot64_d, ncols,
                              sd.dM, sh.A, sh.A64, st));
             CK(gemm_rm64(ncols, sd.r, sd.dM, sh.A64, sd.U64, sh.T64, st));
@@ -473,10 +481,14 @@ mfs_status precond_apply_dev(mfs_ctx *ctx, const double *gamma, double *lambda, 
         } else {
             CK(gather_rotate(D, gamma, ctx->sumM * D, sh.col_body, sh.col_rhs, ctx->tgt_off_d, ctx->rot64_d, ncols,
                              sd.dM, sh.A, nullptr, st));
-            CK(gemm_rm(ncols, sd.r, sd.dM, sh.A, sd.U, sh.Tm, st));
-            CK(gemm_rm(ncols, sd.dN, sd.r, sh.Tm, project ? sd.Wp : sd.Wr, sh.Lm, st));
-            CK(scatter_rotate(D, sh.Lm, nullptr, sh.col_body, sh.col_rhs, ctx->src_off_d, ctx->rot_d, ctx->rot64_d,
+            // t = U^T g (FP32 result), then lambda = W t kept in FP64 (split-K, compensated; Eq. pseudo)
+            const int S1 = gemm_splitk_chunks(ncols, sd.r, sd.dM, ctx->sm_count);
+            const int S2 = gemm_splitk_chunks(ncols, sd.dN, sd.r, ctx->sm_count);
+            CK(gemm_splitk(ncols, sd.r, sd.dM, S1, sh.A, sd.U, sh.Pk, sh.Tm, nullptr, st));
+            CK(gemm_splitk(ncols, sd.dN, sd.r, S2, sh.Tm, project ? sd.Wp : sd.Wr, sh.Pk, nullptr, sh.L64, st));
+            CK(scatter_rotate(D, nullptr, sh.L64, sh.col_body, sh.col_rhs, ctx->src_off_d, ctx->rot_d, ctx->rot64_d,
                               ncols, sd.dN, ctx->sumN, lambda, st));
+            ctx->launches += 2;
         }
         ctx->launches += 4;
     }
@@ -873,7 +885,7 @@ static mfs_status setup_impl(mfs_ctx *ctx, mfs_kind kind, const mfs_bodies *bodi
         // apply factors
         bool ok = ctx->alloc(&sd.U, (size_t)m * n) == cudaSuccess && ctx->alloc(&sd.Wp, (size_t)n * n) == cudaSuccess &&
                   ctx->alloc(&sd.Wr, (size_t)n * n) == cudaSuccess;
-        if (ok && ctx->opt.precision == 1)
+        if (ok && ctx->opt.precision >= 1)
             ok = ctx->alloc(&sd.U64, (size_t)m * n) == cudaSuccess &&
                  ctx->alloc(&sd.Wp64, (size_t)n * n) == cudaSuccess &&
                  ctx->alloc(&sd.Wr64, (size_t)n * n) == cudaSuccess;
@@ -905,10 +917,20 @@ static mfs_status setup_impl(mfs_ctx *ctx, mfs_kind kind, const mfs_bodies *bodi
                  ctx->alloc(&sh.A, (size_t)R * nb * m) == cudaSuccess &&
                  ctx->alloc(&sh.Tm, (size_t)R * nb * n) == cudaSuccess &&
                  ctx->alloc(&sh.Lm, (size_t)R * nb * n) == cudaSuccess;
-            if (ok && ctx->opt.precision == 1)
+            if (ok && ctx->opt.precision >= 1)
                 ok = ctx->alloc(&sh.A64, (size_t)R * nb * m) == cudaSuccess &&
-                     ctx->alloc(&sh.T64, (size_t)R * nb * n) == cudaSuccess &&
-                     ctx->alloc(&sh.L64, (size_t)R * nb * n) == cudaSuccess;
+                     ctx->alloc(&sh.T64, (size_t)R * nb * n) == cudaSuccess;
+            if (ok) ok = ctx->alloc(&sh.L64, (size_t)R * nb * n) == cudaSuccess;
+            if (ok) {  // split-K chunk results: the largest S * rows * cols over nrhs = 1..R and both GEMMs
+                size_t need = 0;
+                for (int h = 1; h <= R; ++h) {
+                    const int rows = h * nb;
+                    need = std::max(need, (size_t)gemm_splitk_chunks(rows, n, m, ctx->sm_count) * rows * n);
+                    need = std::max(need, (size_t)gemm_splitk_chunks(rows, n, n, ctx->sm_count) * rows * n);
+                }
+                sh.Pk_count = need;
+                ok = ctx->alloc(&sh.Pk, need) == cudaSuccess;
+            }
             if (!ok) {
                 fail("device allocation for the preconditioner buffers failed", MFS_ERR_OOM);
                 break;
@@ -921,7 +943,7 @@ static mfs_status setup_impl(mfs_ctx *ctx, mfs_kind kind, const mfs_bodies *bodi
     if (status != MFS_OK) return status;
 
     // work buffers
-    const int recf = pair_record_floats(D, R);
+    const int recf = std::max(pair_record_floats(D, R, 0), D == 3 ? pair_record_floats(D, R, 1) : 0);
     CK(ctx->alloc(&ctx->rec_d, (size_t)ctx->nrec * recf));
     CK(cudaMemset(ctx->rec_d, 0, sizeof(float) * (size_t)ctx->nrec * recf));
     CK(ctx->alloc(&ctx->lam_d, (size_t)R * ctx->sumN * D));
@@ -942,6 +964,8 @@ static mfs_status autotune(mfs_ctx *ctx, int nrhs, cudaStream_t st) {
     const PairVariant *v = pair_variants(&count);
     double best = 1e300;
     int best_i = -1;
+    // zero strengths: the timing does not depend on the values
+    CK(cudaMemsetAsync(ctx->lam_d, 0, sizeof(double) * (size_t)nrhs * ctx->sumN * ctx->D, st));
     for (int i = 0; i < count; ++i) {
         if (v[i].D != ctx->D || v[i].nrhs != nrhs) continue;
         if (pair_occupancy(i) <= 0) continue;
@@ -949,6 +973,8 @@ static mfs_status autotune(mfs_ctx *ctx, int nrhs, cudaStream_t st) {
         CKS(get_plan(ctx, i, 0, &plan));
         const PairWork w = work_of(*plan);
         if (w.total_units == 0) return MFS_OK;
+        CK(pack_sources(ctx->D, nrhs, v[i].packed, ctx->src_pos_d, ctx->rec_pt_d, ctx->lam_d, ctx->sumN, ctx->nrec,
+                        ctx->rec_d, st));
         float ms_best = 1e30f;
         for (int rep = 0; rep < 3; ++rep) {
             CK(cudaEventRecord(ctx->ev0, st));
@@ -983,7 +1009,7 @@ mfs_status mfs_setup(mfs_ctx **out, mfs_kind kind, const mfs_bodies *bodies, int
     if (opt) ctx->opt = *opt; else mfs_default_options(&ctx->opt);
     if (ctx->opt.max_rhs < 1 || ctx->opt.max_rhs > 4 || ctx->opt.max_iter < 1 || ctx->opt.restart < 1 ||
         ctx->opt.restart > 1023 || !(ctx->opt.mu > 0.0) || !(ctx->opt.gmres_tol >= 0.0) ||
-        ctx->opt.precision < 0 || ctx->opt.precision > 1 || !(ctx->opt.eps_trunc >= 0.0)) {
+        ctx->opt.precision < 0 || ctx->opt.precision > 2 || !(ctx->opt.eps_trunc >= 0.0)) {
         g_setup_error = "mfs_setup: invalid options";
         return MFS_ERR_INVALID_ARG;
     }
@@ -1000,13 +1026,9 @@ mfs_status mfs_setup(mfs_ctx **out, mfs_kind kind, const mfs_bodies *bodies, int
     }
     cudaStream_t st = (cudaStream_t)stream;
     mfs_status s = setup_impl(ctx.get(), kind, bodies, num_shapes, proxy, colloc, st);
-    if (s == MFS_OK && ctx->opt.autotune && ctx->opt.precision == 0) {
+    if (s == MFS_OK && ctx->opt.autotune && ctx->opt.precision != 1) {
         // tune the single-rhs variant now; other nrhs on first use
-        std::vector<double> zero((size_t)ctx->sumN * ctx->D, 0.0);
-        mfs_ctx *c = ctx.get();
-        cudaError_t e = cudaMemsetAsync(c->lam_d, 0, sizeof(double) * zero.size(), st);
-        if (e == cudaSuccess) e = pack_sources(c->D, 1, c->src_pos_d, c->rec_pt_d, c->lam_d, c->sumN, c->nrec, c->rec_d, st);
-        s = (e == cudaSuccess) ? autotune(c, 1, st) : MFS_ERR_CUDA;
+        s = autotune(ctx.get(), 1, st);
     }
     if (s != MFS_OK) {
         g_setup_error = ctx->last_error;
@@ -1139,7 +1161,7 @@ mfs_status mfs_solve_mobility(mfs_ctx *ctx, const double *F, const double *T, do
     CKS(stage_in(ctx, Ti, T, nb, st));
     CKS(stage_out_alloc(ctx, Uo, U, nb));
     CKS(stage_out_alloc(ctx, Oo, Omega, nb));
-    if (ctx->opt.autotune && ctx->opt.precision == 0 && ctx->best_variant[1][nrhs] < 0) CKS(autotune(ctx, nrhs, st));
+    if (ctx->opt.autotune && ctx->opt.precision != 1 && ctx->best_variant[1][nrhs] < 0) CKS(autotune(ctx, nrhs, st));
     CKS(ensure_gmres(ctx, nrhs));
     begin_call(ctx);
     CK(cudaEventRecord(ctx->ev0, st));
@@ -1179,7 +1201,7 @@ mfs_status mfs_solve_elastance(mfs_ctx *ctx, const double *Q, double *V, int32_t
     Staged Qi, Vo;
     CKS(stage_in(ctx, Qi, Q, nb, st));
     CKS(stage_out_alloc(ctx, Vo, V, nb));
-    if (ctx->opt.autotune && ctx->opt.precision == 0 && ctx->best_variant[0][nrhs] < 0) CKS(autotune(ctx, nrhs, st));
+    if (ctx->opt.autotune && ctx->opt.precision != 1 && ctx->best_variant[0][nrhs] < 0) CKS(autotune(ctx, nrhs, st));
     CKS(ensure_gmres(ctx, nrhs));
     begin_call(ctx);
     CK(cudaEventRecord(ctx->ev0, st));

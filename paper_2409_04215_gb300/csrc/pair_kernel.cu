@@ -12,27 +12,61 @@
 // Accumulation per target: a fresh FP32 partial per block of 32 sources, the
 // block partials summed per source body, and each body sum added into an
 // FP32 (hi, lo) pair by TwoSum; shares of different CTAs are added in FP64.
+//
+// Two compute policies share one persistent, stream-K staging loop:
+//  * Scalar<D, NRHS, T>: T targets per thread, one FP32 instruction per target.
+//  * PackedStokes<NRHS, TP>: 2*TP targets per thread held as TP f32x2 register
+//    pairs; every Stokeslet operation is one packed f32x2 instruction for two
+//    targets (sm_100+ add/mul/fma.rn.f32x2), halving the issue slots the FP32
+//    pipe needs.  Source records then hold every value twice, so one 128-bit
+//    shared-memory load yields two ready operand pairs.
 #include "common.cuh"
 #include "kernels.h"
 
 namespace mfs {
 
-template <int D, int NRHS>
-struct Rec {
-    static constexpr int C = D * NRHS;                 // strength components per source
-    static constexpr int REC = ((3 + C) + 3) / 4 * 4;  // floats per packed source record
-};
+typedef unsigned long long u64;
 
-template <int D, int NRHS, int T, int NT>
-struct PairCfg {
-    static constexpr int C = Rec<D, NRHS>::C;
-    static constexpr int REC = Rec<D, NRHS>::REC;
-    static constexpr int STAGE_BYTES = 16384;
-    static constexpr int STAGE_REC = (STAGE_BYTES / (REC * 4)) / MFS_BS * MFS_BS;
-    static constexpr int STAGE_BLOCKS = STAGE_REC / MFS_BS;
-    static constexpr int TT = NT * T;
-    static constexpr int SMEM = 2 * STAGE_REC * REC * 4;
-};
+// ---------------------------------------------------------------------------
+// f32x2 helpers (inline PTX, sm_100+)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ u64 f2_add(u64 a, u64 b) {
+    u64 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 f2_sub(u64 a, u64 b) {
+    u64 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 f2_mul(u64 a, u64 b) {
+    u64 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 f2_fma(u64 a, u64 b, u64 c) {
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ u64 f2_pack(float lo, float hi) {
+    u64 d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+    return d;
+}
+__device__ __forceinline__ void f2_unpack(u64 v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+// ---------------------------------------------------------------------------
+// Record layouts
+// ---------------------------------------------------------------------------
+// plain:  [x y z s_0 ... s_{C-1}] padded to a multiple of 4 floats
+// packed: every value twice, [x x y y z z s_0 s_0 ...] padded to a multiple of 4 floats
+__host__ __device__ constexpr int rec_floats(int D, int nrhs, bool packed) {
+    return packed ? (2 * (3 + D * nrhs) + 3) / 4 * 4 : ((3 + D * nrhs) + 3) / 4 * 4;
+}
 
 struct Stage {
     int tile;      // -1: no stage
@@ -43,10 +77,10 @@ struct Stage {
     int nblk;      // blocks in this stage
 };
 
-// First tile whose unit range contains u (tiles are contiguous in unit space; empty tiles skipped).
+// Last tile with u0 <= u (tiles are contiguous in unit space; empty tiles come before the tile they abut).
 __device__ __forceinline__ int tile_of_unit(const PairTile *tiles, int ntiles, long long u) {
     int lo = 0, hi = ntiles - 1;
-    while (lo < hi) {  // last tile with u0 <= u
+    while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
         if (tiles[mid].u0 <= u) lo = mid; else hi = mid - 1;
     }
@@ -71,8 +105,8 @@ __device__ __forceinline__ Stage make_stage(const PairTile *tiles, int ntiles, c
     const int b = lo;
     const int blk = (int)(gbl - blk_off[b]);
     const int body_blocks = (int)(blk_off[b + 1] - blk_off[b]);
-    long long seg_end = tl.u1 < uend ? tl.u1 : uend;
-    long long rem = seg_end - u;
+    const long long seg_end = tl.u1 < uend ? tl.u1 : uend;
+    const long long rem = seg_end - u;
     int n = body_blocks - blk;
     if (n > max_blocks) n = max_blocks;
     if (n > rem) n = (int)rem;
@@ -87,101 +121,39 @@ __device__ __forceinline__ Stage make_stage(const PairTile *tiles, int ntiles, c
     return st;
 }
 
+// ---------------------------------------------------------------------------
+// Compute policies
+// ---------------------------------------------------------------------------
 template <int D, int NRHS, int T, int NT>
-__global__ void __launch_bounds__(NT) pair_sum_kernel(PairGeom geo, PairWork work, int *err) {
-    using Cfg = PairCfg<D, NRHS, T, NT>;
-    constexpr int C = Cfg::C, REC = Cfg::REC, SREC = Cfg::STAGE_REC;
-    extern __shared__ __align__(128) float smem[];
-    __shared__ float dcs[2][MFS_MAX_TILE_BODIES][3];
-    __shared__ __align__(8) uint64_t bars[2];
-
-    const int g = blockIdx.x;
-    const long long W = work.total_units;
-    const long long ubeg = (long long)g * W / work.G;
-    const long long uend = (long long)(g + 1) * W / work.G;
-    if (ubeg >= uend) return;
-    const int tid = threadIdx.x;
-    const long long wait_limit = 1ll << 22;
-
-    if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-
-    const PairTile *tiles = work.tiles;
-    Stage cur = make_stage(tiles, work.ntiles, geo.blk_off, geo.src_off, ubeg, uend, Cfg::STAGE_BLOCKS, -1);
-    const int first_tile = cur.tile;
-    if (tid == 0) {
-        mbar_arrive_expect_tx(&bars[0], (uint32_t)(cur.nrec * REC * 4));
-        bulk_g2s(smem, geo.src + (size_t)cur.rec0 * REC, (uint32_t)(cur.nrec * REC * 4), &bars[0]);
-    }
-
-    // per-target state
-    float3 tp[T];      // body-local target position
-    int tb[T];         // target body
+struct Scalar {
+    static constexpr int C = D * NRHS;
+    static constexpr int REC = rec_floats(D, NRHS, false);
+    static constexpr int TPT = T;  // targets per thread
+    static constexpr int PSM = 0;  // all per-target state in registers
+    float3 tp[T];
+    int tb[T];
     float hi[T][C], lo[T][C], bsum[T][C];
-    PairTile tl = tiles[cur.tile];
-    long long seg_begin = ubeg;
 
-    auto load_targets = [&](const PairTile &t_) {
+    __device__ __forceinline__ void init(float *, int) {}
+    __device__ __forceinline__ void set_target(int j, float4 p) {
+        tp[j] = make_float3(p.x, p.y, p.z);
+        tb[j] = __float_as_int(p.w);
+    }
+    __device__ __forceinline__ void reset() {
 #pragma unroll
-        for (int j = 0; j < T; ++j) {
-            int idx = t_.t0 + tid + j * NT;
-            if (idx >= t_.t1) idx = t_.t1 - 1;
-            float4 p = geo.tgt[idx];
-            tp[j] = make_float3(p.x, p.y, p.z);
-            tb[j] = __float_as_int(p.w);
+        for (int j = 0; j < T; ++j)
 #pragma unroll
-            for (int c = 0; c < C; ++c) { hi[j][c] = 0.f; lo[j][c] = 0.f; bsum[j][c] = 0.f; }
-        }
-    };
-    load_targets(tl);
-
-    int si = 0;
-    while (true) {
-        const int buf = si & 1;
-        // next stage (uniform across the CTA)
-        Stage nxt;
-        nxt.tile = -1;
-        const long long unext = cur.u + cur.nblk;
-        if (unext < uend) {
-            int hint = cur.tile;
-            if (unext >= tiles[hint].u1) {  // next non-empty tile
-                ++hint;
-                while (hint < work.ntiles && tiles[hint].u1 <= unext) ++hint;
-                if (hint >= work.ntiles) hint = -1;
-            }
-            nxt = make_stage(tiles, work.ntiles, geo.blk_off, geo.src_off, unext, uend, Cfg::STAGE_BLOCKS, hint);
-            if (tid == 0) {
-                mbar_arrive_expect_tx(&bars[buf ^ 1], (uint32_t)(nxt.nrec * REC * 4));
-                bulk_g2s(smem + (buf ^ 1) * SREC * REC, geo.src + (size_t)nxt.rec0 * REC,
-                         (uint32_t)(nxt.nrec * REC * 4), &bars[buf ^ 1]);
-            }
-        }
-        // centre offsets of the tile's target bodies relative to this stage's source body
-        if (tid < tl.nb * 3) {
-            const int kb = tl.kb0 + tid / 3, c = tid % 3;
-            dcs[buf][tid / 3][c] = (float)(geo.centres[kb * 3 + c] - geo.centres[cur.body * 3 + c]);
-        }
-        const bool ok = mbar_wait_bounded(&bars[buf], (uint32_t)((si >> 1) & 1), err, wait_limit);
-        if (__syncthreads_or(!ok)) {
-            // give the other buffer's copy (if any) a bounded chance to land, then leave
-            if (nxt.tile >= 0) mbar_wait_bounded(&bars[buf ^ 1], (uint32_t)(((si + 1) >> 1) & 1), nullptr, wait_limit);
-            return;
-        }
-
-        // ---- compute this stage ----
-        const float *sb = smem + buf * SREC * REC;
+            for (int c = 0; c < C; ++c) hi[j][c] = lo[j][c] = bsum[j][c] = 0.f;
+    }
+    __device__ __forceinline__ void compute(const float *sb, int nrec, const float (*dc)[3], int kb0) {
         float3 xt[T];
 #pragma unroll
         for (int j = 0; j < T; ++j) {
-            const int r = tb[j] - tl.kb0;
-            xt[j] = make_float3(dcs[buf][r][0] + tp[j].x, dcs[buf][r][1] + tp[j].y, dcs[buf][r][2] + tp[j].z);
+            const int r = tb[j] - kb0;
+            xt[j] = make_float3(dc[r][0] + tp[j].x, dc[r][1] + tp[j].y, dc[r][2] + tp[j].z);
         }
-        for (int s0 = 0; s0 < cur.nrec; s0 += MFS_BS) {
-            const int s1 = min(s0 + MFS_BS, cur.nrec);
+        for (int s0 = 0; s0 < nrec; s0 += MFS_BS) {
+            const int s1 = min(s0 + MFS_BS, nrec);
             float blk[T][C];
 #pragma unroll
             for (int j = 0; j < T; ++j)
@@ -229,30 +201,356 @@ __global__ void __launch_bounds__(NT) pair_sum_kernel(PairGeom geo, PairWork wor
 #pragma unroll
                 for (int c = 0; c < C; ++c) bsum[j][c] += blk[j][c];
         }
-
-        // ---- end of a source body (for this tile): fold into (hi, lo), leaving self pairs out ----
-        const bool body_ends = (nxt.tile < 0) || nxt.tile != cur.tile || nxt.body != cur.body;
-        if (body_ends) {
+    }
+    __device__ __forceinline__ void end_body(int body, bool include_self) {
 #pragma unroll
-            for (int j = 0; j < T; ++j) {
-                const bool keep = work.include_self || (tb[j] != cur.body);
+        for (int j = 0; j < T; ++j) {
+            const bool keep = include_self || (tb[j] != body);
 #pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    float s, e;
-                    two_sum(hi[j][c], keep ? bsum[j][c] : 0.f, s, e);
-                    hi[j][c] = s;
-                    lo[j][c] += e;
-                    bsum[j][c] = 0.f;
-                }
+            for (int c = 0; c < C; ++c) {
+                float s, e;
+                two_sum(hi[j][c], keep ? bsum[j][c] : 0.f, s, e);
+                hi[j][c] = s;
+                lo[j][c] += e;
+                bsum[j][c] = 0.f;
             }
         }
-        // ---- end of this CTA's segment of the tile: write the tile's result ----
-        const bool tile_ends = (nxt.tile < 0) || nxt.tile != cur.tile;
-        if (tile_ends) {
+    }
+    __device__ __forceinline__ float result(int j, int c, float &l) const {
+        l = lo[j][c];
+        return hi[j][c];
+    }
+};
+
+template <int NRHS, int TP, int NT>
+struct PackedStokes {
+    static constexpr int D = 3;
+    static constexpr int C = 3 * NRHS;
+    static constexpr int REC = rec_floats(3, NRHS, true);
+    static constexpr int TPT = 2 * TP;  // targets per thread
+    static constexpr int T = TPT;
+    // Per-target state touched once per stage or per source body (position, body, hi, lo) lives in
+    // shared memory, thread-contiguous ([field][target][thread]: conflict-free), which leaves the
+    // registers to the packed inner loop.
+    static constexpr int FIELDS = 4 + 2 * C;
+    static constexpr int PSM = FIELDS * T;  // floats of shared memory per thread
+    float *sm;
+    int tid;
+    u64 bsum[TP][C];
+
+    __device__ __forceinline__ float &at(int f, int j) const { return sm[(f * T + j) * NT + tid]; }
+    __device__ __forceinline__ void init(float *base, int t) {
+        sm = base;
+        tid = t;
+    }
+    __device__ __forceinline__ void set_target(int j, float4 p) {
+        at(0, j) = p.x;
+        at(1, j) = p.y;
+        at(2, j) = p.z;
+        at(3, j) = p.w;
+    }
+    __device__ __forceinline__ int body(int j) const { return __float_as_int(at(3, j)); }
+    __device__ __forceinline__ void reset() {
+#pragma unroll
+        for (int j = 0; j < T; ++j)
+#pragma unroll
+            for (int c = 0; c < C; ++c) at(4 + c, j) = at(4 + C + c, j) = 0.f;
+#pragma unroll
+        for (int p = 0; p < TP; ++p)
+#pragma unroll
+            for (int c = 0; c < C; ++c) bsum[p][c] = 0ull;
+    }
+    __device__ __forceinline__ void compute(const float *sb, int nrec, const float (*dc)[3], int kb0) {
+        u64 xt[TP][3];
+#pragma unroll
+        for (int p = 0; p < TP; ++p) {
+            const int j0 = 2 * p, j1 = 2 * p + 1;
+            const int r0 = body(j0) - kb0, r1 = body(j1) - kb0;
+            xt[p][0] = f2_pack(dc[r0][0] + at(0, j0), dc[r1][0] + at(0, j1));
+            xt[p][1] = f2_pack(dc[r0][1] + at(1, j0), dc[r1][1] + at(1, j1));
+            xt[p][2] = f2_pack(dc[r0][2] + at(2, j0), dc[r1][2] + at(2, j1));
+        }
+        for (int s0 = 0; s0 < nrec; s0 += MFS_BS) {
+            const int s1 = min(s0 + MFS_BS, nrec);
+            u64 blk[TP][C];
+#pragma unroll
+            for (int p = 0; p < TP; ++p)
+#pragma unroll
+                for (int c = 0; c < C; ++c) blk[p][c] = 0ull;
+            for (int s = s0; s < s1; s += 4) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    u64 rec[REC / 2];
+#pragma unroll
+                    for (int v = 0; v < REC / 4; ++v) {
+                        const ulonglong2 f = reinterpret_cast<const ulonglong2 *>(sb + (s + q) * REC)[v];
+                        rec[2 * v] = f.x;
+                        rec[2 * v + 1] = f.y;
+                    }
+#pragma unroll
+                    for (int p = 0; p < TP; ++p) {
+                        const u64 dx = f2_sub(xt[p][0], rec[0]);
+                        const u64 dy = f2_sub(xt[p][1], rec[1]);
+                        const u64 dz = f2_sub(xt[p][2], rec[2]);
+                        const u64 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
+                        float a, b;
+                        f2_unpack(r2, a, b);
+                        const u64 ri = f2_pack(rsqrtf(a), rsqrtf(b));
+                        const u64 ri2 = f2_mul(ri, ri);
+#pragma unroll
+                        for (int h = 0; h < NRHS; ++h) {
+                            const u64 lx = rec[3 + 3 * h], ly = rec[4 + 3 * h], lz = rec[5 + 3 * h];
+                            const u64 dot = f2_fma(dx, lx, f2_fma(dy, ly, f2_mul(dz, lz)));
+                            const u64 sc = f2_mul(dot, ri2);
+                            blk[p][3 * h + 0] = f2_fma(f2_fma(dx, sc, lx), ri, blk[p][3 * h + 0]);
+                            blk[p][3 * h + 1] = f2_fma(f2_fma(dy, sc, ly), ri, blk[p][3 * h + 1]);
+                            blk[p][3 * h + 2] = f2_fma(f2_fma(dz, sc, lz), ri, blk[p][3 * h + 2]);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < TP; ++p)
+#pragma unroll
+                for (int c = 0; c < C; ++c) bsum[p][c] = f2_add(bsum[p][c], blk[p][c]);
+        }
+    }
+    __device__ __forceinline__ void end_body(int src_body, bool include_self) {
+#pragma unroll
+        for (int p = 0; p < TP; ++p) {
+            const int j0 = 2 * p, j1 = 2 * p + 1;
+            const bool k0 = include_self || (body(j0) != src_body);
+            const bool k1 = include_self || (body(j1) != src_body);
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                float v0, v1, s, e;
+                f2_unpack(bsum[p][c], v0, v1);
+                two_sum(at(4 + c, j0), k0 ? v0 : 0.f, s, e);
+                at(4 + c, j0) = s;
+                at(4 + C + c, j0) += e;
+                two_sum(at(4 + c, j1), k1 ? v1 : 0.f, s, e);
+                at(4 + c, j1) = s;
+                at(4 + C + c, j1) += e;
+                bsum[p][c] = 0ull;
+            }
+        }
+    }
+    __device__ __forceinline__ float result(int j, int c, float &l) const {
+        l = at(4 + C + c, j);
+        return at(4 + c, j);
+    }
+};
+
+// The same packed Stokeslet arithmetic with all per-target state in registers (more registers,
+// more freedom for the compiler to interleave sources; the autotuner picks per geometry).
+template <int NRHS, int TP, int NT>
+struct PackedStokesReg {
+    static constexpr int D = 3;
+    static constexpr int C = 3 * NRHS;
+    static constexpr int REC = rec_floats(3, NRHS, true);
+    static constexpr int TPT = 2 * TP;
+    static constexpr int T = TPT;
+    static constexpr int PSM = 0;
+    float3 tp[T];
+    int tb[T];
+    float hi[T][C], lo[T][C];
+    u64 bsum[TP][C];
+
+    __device__ __forceinline__ void init(float *, int) {}
+    __device__ __forceinline__ void set_target(int j, float4 p) {
+        tp[j] = make_float3(p.x, p.y, p.z);
+        tb[j] = __float_as_int(p.w);
+    }
+    __device__ __forceinline__ void reset() {
+#pragma unroll
+        for (int j = 0; j < T; ++j)
+#pragma unroll
+            for (int c = 0; c < C; ++c) hi[j][c] = lo[j][c] = 0.f;
+#pragma unroll
+        for (int p = 0; p < TP; ++p)
+#pragma unroll
+            for (int c = 0; c < C; ++c) bsum[p][c] = 0ull;
+    }
+    __device__ __forceinline__ void compute(const float *sb, int nrec, const float (*dc)[3], int kb0) {
+        u64 xt[TP][3];
+#pragma unroll
+        for (int p = 0; p < TP; ++p) {
+            const int r0 = tb[2 * p] - kb0, r1 = tb[2 * p + 1] - kb0;
+            xt[p][0] = f2_pack(dc[r0][0] + tp[2 * p].x, dc[r1][0] + tp[2 * p + 1].x);
+            xt[p][1] = f2_pack(dc[r0][1] + tp[2 * p].y, dc[r1][1] + tp[2 * p + 1].y);
+            xt[p][2] = f2_pack(dc[r0][2] + tp[2 * p].z, dc[r1][2] + tp[2 * p + 1].z);
+        }
+        for (int s0 = 0; s0 < nrec; s0 += MFS_BS) {
+            const int s1 = min(s0 + MFS_BS, nrec);
+            u64 blk[TP][C];
+#pragma unroll
+            for (int p = 0; p < TP; ++p)
+#pragma unroll
+                for (int c = 0; c < C; ++c) blk[p][c] = 0ull;
+            for (int s = s0; s < s1; s += 4) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    u64 rec[REC / 2];
+#pragma unroll
+                    for (int v = 0; v < REC / 4; ++v) {
+                        const ulonglong2 f = reinterpret_cast<const ulonglong2 *>(sb + (s + q) * REC)[v];
+                        rec[2 * v] = f.x;
+                        rec[2 * v + 1] = f.y;
+                    }
+#pragma unroll
+                    for (int p = 0; p < TP; ++p) {
+                        const u64 dx = f2_sub(xt[p][0], rec[0]);
+                        const u64 dy = f2_sub(xt[p][1], rec[1]);
+                        const u64 dz = f2_sub(xt[p][2], rec[2]);
+                        const u64 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
+                        float a, b;
+                        f2_unpack(r2, a, b);
+                        const u64 ri = f2_pack(rsqrtf(a), rsqrtf(b));
+                        const u64 ri2 = f2_mul(ri, ri);
+#pragma unroll
+                        for (int h = 0; h < NRHS; ++h) {
+                            const u64 lx = rec[3 + 3 * h], ly = rec[4 + 3 * h], lz = rec[5 + 3 * h];
+                            const u64 dot = f2_fma(dx, lx, f2_fma(dy, ly, f2_mul(dz, lz)));
+                            const u64 sc = f2_mul(dot, ri2);
+                            blk[p][3 * h + 0] = f2_fma(f2_fma(dx, sc, lx), ri, blk[p][3 * h + 0]);
+                            blk[p][3 * h + 1] = f2_fma(f2_fma(dy, sc, ly), ri, blk[p][3 * h + 1]);
+                            blk[p][3 * h + 2] = f2_fma(f2_fma(dz, sc, lz), ri, blk[p][3 * h + 2]);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < TP; ++p)
+#pragma unroll
+                for (int c = 0; c < C; ++c) bsum[p][c] = f2_add(bsum[p][c], blk[p][c]);
+        }
+    }
+    __device__ __forceinline__ void end_body(int body, bool include_self) {
+#pragma unroll
+        for (int p = 0; p < TP; ++p) {
+            const bool k0 = include_self || (tb[2 * p] != body);
+            const bool k1 = include_self || (tb[2 * p + 1] != body);
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                float v0, v1, s, e;
+                f2_unpack(bsum[p][c], v0, v1);
+                two_sum(hi[2 * p][c], k0 ? v0 : 0.f, s, e);
+                hi[2 * p][c] = s;
+                lo[2 * p][c] += e;
+                two_sum(hi[2 * p + 1][c], k1 ? v1 : 0.f, s, e);
+                hi[2 * p + 1][c] = s;
+                lo[2 * p + 1][c] += e;
+                bsum[p][c] = 0ull;
+            }
+        }
+    }
+    __device__ __forceinline__ float result(int j, int c, float &l) const {
+        l = lo[j][c];
+        return hi[j][c];
+    }
+};
+
+// ---------------------------------------------------------------------------
+// The persistent stream-K kernel
+// ---------------------------------------------------------------------------
+template <class Pol, int NT>
+struct StageCfg {
+    static constexpr int REC = Pol::REC;
+    // 16 KB stages; 12 KB when the policy keeps per-target state in shared memory (occupancy)
+    static constexpr int STAGE_BYTES = Pol::PSM ? 12288 : 16384;
+    static constexpr int STAGE_REC = (STAGE_BYTES / (REC * 4)) / MFS_BS * MFS_BS;
+    static constexpr int STAGE_BLOCKS = STAGE_REC / MFS_BS;
+    static constexpr int SMEM = 2 * STAGE_REC * REC * 4 + Pol::PSM * NT * 4;
+};
+
+template <class Pol, int NT>
+__global__ void __launch_bounds__(NT) pair_sum_kernel(PairGeom geo, PairWork work, int *err) {
+    using Cfg = StageCfg<Pol, NT>;
+    constexpr int REC = Cfg::REC, SREC = Cfg::STAGE_REC, C = Pol::C, TPT = Pol::TPT;
+    extern __shared__ __align__(128) float smem[];
+    __shared__ float dcs[2][MFS_MAX_TILE_BODIES][3];
+    __shared__ __align__(8) uint64_t bars[2];
+
+    const int g = blockIdx.x;
+    const long long W = work.total_units;
+    const long long ubeg = (long long)g * W / work.G;
+    const long long uend = (long long)(g + 1) * W / work.G;
+    if (ubeg >= uend) return;
+    const int tid = threadIdx.x;
+    const long long wait_limit = 1ll << 22;
+
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    const PairTile *tiles = work.tiles;
+    Stage cur = make_stage(tiles, work.ntiles, geo.blk_off, geo.src_off, ubeg, uend, Cfg::STAGE_BLOCKS, -1);
+    const int first_tile = cur.tile;
+    if (tid == 0) {
+        mbar_arrive_expect_tx(&bars[0], (uint32_t)(cur.nrec * REC * 4));
+        bulk_g2s(smem, geo.src + (size_t)cur.rec0 * REC, (uint32_t)(cur.nrec * REC * 4), &bars[0]);
+    }
+
+    Pol pol;
+    pol.init(smem + 2 * SREC * REC, tid);
+    PairTile tl = tiles[cur.tile];
+    long long seg_begin = ubeg;
+    auto load_targets = [&](const PairTile &t_) {
+#pragma unroll
+        for (int j = 0; j < TPT; ++j) {
+            int idx = t_.t0 + tid + j * NT;
+            if (idx >= t_.t1) idx = t_.t1 - 1;
+            pol.set_target(j, geo.tgt[idx]);
+        }
+        pol.reset();
+    };
+    load_targets(tl);
+
+    int si = 0;
+    while (true) {
+        const int buf = si & 1;
+        Stage nxt;
+        nxt.tile = -1;
+        const long long unext = cur.u + cur.nblk;
+        if (unext < uend) {
+            int hint = cur.tile;
+            if (unext >= tiles[hint].u1) {  // next non-empty tile
+                ++hint;
+                while (hint < work.ntiles && tiles[hint].u1 <= unext) ++hint;
+                if (hint >= work.ntiles) hint = -1;
+            }
+            nxt = make_stage(tiles, work.ntiles, geo.blk_off, geo.src_off, unext, uend, Cfg::STAGE_BLOCKS, hint);
+            if (tid == 0) {
+                mbar_arrive_expect_tx(&bars[buf ^ 1], (uint32_t)(nxt.nrec * REC * 4));
+                bulk_g2s(smem + (buf ^ 1) * SREC * REC, geo.src + (size_t)nxt.rec0 * REC,
+                         (uint32_t)(nxt.nrec * REC * 4), &bars[buf ^ 1]);
+            }
+        }
+        // centre offsets of the tile's target bodies relative to this stage's source body
+        if (tid < tl.nb * 3) {
+            const int kb = tl.kb0 + tid / 3, c = tid % 3;
+            dcs[buf][tid / 3][c] = (float)(geo.centres[kb * 3 + c] - geo.centres[cur.body * 3 + c]);
+        }
+        const bool ok = mbar_wait_bounded(&bars[buf], (uint32_t)((si >> 1) & 1), err, wait_limit);
+        if (__syncthreads_or(!ok)) {
+            // give the other buffer's copy (if any) a bounded chance to land, then leave
+            if (nxt.tile >= 0) mbar_wait_bounded(&bars[buf ^ 1], (uint32_t)(((si + 1) >> 1) & 1), nullptr, wait_limit);
+            return;
+        }
+
+        pol.compute(smem + buf * SREC * REC, cur.nrec, dcs[buf], tl.kb0);
+
+        // end of a source body (for this tile): fold into (hi, lo), leaving self pairs out
+        if ((nxt.tile < 0) || nxt.tile != cur.tile || nxt.body != cur.body) pol.end_body(cur.body, work.include_self);
+        // end of this CTA's segment of the tile: write the tile's result
+        if ((nxt.tile < 0) || nxt.tile != cur.tile) {
             const long long seg_end = cur.u + cur.nblk;
             const bool whole = (seg_begin == tl.u0) && (seg_end == tl.u1);
 #pragma unroll
-            for (int j = 0; j < T; ++j) {
+            for (int j = 0; j < TPT; ++j) {
                 const int idx = tl.t0 + tid + j * NT;
                 if (idx < tl.t1) {
                     double *dst;
@@ -263,7 +561,11 @@ __global__ void __launch_bounds__(NT) pair_sum_kernel(PairGeom geo, PairWork wor
                         dst = work.partial + ((size_t)(g * 2 + slot) * work.tile_targets + (idx - tl.t0)) * C;
                     }
 #pragma unroll
-                    for (int c = 0; c < C; ++c) dst[c] = (double)hi[j][c] + (double)lo[j][c];
+                    for (int c = 0; c < C; ++c) {
+                        float l;
+                        const float h = pol.result(j, c, l);
+                        dst[c] = (double)h + (double)l;
+                    }
                 }
             }
             if (nxt.tile >= 0) {
@@ -319,40 +621,50 @@ __global__ void pair_epilogue_kernel(PairWork work, const double *base, double b
 // Pack proxy strengths (FP64 [nrhs][sum_N][D], body-local rotated positions) into FP32 records.
 // Padding records (beyond N_k in each body) sit at the body centre with zero strength, which
 // contributes exactly zero to every target off that centre.
-template <int D, int NRHS>
-__global__ void pack_sources_kernel(const float4 *src_pos, const int *src_body_of_rec, const int *src_pt_of_rec,
-                                    const double *strength, int nsrc, int nrec, float *records) {
-    constexpr int C = D * NRHS, REC = Rec<D, NRHS>::REC;
+template <int D, int NRHS, bool PACKED>
+__global__ void pack_sources_kernel(const float4 *src_pos, const int *src_pt_of_rec, const double *strength, int nsrc,
+                                    int nrec, float *records) {
+    constexpr int NV = 3 + D * NRHS, REC = rec_floats(D, NRHS, PACKED);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nrec) return;
-    float r[REC];
+    float v[NV];
 #pragma unroll
-    for (int c = 0; c < REC; ++c) r[c] = 0.f;
+    for (int c = 0; c < NV; ++c) v[c] = 0.f;
     const int p = src_pt_of_rec[i];
     if (p >= 0) {
         const float4 y = src_pos[p];
-        r[0] = y.x;
-        r[1] = y.y;
-        r[2] = y.z;
+        v[0] = y.x;
+        v[1] = y.y;
+        v[2] = y.z;
 #pragma unroll
         for (int h = 0; h < NRHS; ++h)
 #pragma unroll
-            for (int d = 0; d < D; ++d) r[3 + h * D + d] = (float)strength[((size_t)h * nsrc + p) * D + d];
+            for (int d = 0; d < D; ++d) v[3 + h * D + d] = (float)strength[((size_t)h * nsrc + p) * D + d];
+    }
+    float r[REC];
+#pragma unroll
+    for (int c = 0; c < REC; ++c) r[c] = 0.f;
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+        if (PACKED) {
+            r[2 * c] = v[c];
+            r[2 * c + 1] = v[c];
+        } else {
+            r[c] = v[c];
+        }
     }
     float4 *o = reinterpret_cast<float4 *>(records + (size_t)i * REC);
 #pragma unroll
-    for (int v = 0; v < REC / 4; ++v) o[v] = make_float4(r[4 * v], r[4 * v + 1], r[4 * v + 2], r[4 * v + 3]);
-    (void)src_body_of_rec;
-    (void)C;
+    for (int q = 0; q < REC / 4; ++q) o[q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
 }
 
 // ---------------------------------------------------------------------------
 // Host side: variant table
 // ---------------------------------------------------------------------------
-template <int D, int NRHS, int T, int NT>
+template <class Pol, int NT>
 static cudaError_t launch_variant(const PairGeom &geo, const PairWork &work, int *err, cudaStream_t st) {
-    using Cfg = PairCfg<D, NRHS, T, NT>;
-    auto kern = pair_sum_kernel<D, NRHS, T, NT>;
+    using Cfg = StageCfg<Pol, NT>;
+    auto kern = pair_sum_kernel<Pol, NT>;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
@@ -363,36 +675,49 @@ static cudaError_t launch_variant(const PairGeom &geo, const PairWork &work, int
     return cudaGetLastError();
 }
 
-template <int D, int NRHS, int T, int NT>
+template <class Pol, int NT>
 static int occupancy_variant() {
-    using Cfg = PairCfg<D, NRHS, T, NT>;
-    auto kern = pair_sum_kernel<D, NRHS, T, NT>;
+    using Cfg = StageCfg<Pol, NT>;
+    auto kern = pair_sum_kernel<Pol, NT>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
     int blocks = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, NT, Cfg::SMEM) != cudaSuccess) return 0;
     return blocks;
 }
 
-#define MFS_VARIANTS(X)      \
-    X(3, 1, 4, 128)          \
-    X(3, 1, 2, 128)          \
-    X(3, 1, 4, 256)          \
-    X(3, 1, 2, 256)          \
-    X(3, 2, 2, 128)          \
-    X(3, 3, 2, 128)          \
-    X(3, 4, 2, 128)          \
-    X(3, 4, 1, 128)          \
-    X(1, 1, 4, 128)          \
-    X(1, 1, 8, 128)          \
-    X(1, 1, 4, 256)          \
-    X(1, 2, 4, 128)          \
-    X(1, 3, 4, 128)          \
-    X(1, 4, 4, 128)
+// Scalar S(D, nrhs, targets per thread, threads); packed Stokes P(nrhs, target pairs per thread, threads)
+#define MFS_VARIANTS(S, P)  \
+    S(3, 1, 4, 128)         \
+    S(3, 1, 2, 128)         \
+    S(3, 1, 4, 256)         \
+    S(3, 1, 2, 256)         \
+    S(3, 2, 2, 128)         \
+    S(3, 3, 2, 128)         \
+    S(3, 4, 2, 128)         \
+    S(3, 4, 1, 128)         \
+    S(1, 1, 4, 128)         \
+    S(1, 1, 8, 128)         \
+    S(1, 1, 4, 256)         \
+    S(1, 2, 4, 128)         \
+    S(1, 3, 4, 128)         \
+    S(1, 4, 4, 128)         \
+    P(PackedStokesReg, 1, 1, 128) \
+    P(PackedStokesReg, 1, 2, 128) \
+    P(PackedStokesReg, 1, 1, 256) \
+    P(PackedStokesReg, 2, 1, 128) \
+    P(PackedStokesReg, 4, 1, 128) \
+    P(PackedStokes, 1, 2, 128)    \
+    P(PackedStokes, 1, 2, 256)    \
+    P(PackedStokes, 1, 3, 128)    \
+    P(PackedStokes, 2, 1, 128)    \
+    P(PackedStokes, 4, 1, 128)
 
 static const PairVariant kVariants[] = {
-#define X(D_, R_, T_, N_) {D_, R_, T_, N_, N_ * T_},
-    MFS_VARIANTS(X)
-#undef X
+#define S(D_, R_, T_, N_) {D_, R_, T_, N_, N_ * T_, 0},
+#define P(POL_, R_, TP_, N_) {3, R_, 2 * TP_, N_, N_ * 2 * TP_, 1},
+    MFS_VARIANTS(S, P)
+#undef S
+#undef P
 };
 
 const PairVariant *pair_variants(int *count) {
@@ -400,23 +725,29 @@ const PairVariant *pair_variants(int *count) {
     return kVariants;
 }
 
-int pair_record_floats(int D, int nrhs) { return ((3 + D * nrhs) + 3) / 4 * 4; }
+int pair_record_floats(int D, int nrhs, int packed) { return rec_floats(D, nrhs, packed != 0); }
 
 int pair_occupancy(int vi) {
     int i = 0;
-#define X(D_, R_, T_, N_) \
-    if (vi == i++) return occupancy_variant<D_, R_, T_, N_>();
-    MFS_VARIANTS(X)
-#undef X
+#define S(D_, R_, T_, N_) \
+    if (vi == i++) return occupancy_variant<Scalar<D_, R_, T_, N_>, N_>();
+#define P(POL_, R_, TP_, N_) \
+    if (vi == i++) return occupancy_variant<POL_<R_, TP_, N_>, N_>();
+    MFS_VARIANTS(S, P)
+#undef S
+#undef P
     return 0;
 }
 
 cudaError_t pair_launch(int vi, const PairGeom &geo, const PairWork &work, int *err, cudaStream_t st) {
     int i = 0;
-#define X(D_, R_, T_, N_) \
-    if (vi == i++) return launch_variant<D_, R_, T_, N_>(geo, work, err, st);
-    MFS_VARIANTS(X)
-#undef X
+#define S(D_, R_, T_, N_) \
+    if (vi == i++) return launch_variant<Scalar<D_, R_, T_, N_>, N_>(geo, work, err, st);
+#define P(POL_, R_, TP_, N_) \
+    if (vi == i++) return launch_variant<POL_<R_, TP_, N_>, N_>(geo, work, err, st);
+    MFS_VARIANTS(S, P)
+#undef S
+#undef P
     return cudaErrorInvalidValue;
 }
 
@@ -434,18 +765,20 @@ cudaError_t pair_epilogue(int D, int nrhs, const PairWork &work, const double *b
     return cudaErrorInvalidValue;
 }
 
-cudaError_t pack_sources(int D, int nrhs, const float4 *src_pos, const int *src_pt_of_rec, const double *strength,
-                         int nsrc, int nrec, float *records, cudaStream_t st) {
+cudaError_t pack_sources(int D, int nrhs, int packed, const float4 *src_pos, const int *src_pt_of_rec,
+                         const double *strength, int nsrc, int nrec, float *records, cudaStream_t st) {
     const int threads = 256, blocks = (nrec + threads - 1) / threads;
     if (nrec == 0) return cudaSuccess;
-#define P(D_, R_)                                                                                        \
-    if (D == D_ && nrhs == R_) {                                                                         \
-        pack_sources_kernel<D_, R_><<<blocks, threads, 0, st>>>(src_pos, nullptr, src_pt_of_rec, strength, nsrc, \
-                                                                 nrec, records);                         \
-        return cudaGetLastError();                                                                       \
+#define PK(D_, R_, PA_)                                                                                 \
+    if (D == D_ && nrhs == R_ && (packed != 0) == PA_) {                                                \
+        pack_sources_kernel<D_, R_, PA_><<<blocks, threads, 0, st>>>(src_pos, src_pt_of_rec, strength, nsrc, nrec, \
+                                                                     records);                         \
+        return cudaGetLastError();                                                                      \
     }
-    P(3, 1) P(3, 2) P(3, 3) P(3, 4) P(1, 1) P(1, 2) P(1, 3) P(1, 4)
-#undef P
+    PK(3, 1, false) PK(3, 2, false) PK(3, 3, false) PK(3, 4, false)
+    PK(1, 1, false) PK(1, 2, false) PK(1, 3, false) PK(1, 4, false)
+    PK(3, 1, true) PK(3, 2, true) PK(3, 3, true) PK(3, 4, true)
+#undef PK
     return cudaErrorInvalidValue;
 }
 

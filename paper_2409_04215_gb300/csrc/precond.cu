@@ -8,6 +8,8 @@
 //  * rotation of congruent bodies: S_L^(k)+ = R_N V Sigma^+ U^T R_M^T (Remark congruent, Eq. Krot),
 //  * completion strengths lambda_0 = K_N (K_N^T K_N)^{-1} [f; t] (Eq. lambda01, lambda02) and
 //    alpha_0 = q/N 1 (Eq. al0); extraction U = -K_N^T lambda (Eq. getU), phi = -mean(alpha) (Eq. vkal).
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -347,6 +349,106 @@ __global__ void __launch_bounds__(256) gemm_rm_kernel(int m, int n, int k, const
             const int gm = m0 + ty * 4 + i, gn = n0 + tx * 4 + j;
             if (gm < m && gn < n) C[(size_t)gm * n + gn] = acc[i][j];
         }
+}
+
+// Split-K FP32 GEMM with compensated accumulation: CTA (x, y, z) computes the 64x64 tile (y, x)
+// over the z-th chunk of k.  Each 16-deep k slice is summed in FP32 from zero and folded into a
+// per-output (hi, lo) pair by TwoSum, so the rounding of a long sequential FP32 sum (which, over
+// k = 3600, limits the solved velocities to ~2e-5) never builds up; the chunk results are
+// written in FP64 and added in FP64 by splitk_reduce_kernel.
+__global__ void __launch_bounds__(256) gemm_splitk_kernel(int m, int n, int k, int kchunk,
+                                                          const float *__restrict__ A,
+                                                          const float *__restrict__ B, double *__restrict__ P) {
+    constexpr int BM = 64, BN = 64, BK = 16;
+    __shared__ float As[BK][BM + 4];
+    __shared__ float Bs[BK][BN + 4];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int kb = blockIdx.z * kchunk, ke = min(k, kb + kchunk);
+    float hi[4][4], lo[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) hi[i][j] = lo[i][j] = 0.f;
+    for (int k0 = kb; k0 < ke; k0 += BK) {
+        for (int e = threadIdx.x; e < BM * BK; e += 256) {
+            const int r = e / BK, c = e % BK;
+            const int gm = m0 + r, gk = k0 + c;
+            As[c][r] = (gm < m && gk < ke) ? A[(size_t)gm * k + gk] : 0.f;
+        }
+        for (int e = threadIdx.x; e < BK * BN; e += 256) {
+            const int r = e / BN, c = e % BN;
+            const int gk = k0 + r, gn = n0 + c;
+            Bs[r][c] = (gk < ke && gn < n) ? B[(size_t)gk * n + gn] : 0.f;
+        }
+        __syncthreads();
+        float s[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) s[i][j] = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) s[i][j] = fmaf(a[i], b[j], s[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float t, e;
+                two_sum(hi[i][j], s[i][j], t, e);
+                hi[i][j] = t;
+                lo[i][j] += e;
+            }
+        __syncthreads();
+    }
+    double *Pz = P + (size_t)blockIdx.z * m * n;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gm = m0 + ty * 4 + i, gn = n0 + tx * 4 + j;
+            if (gm < m && gn < n) Pz[(size_t)gm * n + gn] = (double)hi[i][j] + (double)lo[i][j];
+        }
+}
+
+// C = sum_z P[z] in FP64, stored as FP32 (C32) or FP64 (C64).
+__global__ void splitk_reduce_kernel(int S, size_t mn, const double *__restrict__ P, float *C32, double *C64) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < mn; i += (size_t)gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int z = 0; z < S; ++z) v += P[(size_t)z * mn + i];
+        if (C64) C64[i] = v;
+        else C32[i] = (float)v;
+    }
+}
+
+int gemm_splitk_chunks(int m, int n, int k, int sm_count) {
+    const long long tiles = (long long)((n + 63) / 64) * ((m + 63) / 64);
+    long long s = (4LL * sm_count + tiles - 1) / tiles;  // about four resident waves of CTAs
+    const long long smax = (k + 63) / 64;                // at least 64 k per chunk
+    if (s > smax) s = smax;
+    if (s > 32) s = 32;
+    return (int)(s < 1 ? 1 : s);
+}
+
+cudaError_t gemm_splitk(int m, int n, int k, int S, const float *A, const float *B, double *P, float *C32,
+                        double *C64, cudaStream_t st) {
+    if (m == 0 || n == 0) return cudaSuccess;
+    const int kchunk = ((k + S - 1) / S + 15) / 16 * 16;
+    const int Sz = (k + kchunk - 1) / kchunk;
+    dim3 grid((n + 63) / 64, (m + 63) / 64, Sz);
+    gemm_splitk_kernel<<<grid, 256, 0, st>>>(m, n, k, kchunk, A, B, P);
+    const size_t mn = (size_t)m * n;
+    splitk_reduce_kernel<<<(unsigned)std::min<size_t>((mn + 255) / 256, 4096), 256, 0, st>>>(Sz, mn, P, C32, C64);
+    return cudaGetLastError();
 }
 
 cudaError_t gemm_rm(int m, int n, int k, const float *A, const float *B, float *C, cudaStream_t st) {
