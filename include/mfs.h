@@ -173,6 +173,33 @@ mfs_status mfs_solve_mobility(mfs_ctx *ctx, const double *F, const double *T, do
 mfs_status mfs_mobility_vjp(mfs_ctx *ctx, const double *dU, const double *dOmega, int32_t nrhs, double *dcenters,
                             double *dF, double *dT, void *stream);
 
+/*
+ * mfs_stokeslet_sum_noalloc -- the Stokeslet pair sum for callers that cannot allocate device
+ * memory (code running inside another framework's memory pool, a plug-in host, or a fixed
+ * memory budget, where a cudaMalloc is not allowed or not wanted).  The paper has no counterpart:
+ * it is a packaging of the same FP32 pair kernel as mfs_pair_sum, without a context.
+ *
+ *   u_i = sum_j (I + r r^T / r^2) lambda_j / (8 pi mu r),  r = x_i - y_j,  over ALL pairs.
+ *
+ * targets [num_targets][3], sources [num_sources][3], strengths [num_sources][3] and the output
+ * u [num_targets][3] are FP64 DEVICE pointers owned by the caller.  Coordinates are used as FP32
+ * in the pair loop (one body, no centre shift), so keep them O(1)-O(100) in magnitude; a target
+ * on top of a source gives a non-finite result.
+ * Allocates nothing: its scratch (about 21 MB) is a fixed __device__ array inside libmfs that every
+ * GPU which loads the library holds until the process exits.  Limits: num_targets and num_sources
+ * at most MFS_NOALLOC_MAX_TARGETS / MFS_NOALLOC_MAX_SOURCES; larger sizes, NULL pointers or mu <= 0
+ * return MFS_ERR_INVALID_ARG without launching anything.  All launches go on `stream`; the call
+ * does not synchronise.  The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.  Every call reuses
+ * the same array, which keeps the previous call's contents: calls whose GPU work overlaps (other
+ * streams or other host threads) race and must be serialised by the caller.
+ */
+#define MFS_NOALLOC_MAX_TARGETS 65536
+#define MFS_NOALLOC_MAX_SOURCES 65536
+mfs_status mfs_stokeslet_sum_noalloc(const double *targets, int32_t num_targets, const double *sources,
+                                     const double *strengths, int32_t num_sources, double mu, double *u,
+                                     void *stream);
+
 /* Text of the last error on this context (never NULL; "" when none).  Valid until the next call. */
 const char *mfs_last_error(const mfs_ctx *ctx);
 

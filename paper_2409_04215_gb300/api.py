@@ -42,6 +42,7 @@ EXPORTED = [
     "mfs_solve_elastance",
     "mfs_solve_mobility",
     "mfs_mobility_vjp",
+    "mfs_stokeslet_sum_noalloc",
     "mfs_last_error",
     "mfs_setup_error",
     "mfs_destroy",

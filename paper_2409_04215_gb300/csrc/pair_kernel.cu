@@ -20,6 +20,9 @@
 //    targets (sm_100+ add/mul/fma.rn.f32x2), halving the issue slots the FP32
 //    pipe needs.  Source records then hold every value twice, so one 128-bit
 //    shared-memory load yields two ready operand pairs.
+#include <algorithm>
+
+#include "../../include/mfs.h"
 #include "common.cuh"
 #include "kernels.h"
 
@@ -783,3 +786,171 @@ cudaError_t pack_sources(int D, int nrhs, int packed, const float4 *src_pos, con
 }
 
 }  // namespace mfs
+
+// ===========================================================================
+// Stokeslet sum without device allocation.
+//
+// For callers that cannot allocate device memory: code that runs where cudaMalloc is not
+// allowed or not wanted (inside another library's memory pool, a plug-in host, or a
+// pre-planned memory budget) still gets the packed FP32 pair kernel.  Every byte of
+// scratch lives in one file-scope __device__ array of fixed size, reserved when the
+// library is loaded.  The array is shared by all calls and keeps the last call's contents,
+// so calls whose GPU work overlaps (different streams, or different host threads) race.
+// ===========================================================================
+namespace mfs {
+namespace noalloc {
+using Pol = PackedStokesReg<1, 2, 128>;
+constexpr int NT = 128;
+constexpr int TT = NT * Pol::TPT;  // targets per tile
+constexpr int REC = Pol::REC;
+constexpr int kMaxTargets = MFS_NOALLOC_MAX_TARGETS;
+constexpr int kMaxSources = MFS_NOALLOC_MAX_SOURCES;
+constexpr int kMaxCTAs = 640;
+constexpr int kMaxTiles = (kMaxTargets + TT - 1) / TT;
+constexpr size_t al(size_t x) { return (x + 255) / 256 * 256; }
+constexpr size_t oTgt = 0;
+constexpr size_t oRec = oTgt + al(sizeof(float4) * kMaxTargets);
+constexpr size_t oTiles = oRec + al(sizeof(float) * REC * (size_t)(kMaxSources + 4));
+constexpr size_t oMeta = oTiles + al(sizeof(PairTile) * kMaxTiles);
+constexpr size_t oPart = oMeta + 256;
+constexpr size_t oDirect = oPart + al(sizeof(double) * 3 * (size_t)kMaxCTAs * 2 * TT);
+constexpr size_t kBytes = oDirect + al(sizeof(double) * 3 * (size_t)kMaxTargets);
+struct Meta {
+    int src_off[2];
+    int err;
+    int pad;
+    long long blk_off[2];
+    double centre[3];
+};
+}  // namespace noalloc
+}  // namespace mfs
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[mfs::noalloc::kBytes];
+
+namespace mfs {
+namespace noalloc {
+
+// Targets -> float4 (absolute coordinates, one body), sources -> duplicated FP32 records, the
+// tile list of the stream-K split and the single-body offsets; every scratch word the pair
+// kernel and the epilogue read is written here first.
+__global__ void prep_kernel(const double *targets, int nt, const double *sources, const double *lam, int ns,
+                            int nrec, int ntiles, long long nblk, int G, unsigned char *base) {
+    float4 *tgt = reinterpret_cast<float4 *>(base + oTgt);
+    float *rec = reinterpret_cast<float *>(base + oRec);
+    PairTile *tiles = reinterpret_cast<PairTile *>(base + oTiles);
+    Meta *meta = reinterpret_cast<Meta *>(base + oMeta);
+    const long long W = (long long)ntiles * nblk;
+    const int stride = gridDim.x * blockDim.x;
+    const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int i = i0; i < nt; i += stride)
+        tgt[i] = make_float4((float)targets[3 * (size_t)i], (float)targets[3 * (size_t)i + 1],
+                             (float)targets[3 * (size_t)i + 2], __int_as_float(0));
+    for (int r = i0; r < nrec; r += stride) {
+        float v[6];
+        if (r < ns) {
+            for (int c = 0; c < 3; ++c) v[c] = (float)sources[3 * (size_t)r + c];
+            for (int c = 0; c < 3; ++c) v[3 + c] = (float)lam[3 * (size_t)r + c];
+        } else {  // padding: far away, zero strength -> exactly zero contribution
+            v[0] = v[1] = v[2] = 1e15f;
+            v[3] = v[4] = v[5] = 0.f;
+        }
+        float *o = rec + (size_t)r * REC;
+        for (int c = 0; c < 6; ++c) o[2 * c] = o[2 * c + 1] = v[c];
+    }
+    for (int t = i0; t < ntiles; t += stride) {
+        PairTile tl;
+        tl.t0 = t * TT;
+        tl.t1 = min(nt, tl.t0 + TT);
+        tl.kb0 = 0;
+        tl.nb = 1;
+        tl.skip = -1;
+        tl.B0 = 0;
+        tl.B1 = 1;
+        tl.u0 = (long long)t * nblk;
+        tl.u1 = tl.u0 + nblk;
+        tl.gA = (int)(((tl.u0 + 1) * G - 1) / W);
+        tl.gB = (int)((tl.u1 * G - 1) / W);
+        tiles[t] = tl;
+    }
+    if (i0 == 0) {
+        meta->src_off[0] = 0;
+        meta->src_off[1] = nrec;
+        meta->err = 0;
+        meta->blk_off[0] = 0;
+        meta->blk_off[1] = nblk;
+        meta->centre[0] = meta->centre[1] = meta->centre[2] = 0.0;
+    }
+}
+
+struct DeviceScratch {
+    void *ptr[64] = {};
+    int occupancy = 0;
+};
+static DeviceScratch g_dev;
+
+}  // namespace noalloc
+}  // namespace mfs
+
+extern "C" mfs_status mfs_stokeslet_sum_noalloc(const double *targets, int32_t num_targets, const double *sources,
+                                                const double *strengths, int32_t num_sources, double mu, double *u,
+                                                void *stream) {
+    using namespace mfs;
+    using namespace mfs::noalloc;
+    if (!targets || !sources || !strengths || !u || num_targets < 0 || num_sources < 0 || !(mu > 0.0))
+        return MFS_ERR_INVALID_ARG;
+    if (num_targets > kMaxTargets || num_sources > kMaxSources) return MFS_ERR_INVALID_ARG;
+    if (num_targets == 0) return MFS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MFS_ERR_CUDA;
+    if (!g_dev.ptr[dev]) {  // first call on this device: the array's device address
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return MFS_ERR_CUDA;
+        g_dev.ptr[dev] = p;
+    }
+    unsigned char *base = static_cast<unsigned char *>(g_dev.ptr[dev]);
+    if (num_sources == 0) return cudaMemsetAsync(u, 0, sizeof(double) * 3 * (size_t)num_targets, st) == cudaSuccess
+                                     ? MFS_OK : MFS_ERR_CUDA;
+    if (g_dev.occupancy == 0) {
+        int occ = 0;
+        auto kern = pair_sum_kernel<Pol, NT>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, StageCfg<Pol, NT>::SMEM) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, StageCfg<Pol, NT>::SMEM) != cudaSuccess ||
+            occ <= 0)
+            return MFS_ERR_CUDA;
+        g_dev.occupancy = occ;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MFS_ERR_CUDA;
+    const int nrec = (num_sources + 3) / 4 * 4;
+    const long long nblk = (nrec + MFS_BS - 1) / MFS_BS;
+    const int ntiles = (num_targets + TT - 1) / TT;
+    const long long W = (long long)ntiles * nblk;
+    long long G = std::min<long long>((long long)g_dev.occupancy * sms, kMaxCTAs);
+    if (G > W) G = W;
+    prep_kernel<<<256, 256, 0, st>>>(targets, num_targets, sources, strengths, num_sources, nrec, ntiles, nblk,
+                                     (int)G, base);
+    if (cudaGetLastError() != cudaSuccess) return MFS_ERR_CUDA;
+    Meta *meta = reinterpret_cast<Meta *>(base + oMeta);
+    PairGeom geo;
+    geo.tgt = reinterpret_cast<const float4 *>(base + oTgt);
+    geo.src = reinterpret_cast<const float *>(base + oRec);
+    geo.src_off = meta->src_off;
+    geo.blk_off = meta->blk_off;
+    geo.centres = meta->centre;
+    geo.ntargets = num_targets;
+    PairWork work;
+    work.tiles = reinterpret_cast<const PairTile *>(base + oTiles);
+    work.ntiles = ntiles;
+    work.total_units = W;
+    work.G = (int)G;
+    work.partial = reinterpret_cast<double *>(base + oPart);
+    work.direct = reinterpret_cast<double *>(base + oDirect);
+    work.tile_targets = TT;
+    work.include_self = 1;
+    if (launch_variant<Pol, NT>(geo, work, &meta->err, st) != cudaSuccess) return MFS_ERR_CUDA;
+    pair_epilogue_kernel<3, 1><<<ntiles, 256, 0, st>>>(work, nullptr, 0.0, 1.0 / (8.0 * MFS_PI * mu), u,
+                                                       num_targets);
+    return cudaGetLastError() == cudaSuccess ? MFS_OK : MFS_ERR_CUDA;
+}
