@@ -15,6 +15,7 @@
  */
 #include <math.h>
 #include <stddef.h>
+#include <stdlib.h>
 
 static const double PI_ORACLE = 3.14159265358979323846;
 
@@ -82,33 +83,41 @@ void oracle_stokeslet_center_grad(long nt, const double *x, const int *tgroup, c
                                   double *grad /* nbody x 3, accumulated */)
 {
     const double c = 1.0 / (8.0 * PI_ORACLE * visc);
-    for (long i = 0; i < nt; ++i) {
-        double gx = 0.0, gy = 0.0, gz = 0.0;
-        double wx = w[3 * i + 0], wy = w[3 * i + 1], wz = w[3 * i + 2];
-        for (long j = 0; j < ns; ++j) {
-            if (sgroup[j] != tgroup[i]) continue;
-            if (sbody[j] == tbody[i]) continue;
-            double rx = x[3 * i + 0] - y[3 * j + 0];
-            double ry = x[3 * i + 1] - y[3 * j + 1];
-            double rz = x[3 * i + 2] - y[3 * j + 2];
-            double r2 = rx * rx + ry * ry + rz * rz;
-            double r = sqrt(r2);
-            double r3 = r2 * r, r5 = r3 * r2;
-            double mx = muv[3 * j + 0], my = muv[3 * j + 1], mz = muv[3 * j + 2];
-            double wm = wx * mx + wy * my + wz * mz;
-            double wr = wx * rx + wy * ry + wz * rz;
-            double rm = rx * mx + ry * my + rz * mz;
-            double dx = -wm * rx / r3 + (wx * rm + mx * wr) / r3 - 3.0 * wr * rm * rx / r5;
-            double dy = -wm * ry / r3 + (wy * rm + my * wr) / r3 - 3.0 * wr * rm * ry / r5;
-            double dz = -wm * rz / r3 + (wz * rm + mz * wr) / r3 - 3.0 * wr * rm * rz / r5;
-            gx += dx; gy += dy; gz += dz;
-            /* source body moves the other way */
-            grad[3 * sbody[j] + 0] -= c * dx;
-            grad[3 * sbody[j] + 1] -= c * dy;
-            grad[3 * sbody[j] + 2] -= c * dz;
+#pragma omp parallel
+    {
+        double *g = (double *)calloc((size_t)3 * nbody, sizeof(double));
+#pragma omp for schedule(dynamic, 64)
+        for (long i = 0; i < nt; ++i) {
+            double gx = 0.0, gy = 0.0, gz = 0.0;
+            double wx = w[3 * i + 0], wy = w[3 * i + 1], wz = w[3 * i + 2];
+            for (long j = 0; j < ns; ++j) {
+                if (sgroup[j] != tgroup[i]) continue;
+                if (sbody[j] == tbody[i]) continue;
+                double rx = x[3 * i + 0] - y[3 * j + 0];
+                double ry = x[3 * i + 1] - y[3 * j + 1];
+                double rz = x[3 * i + 2] - y[3 * j + 2];
+                double r2 = rx * rx + ry * ry + rz * rz;
+                double r = sqrt(r2);
+                double r3 = r2 * r, r5 = r3 * r2;
+                double mx = muv[3 * j + 0], my = muv[3 * j + 1], mz = muv[3 * j + 2];
+                double wm = wx * mx + wy * my + wz * mz;
+                double wr = wx * rx + wy * ry + wz * rz;
+                double rm = rx * mx + ry * my + rz * mz;
+                double dx = -wm * rx / r3 + (wx * rm + mx * wr) / r3 - 3.0 * wr * rm * rx / r5;
+                double dy = -wm * ry / r3 + (wy * rm + my * wr) / r3 - 3.0 * wr * rm * ry / r5;
+                double dz = -wm * rz / r3 + (wz * rm + mz * wr) / r3 - 3.0 * wr * rm * rz / r5;
+                gx += dx; gy += dy; gz += dz;
+                /* the source body moves the other way */
+                g[3 * sbody[j] + 0] -= c * dx;
+                g[3 * sbody[j] + 1] -= c * dy;
+                g[3 * sbody[j] + 2] -= c * dz;
+            }
+            g[3 * tbody[i] + 0] += c * gx;
+            g[3 * tbody[i] + 1] += c * gy;
+            g[3 * tbody[i] + 2] += c * gz;
         }
-        grad[3 * tbody[i] + 0] += c * gx;
-        grad[3 * tbody[i] + 1] += c * gy;
-        grad[3 * tbody[i] + 2] += c * gz;
+#pragma omp critical
+        for (long q = 0; q < 3 * (long)nbody; ++q) grad[q] += g[q];
+        free(g);
     }
 }

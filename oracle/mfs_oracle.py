@@ -405,6 +405,86 @@ class Problem:
         g = self.split(bodies, gamma)
         return np.concatenate([self.pinv_apply(k, gk, project) for k, gk in zip(bodies, g)])
 
+    # -- adjoint (the paper gives none; derived from Eq. 2esysprec, Eq. stou0, Eq. getU) --------
+    #
+    # U = E gamma with E = -K_N^T S_L^+ (block diagonal, independent of the centres), and
+    # A(c) gamma = b(c) = -u_0(c).  For a loss L(U):  g_gamma = E^T dL/dU,  A^T w = g_gamma,
+    # dL = w^T (db - dA gamma) = -sum_{k != k'} w_k^T dS^(kk') mu_k',  mu = lambda_0 + (I - L) S_L^+ gamma,
+    # where only the off-diagonal blocks depend on the centres (through r = c_k - c_k' + ...).
+    def pinv_apply_T(self, k: int, x: np.ndarray, project: bool) -> np.ndarray:
+        """(S_L^(k)+)^T x = R_M U Sigma^+ V^T R_N^T x, after (I - L^(k)) when project (L is symmetric)."""
+        f = self.shape_of(k)
+        if project:
+            x = self.project(k, x)
+        t = f.sigma_pinv * (f.Vt @ self.rotate_points(k, x, transpose=True))
+        return self.rotate_points(k, f.U @ t, transpose=False)
+
+    def pair_sum_T(self, bodies: Sequence[int], w: Sequence[np.ndarray], include_self: bool) -> List[np.ndarray]:
+        """z^(k') = sum_k S^(kk')^T w^(k) at the proxy points (G is symmetric and even in r)."""
+        d = self.d
+        x = np.concatenate([self.Y[k] for k in bodies])
+        tg = np.concatenate([np.full(self.Y[k].shape[0], self.group[k], np.int32) for k in bodies])
+        tb = np.concatenate([np.full(self.Y[k].shape[0], k, np.int32) for k in bodies])
+        y = np.concatenate([self.X[k] for k in bodies])
+        sg = np.concatenate([np.full(self.X[k].shape[0], self.group[k], np.int32) for k in bodies])
+        sb = np.concatenate([np.full(self.X[k].shape[0], k, np.int32) for k in bodies])
+        s = np.concatenate([np.asarray(v).reshape(-1, d) if d == 3 else np.asarray(v) for v in w])
+        out = direct_sum(self.kind, x, tg, tb, y, sg, sb, s, include_self, self.mu)
+        res, o = [], 0
+        for k in bodies:
+            n = self.Y[k].shape[0]
+            res.append(out[o:o + n].reshape(-1).copy())
+            o += n
+        return res
+
+    def matvec_T(self, bodies: Sequence[int], w: np.ndarray) -> np.ndarray:
+        """A^T w = w + [((I - L^(k')) S_L^(k')+)^T sum_{k != k'} S^(kk')^T w^(k)]_k'."""
+        z = self.pair_sum_T(bodies, self.split(bodies, w), include_self=False)
+        return w + np.concatenate([self.pinv_apply_T(k, zk, project=True) for k, zk in zip(bodies, z)])
+
+    def mobility_vjp(self, F: np.ndarray, T: np.ndarray, dU: np.ndarray, dW: np.ndarray, tol: float = 1e-13,
+                     max_iter: int = 300):
+        """dL/dc [P][3], dL/dF, dL/dT [P][3] for the cotangents dU = dL/dU, dW = dL/dOmega."""
+        grad_c = np.zeros((self.P, 3))
+        gF = np.zeros((self.P, 3))
+        gT = np.zeros((self.P, 3))
+        for s in range(self.wl.num_suspensions):
+            bodies = list(self.suspension_bodies(s))
+            lam0 = [self.lambda0(k, F[k], T[k]) for k in bodies]
+            u0 = np.concatenate(self.pair_sum(bodies, lam0, include_self=True))
+            gamma = gmres(lambda v: self.matvec(bodies, v), -u0, tol, max_iter).x
+            # g_gamma = E^T dL/dU = -(S_L^+)^T K_N [dU; dW]
+            gg = np.concatenate([-self.pinv_apply_T(k, self.K_N(k) @ np.concatenate([dU[k], dW[k]]), False)
+                                 for k in bodies])
+            w = gmres(lambda v: self.matvec_T(bodies, v), gg, tol, max_iter).x
+            mu = [l0 + self.pinv_apply(k, gk, project=True)
+                  for k, l0, gk in zip(bodies, lam0, self.split(bodies, gamma))]
+            grad_c[bodies] -= self.centre_gradient(bodies, self.split(bodies, w), mu)[bodies]
+            # dL/dlambda_0 = -S_full^T w (all pairs, Eq. stou0); lambda_0 = K_N G^-1 [f; t]
+            z = self.pair_sum_T(bodies, self.split(bodies, w), include_self=True)
+            for k, zk in zip(bodies, z):
+                KN = self.K_N(k)
+                g6 = -np.linalg.solve(KN.T @ KN, KN.T @ zk)
+                gF[k], gT[k] = g6[:3], g6[3:]
+        return grad_c, gF, gT
+
+    def centre_gradient(self, bodies: Sequence[int], w: Sequence[np.ndarray], mu: Sequence[np.ndarray]):
+        """sum over off-diagonal pairs of d/dr [w_i^T G(r_ij) mu_j], +1 to the target body, -1 to the source body."""
+        x = np.concatenate([self.X[k] for k in bodies])
+        tg = np.concatenate([np.full(self.X[k].shape[0], self.group[k], np.int32) for k in bodies])
+        tb = np.concatenate([np.full(self.X[k].shape[0], k, np.int32) for k in bodies])
+        y = np.concatenate([self.Y[k] for k in bodies])
+        sg = np.concatenate([np.full(self.Y[k].shape[0], self.group[k], np.int32) for k in bodies])
+        sb = np.concatenate([np.full(self.Y[k].shape[0], k, np.int32) for k in bodies])
+        ww = np.ascontiguousarray(np.concatenate([np.asarray(v).reshape(-1, 3) for v in w]))
+        mm = np.ascontiguousarray(np.concatenate([np.asarray(v).reshape(-1, 3) for v in mu]))
+        g = np.zeros((self.P, 3))
+        lib = _clib()
+        xs, ys = np.ascontiguousarray(x), np.ascontiguousarray(y)
+        lib.oracle_stokeslet_center_grad(x.shape[0], _dp(xs), _ip(tg), _ip(tb), _dp(ww), y.shape[0], _dp(ys),
+                                         _ip(sg), _ip(sb), _dp(mm), float(self.mu), int(self.P), _dp(g))
+        return g
+
     # -- completion (Sec. 3.1, Sec. 3.2) -------------------------------------
     def lambda0(self, k: int, f: np.ndarray, t: np.ndarray) -> np.ndarray:
         """lambda_0 = K_N (K_N^T K_N)^{-1} [f; t]  (Eq. lambda01, lambda02)."""
