@@ -6,6 +6,6 @@ names; importing it does not load the library -- the first call does, and fails
 loudly when the library is missing.
 """
 
-from .api import MFS, MFSError, SolveInfo, Options, load_library  # noqa: F401
+from .api import MFS, MFSError, SolveInfo, Options, load_library, mobility  # noqa: F401
 
-__all__ = ["MFS", "MFSError", "SolveInfo", "Options", "load_library"]
+__all__ = ["MFS", "MFSError", "SolveInfo", "Options", "load_library", "mobility"]

@@ -345,3 +345,26 @@ class MFS:
 def _info(i: _Info, rc: int) -> SolveInfo:
     return SolveInfo(i.iters, bool(i.converged), i.matvecs, i.lanes, i.rel_residual, i.ms_setup, i.ms_solve,
                      i.ms_pairs, i.pairs, i.launches, i.pair_launches, rc)
+
+
+def mobility(mfs: "MFS", centres, F, T):
+    """(U, Omega) = mobility(centres, F, T) as a differentiable torch operation.
+
+    Forward: mfs_update_centers + mfs_solve_mobility; backward: mfs_mobility_vjp (gradients with
+    respect to the body centres, the forces and the torques).  F, T: [nrhs][P][3].
+    """
+    torch = _torch()
+
+    class _Mobility(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx_, c, f, t):
+            mfs.update_centers(c.detach())
+            U, W, _ = mfs.solve_mobility(f.detach(), t.detach())
+            return U, W
+
+        @staticmethod
+        def backward(ctx_, gU, gW):
+            dc, dF, dT = mfs.mobility_vjp(gU.contiguous(), gW.contiguous(), want_force_grads=True)
+            return dc.to(gU.device), dF.to(gU.device), dT.to(gU.device)
+
+    return _Mobility.apply(centres, F, T)

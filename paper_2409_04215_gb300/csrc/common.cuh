@@ -42,6 +42,7 @@ struct PairGeom {
     const long long *blk_off;  // [P+1] global block offset of each body (blocks of MFS_BS records)
     const double *centres;     // [P][3]
     int ntargets;
+    const float *tgt_w = nullptr;  // gradient kernel only: target strengths w, FP32 [nrhs][ntargets][3]
 };
 
 struct PairWork {
@@ -53,6 +54,7 @@ struct PairWork {
     double *direct;            // [ntargets][C]
     int tile_targets;
     int include_self;          // 1: self pairs included (right-hand side u_0)
+    double *src_grad = nullptr;  // gradient kernel only: per source body sums, FP64 [P][3] (atomic adds)
 };
 
 // ---------------------------------------------------------------------------

@@ -10,6 +10,7 @@ namespace mfs {
 struct PairVariant {
     int D, nrhs, T, NT, tile_targets;
     int packed;  // 1: f32x2 Stokes policy with duplicated source records
+    int grad;    // 1: centre-gradient kernel of the adjoint (not a pair sum)
 };
 const PairVariant *pair_variants(int *count);
 int pair_occupancy(int variant);  // resident CTAs per SM
@@ -54,7 +55,7 @@ cudaError_t gemm_rm(int m, int n, int k, const float *A, const float *B, float *
 // into C32 (FP32) or C64 (FP64).  S from gemm_splitk_chunks; P must hold S*m*n doubles.
 int gemm_splitk_chunks(int m, int n, int k, int sm_count);
 cudaError_t gemm_splitk(int m, int n, int k, int S, const float *A, const float *B, double *P, float *C32,
-                        double *C64, cudaStream_t st);
+                        double *C64, cudaStream_t st, bool trans_b = false);  // trans_b: B stored [n][k]
 cudaError_t gemm_rm64(int m, int n, int k, const double *A, const double *B, double *C, cudaStream_t st);
 // Scatter: lambda (FP64 [nrhs][sum_N][D]) at the columns' bodies = R_k * Lcol (rotate back).
 cudaError_t scatter_rotate(int D, const float *L, const double *L64, const int *col_body, const int *col_rhs,

@@ -48,6 +48,7 @@ struct ShapeHost {
     float *A = nullptr, *Tm = nullptr, *Lm = nullptr;  // GEMM buffers
     double *Pk = nullptr;                              // split-K chunk results
     size_t Pk_count = 0;
+    double *O64 = nullptr, *PkT = nullptr;             // adjoint: transposed-apply output and chunks
     double *A64 = nullptr, *T64 = nullptr, *L64 = nullptr;
     ShapeDev dev{};
 };
@@ -82,7 +83,7 @@ struct mfs_ctx {
     float *rec_d = nullptr;      // packed source records (max_rhs)
     double *lam_d = nullptr;     // [max_rhs][sumN][D]
     double *raw_d = nullptr;     // FP64 reference pair sums [max_rhs][sumM][D]
-    std::map<std::pair<int, int>, PairPlan> plans;  // (variant, include_self)
+    std::map<int, PairPlan> plans;  // key: variant * 4 + include_self * 2 + transposed
     int best_variant[2][5] = {{-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}};  // [D==3][nrhs]
 
     // GMRES
@@ -94,8 +95,25 @@ struct mfs_ctx {
     int *done_h = nullptr;
 
     // solution kept for the adjoint
-    double *last_gamma = nullptr;
+    double *keep_gamma = nullptr;  // [max_rhs][sum_M][3] solution gamma of the last mobility solve
+    double *keep_lam0 = nullptr;   // [max_rhs][sum_N][3] its completion strengths lambda_0
     int last_nrhs = 0;
+
+    // adjoint: the transposed direction (proxy targets, collocation sources)
+    bool trans_ready = false;
+    std::vector<int> src_body, recT_off;
+    std::vector<long long> blkT_off;
+    int nrecT = 0;
+    float4 *tgtT_pos_d = nullptr;
+    float *recT_d = nullptr;
+    int *recT_off_d = nullptr, *rec_ptT_d = nullptr;
+    long long *blkT_off_d = nullptr;
+    double *tmpM_d = nullptr;     // [max_rhs][sum_M][3]
+    double *gradT_d = nullptr;    // [sum_M][3] per-target gradient sums
+    double *src_grad_d = nullptr; // [P][3]
+    double *six_d = nullptr;      // [max_rhs][P][6] scratch for -K_N^T z
+    float *w32_d = nullptr;       // [max_rhs][sum_M][3] FP32 adjoint strengths
+    double *eye6_d = nullptr;     // [nshapes][36] identity (K_N [u; w] expansion)
 
     int sm_count = 0;
     std::string last_error;
@@ -273,32 +291,40 @@ int default_variant(int D, int nrhs) {
     const int wantT = (D == 3) ? (nrhs == 1 ? 4 : 2) : 4;
     const int wantNT = 128, wantPacked = (D == 3 && nrhs != 3) ? 1 : 0;
     for (int i = 0; i < count; ++i)
-        if (v[i].D == D && v[i].nrhs == nrhs && v[i].T == wantT && v[i].NT == wantNT && v[i].packed == wantPacked)
+        if (!v[i].grad && v[i].D == D && v[i].nrhs == nrhs && v[i].T == wantT && v[i].NT == wantNT &&
+            v[i].packed == wantPacked)
             return i;
     for (int i = 0; i < count; ++i)
-        if (v[i].D == D && v[i].nrhs == nrhs) return i;
+        if (!v[i].grad && v[i].D == D && v[i].nrhs == nrhs) return i;
     return -1;
 }
 
-mfs_status build_plan(mfs_ctx *ctx, int variant, int include_self, PairPlan &plan) {
+// Tiles and CTA shares for one pair-kernel variant.  transposed = 0: collocation targets, proxy
+// sources (the matvec and u_0); transposed = 1: proxy targets, collocation sources (the adjoint's
+// S^T sums).
+mfs_status build_plan(mfs_ctx *ctx, int variant, int include_self, int transposed, PairPlan &plan) {
     int count = 0;
     const PairVariant *vv = pair_variants(&count);
     const PairVariant &v = vv[variant];
     const int TT = v.tile_targets;
-    const int C = v.D * v.nrhs;
+    const int C = v.grad ? 3 : v.D * v.nrhs;
+    const std::vector<int> &toff = transposed ? ctx->src_off : ctx->tgt_off;
+    const std::vector<int> &tbody = transposed ? ctx->src_body : ctx->tgt_body;
+    const std::vector<long long> &boff = transposed ? ctx->blkT_off : ctx->blk_off;
+    const int ntargets = transposed ? ctx->sumN : ctx->sumM;
     std::vector<PairTile> tiles;
     long long units = 0;
     for (int s = 0; s < ctx->S; ++s) {
         const int B0 = ctx->body_off[s], B1 = ctx->body_off[s + 1];
-        const int t_end = ctx->tgt_off[B1];
-        int t = ctx->tgt_off[B0];
+        const int t_end = toff[B1];
+        int t = toff[B0];
         while (t < t_end) {
             int t1 = std::min(t + TT, t_end);
-            const int kb0 = ctx->tgt_body[t];
-            int kb1 = ctx->tgt_body[t1 - 1];
+            const int kb0 = tbody[t];
+            int kb1 = tbody[t1 - 1];
             if (kb1 - kb0 + 1 > MFS_MAX_TILE_BODIES) {
                 kb1 = kb0 + MFS_MAX_TILE_BODIES - 1;
-                t1 = ctx->tgt_off[kb1 + 1];
+                t1 = toff[kb1 + 1];
             }
             PairTile tl;
             tl.t0 = t;
@@ -310,7 +336,7 @@ mfs_status build_plan(mfs_ctx *ctx, int variant, int include_self, PairPlan &pla
             tl.B1 = B1;
             long long u = 0;
             for (int b = B0; b < B1; ++b)
-                if (b != tl.skip) u += ctx->blk_off[b + 1] - ctx->blk_off[b];
+                if (b != tl.skip) u += boff[b + 1] - boff[b];
             tl.u0 = units;
             tl.u1 = units + u;
             units += u;
@@ -344,18 +370,18 @@ mfs_status build_plan(mfs_ctx *ctx, int variant, int include_self, PairPlan &pla
     CK(ctx->alloc(&plan.tiles, tiles.size()));
     CK(cudaMemcpy(plan.tiles, tiles.data(), sizeof(PairTile) * tiles.size(), cudaMemcpyHostToDevice));
     plan.partial_bytes = sizeof(double) * (size_t)G * 2 * TT * C;
-    plan.direct_bytes = sizeof(double) * (size_t)ctx->sumM * C;
+    plan.direct_bytes = sizeof(double) * (size_t)ntargets * C;
     CK(ctx->alloc(&plan.partial, (size_t)G * 2 * TT * C));
-    CK(ctx->alloc(&plan.direct, (size_t)ctx->sumM * C));
+    CK(ctx->alloc(&plan.direct, (size_t)ntargets * C));
     return MFS_OK;
 }
 
-mfs_status get_plan(mfs_ctx *ctx, int variant, int include_self, PairPlan **out) {
-    auto key = std::make_pair(variant, include_self);
+mfs_status get_plan(mfs_ctx *ctx, int variant, int include_self, PairPlan **out, int transposed = 0) {
+    const int key = variant * 4 + include_self * 2 + transposed;
     auto it = ctx->plans.find(key);
     if (it == ctx->plans.end()) {
         PairPlan p;
-        CKS(build_plan(ctx, variant, include_self, p));
+        CKS(build_plan(ctx, variant, include_self, transposed, p));
         it = ctx->plans.emplace(key, p).first;
     }
     *out = &it->second;
@@ -559,19 +585,151 @@ mfs_status ensure_gmres(mfs_ctx *ctx, int nrhs) {
     return MFS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint (transposed) operators
+// ---------------------------------------------------------------------------
+// The transposed geometry: proxy points as targets (float4 with body bits), collocation points
+// as sources packed into records with their own padded offsets; plus adjoint scratch.
+mfs_status ensure_transposed(mfs_ctx *ctx) {
+    if (ctx->trans_ready) return MFS_OK;
+    const int P = ctx->P, R = ctx->opt.max_rhs;
+    ctx->src_body.resize(ctx->sumN);
+    for (int k = 0; k < P; ++k)
+        for (int q = ctx->src_off[k]; q < ctx->src_off[k + 1]; ++q) ctx->src_body[q] = k;
+    ctx->recT_off.assign(P + 1, 0);
+    ctx->blkT_off.assign(P + 1, 0);
+    for (int k = 0; k < P; ++k) {
+        const int mpad = (ctx->tgt_off[k + 1] - ctx->tgt_off[k] + 3) / 4 * 4;
+        ctx->recT_off[k + 1] = ctx->recT_off[k] + mpad;
+        ctx->blkT_off[k + 1] = ctx->blkT_off[k] + (mpad + MFS_BS - 1) / MFS_BS;
+    }
+    ctx->nrecT = ctx->recT_off[P];
+    std::vector<int> rec_pt(ctx->nrecT, -1);
+    for (int k = 0; k < P; ++k)
+        for (int i = 0; i < ctx->tgt_off[k + 1] - ctx->tgt_off[k]; ++i) rec_pt[ctx->recT_off[k] + i] = ctx->tgt_off[k] + i;
+    // proxy targets: rotated local coordinates with the body id in w
+    std::vector<float4> tp(ctx->sumN);
+    std::vector<float> s4(4 * (size_t)ctx->sumN);
+    CK(cudaMemcpy(tp.data(), ctx->src_pos_d, sizeof(float4) * ctx->sumN, cudaMemcpyDeviceToHost));
+    for (int q = 0; q < ctx->sumN; ++q) {
+        int k = ctx->src_body[q];
+        float kb;
+        std::memcpy(&kb, &k, sizeof(float));
+        tp[q].w = kb;
+    }
+    const int recf = std::max(pair_record_floats(3, R, 0), pair_record_floats(3, R, 1));
+    CK(ctx->alloc(&ctx->tgtT_pos_d, ctx->sumN));
+    CK(ctx->alloc(&ctx->recT_d, (size_t)ctx->nrecT * recf));
+    CK(ctx->alloc(&ctx->recT_off_d, P + 1));
+    CK(ctx->alloc(&ctx->rec_ptT_d, ctx->nrecT));
+    CK(ctx->alloc(&ctx->blkT_off_d, P + 1));
+    CK(ctx->alloc(&ctx->tmpM_d, (size_t)R * ctx->sumM * 3));
+    CK(ctx->alloc(&ctx->gradT_d, (size_t)ctx->sumM * 3));
+    CK(ctx->alloc(&ctx->src_grad_d, (size_t)P * 3));
+    CK(ctx->alloc(&ctx->six_d, (size_t)R * P * 6));
+    CK(ctx->alloc(&ctx->w32_d, (size_t)R * ctx->sumM * 3));
+    CK(ctx->alloc(&ctx->eye6_d, (size_t)ctx->nshapes * 36));
+    CK(cudaMemcpy(ctx->tgtT_pos_d, tp.data(), sizeof(float4) * ctx->sumN, cudaMemcpyHostToDevice));
+    CK(cudaMemset(ctx->recT_d, 0, sizeof(float) * (size_t)ctx->nrecT * recf));
+    CK(cudaMemcpy(ctx->recT_off_d, ctx->recT_off.data(), sizeof(int) * (P + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->rec_ptT_d, rec_pt.data(), sizeof(int) * ctx->nrecT, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->blkT_off_d, ctx->blkT_off.data(), sizeof(long long) * (P + 1), cudaMemcpyHostToDevice));
+    std::vector<double> eye(36 * (size_t)ctx->nshapes, 0.0);
+    for (int s = 0; s < ctx->nshapes; ++s)
+        for (int i = 0; i < 6; ++i) eye[36 * s + 7 * i] = 1.0;
+    CK(cudaMemcpy(ctx->eye6_d, eye.data(), sizeof(double) * eye.size(), cudaMemcpyHostToDevice));
+    for (auto &sh : ctx->shapes) {  // transposed-apply buffers
+        const int nb = (int)sh.bodies.size();
+        if (nb == 0) continue;
+        const int m = sh.dev.dM, n = sh.dev.dN;
+        size_t need = 0;
+        for (int h = 1; h <= R; ++h) {
+            const int rows = h * nb;
+            need = std::max(need, (size_t)gemm_splitk_chunks(rows, n, n, ctx->sm_count) * rows * n);
+            need = std::max(need, (size_t)gemm_splitk_chunks(rows, m, n, ctx->sm_count) * rows * m);
+        }
+        CK(ctx->alloc(&sh.PkT, need));
+        CK(ctx->alloc(&sh.O64, (size_t)R * nb * m));
+    }
+    ctx->trans_ready = true;
+    return MFS_OK;
+}
+
+// z^(k') = sum_k S^(kk')^T w^(k) at the proxy points (the Stokeslet is symmetric and even in r),
+// self pairs included or not.  w: [nrhs][sum_M][3], z: [nrhs][sum_N][3], both FP64 on the device.
+mfs_status pair_apply_T(mfs_ctx *ctx, const double *w, double *z, int nrhs, int include_self, cudaStream_t st) {
+    const int variant = ctx->best_variant[1][nrhs] >= 0 ? ctx->best_variant[1][nrhs] : default_variant(3, nrhs);
+    int vc = 0;
+    const PairVariant *vv = pair_variants(&vc);
+    PairPlan *plan = nullptr;
+    CKS(get_plan(ctx, variant, include_self, &plan, 1));
+    CK(pack_sources(3, nrhs, vv[variant].packed, ctx->tgt_pos_d, ctx->rec_ptT_d, w, ctx->sumM, ctx->nrecT,
+                    ctx->recT_d, st));
+    PairGeom g;
+    g.tgt = ctx->tgtT_pos_d;
+    g.src = ctx->recT_d;
+    g.src_off = ctx->recT_off_d;
+    g.blk_off = ctx->blkT_off_d;
+    g.centres = ctx->centres_d;
+    g.ntargets = ctx->sumN;
+    const PairWork wk = work_of(*plan);
+    if (wk.total_units > 0) {
+        CK(pair_launch(variant, g, wk, ctx->err_d, st));
+        ctx->launches += 1;
+    }
+    CK(pair_epilogue(3, nrhs, wk, nullptr, 0.0, kernel_scale(ctx), z, ctx->sumN, st));
+    ctx->launches += 2;
+    return MFS_OK;
+}
+
+// out^(k) = ((I - L^(k)) S_L^(k)+)^T z^(k) = R_M U W_p R_N^T z (project) or (S_L^(k)+)^T z = R_M U W_r R_N^T z,
+// z [nrhs][sum_N][3] -> out [nrhs][sum_M][3] (transposes of the two-step apply, Eq. pseudo).
+mfs_status precondT_dev(mfs_ctx *ctx, const double *z, double *out, int project, int nrhs, cudaStream_t st) {
+    for (auto &sh : ctx->shapes) {
+        const int nb = (int)sh.bodies.size();
+        if (nb == 0) continue;
+        const int ncols = nb * nrhs;
+        const ShapeDev &sd = sh.dev;
+        CK(gather_rotate(3, z, ctx->sumN * 3, sh.col_body, sh.col_rhs, ctx->src_off_d, ctx->rot64_d, ncols, sd.dN,
+                         sh.A, nullptr, st));
+        const int S1 = gemm_splitk_chunks(ncols, sd.r, sd.dN, ctx->sm_count);
+        const int S2 = gemm_splitk_chunks(ncols, sd.dM, sd.r, ctx->sm_count);
+        CK(gemm_splitk(ncols, sd.r, sd.dN, S1, sh.A, project ? sd.Wp : sd.Wr, sh.PkT, sh.Tm, nullptr, st, true));
+        CK(gemm_splitk(ncols, sd.dM, sd.r, S2, sh.Tm, sd.U, sh.PkT, nullptr, sh.O64, st, true));
+        CK(scatter_rotate(3, nullptr, sh.O64, sh.col_body, sh.col_rhs, ctx->tgt_off_d, ctx->rot_d, ctx->rot64_d,
+                          ncols, sd.dM, ctx->sumM, out, st));
+        ctx->launches += 6;
+    }
+    return MFS_OK;
+}
+
+// y = A^T w = w + [((I - L^(k')) S_L^(k')+)^T sum_{k != k'} S^(kk')^T w^(k)]_k'
+mfs_status matvec_T_dev(mfs_ctx *ctx, const double *w, double *y, int nrhs, cudaStream_t st) {
+    CKS(pair_apply_T(ctx, w, ctx->lam_d, nrhs, 0, st));
+    CKS(precondT_dev(ctx, ctx->lam_d, ctx->tmpM_d, 1, nrhs, st));
+    const size_t n = (size_t)nrhs * ctx->sumM * 3;
+    combine_raw_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ctx->tmpM_d, w, 1.0, 1.0, y, n);
+    CK(cudaGetLastError());
+    ctx->launches += 1;
+    return MFS_OK;
+}
+
 struct SolveStats {
     int iters = 0, converged = 1, matvecs = 0, breakdown = 0;
     double resid = 0.0;
 };
 
-// Solve A x = b (b = ctx->b_d) for all lanes; x in ctx->x_d.
-mfs_status gmres_solve(mfs_ctx *ctx, int nrhs, cudaStream_t st, SolveStats &stats) {
+// Solve A x = b (or A^T x = b) with b = ctx->b_d for all lanes; x in ctx->x_d.
+mfs_status gmres_solve(mfs_ctx *ctx, int nrhs, cudaStream_t st, SolveStats &stats, bool transposed = false) {
     GmresDev &gd = ctx->gd;
     CK(gmres_init(gd, ctx->b_d, st));
     ctx->launches += 5;
     int j = 0;
     for (; j < gd.m; ++j) {
-        CKS(matvec_dev(ctx, gd.V + (size_t)j * gd.n, ctx->w_d, nrhs, st));
+        if (transposed)
+            CKS(matvec_T_dev(ctx, gd.V + (size_t)j * gd.n, ctx->w_d, nrhs, st));
+        else
+            CKS(matvec_dev(ctx, gd.V + (size_t)j * gd.n, ctx->w_d, nrhs, st));
         stats.matvecs++;
         CK(gmres_arnoldi(gd, ctx->w_d, j, st));
         ctx->launches += 9;
@@ -967,7 +1125,7 @@ static mfs_status autotune(mfs_ctx *ctx, int nrhs, cudaStream_t st) {
     // zero strengths: the timing does not depend on the values
     CK(cudaMemsetAsync(ctx->lam_d, 0, sizeof(double) * (size_t)nrhs * ctx->sumN * ctx->D, st));
     for (int i = 0; i < count; ++i) {
-        if (v[i].D != ctx->D || v[i].nrhs != nrhs) continue;
+        if (v[i].grad || v[i].D != ctx->D || v[i].nrhs != nrhs) continue;
         if (pair_occupancy(i) <= 0) continue;
         PairPlan *plan = nullptr;
         CKS(get_plan(ctx, i, 0, &plan));
@@ -1177,6 +1335,14 @@ mfs_status mfs_solve_mobility(mfs_ctx *ctx, const double *F, const double *T, do
     CK(extract_stokes(ctx->lam_d, nrhs, ctx->P, ctx->src_local64_d, ctx->src_off_d, ctx->sumN, Uo.d, Oo.d, st));
     ctx->launches += 1;
     CK(cudaEventRecord(ctx->ev1, st));
+    // keep gamma, F and T for mfs_mobility_vjp (outside the timed region)
+    if (!ctx->keep_gamma) {
+        CK(ctx->alloc(&ctx->keep_gamma, (size_t)ctx->opt.max_rhs * ctx->sumM * 3));
+        CK(ctx->alloc(&ctx->keep_lam0, (size_t)ctx->opt.max_rhs * ctx->P * 6));  // F then T
+    }
+    CK(cudaMemcpyAsync(ctx->keep_gamma, ctx->x_d, sizeof(double) * nrhs * ctx->sumM * 3, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ctx->keep_lam0, Fi.d, sizeof(double) * nb, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ctx->keep_lam0 + nb, Ti.d, sizeof(double) * nb, cudaMemcpyDeviceToDevice, st));
     CK(cudaEventSynchronize(ctx->ev1));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
@@ -1221,11 +1387,146 @@ mfs_status mfs_solve_elastance(mfs_ctx *ctx, const double *Q, double *V, int32_t
     return finish_info(ctx, info, ss, ms, nrhs);
 }
 
+}  // extern "C"
+
+// FP64 -> FP32 (adjoint strengths for the gradient kernel)
+static __global__ void to_f32_kernel(const double *x, float *y, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        y[i] = (float)x[i];
+}
+
+// dL/dc_k = scale * (source-side sum of body k) - (sum over the targets of body k of their gradient sums)
+static __global__ void centre_grad_kernel(const double *gradT, const int *tgt_off, const double *src_grad, double scale,
+                                          double *dc) {
+    const int k = blockIdx.x;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int i = tgt_off[k] + threadIdx.x; i < tgt_off[k + 1]; i += blockDim.x)
+        for (int c = 0; c < 3; ++c) acc[c] += gradT[3 * (size_t)i + c];
+    __shared__ double red[3][128];
+    for (int c = 0; c < 3; ++c) red[c][threadIdx.x] = acc[c];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) dc[3 * k + threadIdx.x] = scale * src_grad[3 * k + threadIdx.x] - red[threadIdx.x][0];
+}
+
+// [dF; dT]_k = G_k^{-1} v_k with G_k = R_2 G_0 R_2^T (v = -K_N^T z, given as its force and torque parts)
+static __global__ void gram_solve_kernel(const double *vf, const double *vt, int P, int nrhs, const double *rot64,
+                                         const double *G0inv_shapes, const int *shape_id, double *dF, double *dT) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P * nrhs) return;
+    const int k = i % P;
+    const double *R = rot64 + 9 * k;
+    const double *f = vf + 3 * (size_t)i, *t = vt + 3 * (size_t)i;
+    double b[6], a[6];
+    for (int c = 0; c < 3; ++c) {
+        b[c] = R[c] * f[0] + R[3 + c] * f[1] + R[6 + c] * f[2];
+        b[3 + c] = R[c] * t[0] + R[3 + c] * t[1] + R[6 + c] * t[2];
+    }
+    const double *Gi = G0inv_shapes + 36 * shape_id[k];
+    for (int m = 0; m < 6; ++m) {
+        double s = 0.0;
+        for (int n = 0; n < 6; ++n) s += Gi[m * 6 + n] * b[n];
+        a[m] = s;
+    }
+    for (int c = 0; c < 3; ++c) {
+        dF[3 * (size_t)i + c] = R[3 * c] * a[0] + R[3 * c + 1] * a[1] + R[3 * c + 2] * a[2];
+        dT[3 * (size_t)i + c] = R[3 * c] * a[3] + R[3 * c + 1] * a[4] + R[3 * c + 2] * a[5];
+    }
+}
+
+extern "C" {
+
+// Reverse mode of the last mfs_solve_mobility.  With U = E gamma, E = -K_N^T S_L^+ and A gamma = -u_0:
+//   g = E^T dL/dU = -(S_L^+)^T K_N [dU; dOmega];  A^T w = g;  mu = lambda_0 + (I - L) S_L^+ gamma;
+//   dL/dc_k = -sum_{i in k, j not in k} d/dr[w_i^T G mu_j] + sum_{j in k, i not in k} d/dr[w_i^T G mu_j];
+//   dL/d[f; t]_k = -G_k^{-1} K_N^T (S^T w)_k over all pairs (Eq. stou0, Eq. lambda01-02).
 mfs_status mfs_mobility_vjp(mfs_ctx *ctx, const double *dU, const double *dOmega, int32_t nrhs, double *dcenters,
                             double *dF, double *dT, void *stream) {
-    (void)dU; (void)dOmega; (void)nrhs; (void)dcenters; (void)dF; (void)dT; (void)stream;
-    if (ctx) ctx->last_error = "mfs_mobility_vjp: not available in this build";
-    return MFS_ERR_INVALID_ARG;
+    if (!ctx || !dU || !dOmega || !dcenters || nrhs < 1 || nrhs > ctx->opt.max_rhs || (!dF) != (!dT)) {
+        if (ctx) ctx->last_error = "mfs_mobility_vjp: invalid argument";
+        return MFS_ERR_INVALID_ARG;
+    }
+    if (ctx->kind != MFS_STOKES || !ctx->keep_gamma || ctx->last_nrhs != nrhs) {
+        ctx->last_error = "mfs_mobility_vjp needs a preceding mfs_solve_mobility with the same nrhs";
+        return MFS_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int P = ctx->P;
+    const size_t nb = (size_t)nrhs * P * 3, nM = (size_t)nrhs * ctx->sumM * 3;
+    Staged dUi, dWi, dco, dFo, dTo;
+    CKS(stage_in(ctx, dUi, dU, nb, st));
+    CKS(stage_in(ctx, dWi, dOmega, nb, st));
+    CKS(stage_out_alloc(ctx, dco, dcenters, (size_t)P * 3));
+    if (dF) {
+        CKS(stage_out_alloc(ctx, dFo, dF, nb));
+        CKS(stage_out_alloc(ctx, dTo, dT, nb));
+    }
+    CKS(ensure_transposed(ctx));
+    CKS(ensure_gmres(ctx, nrhs));
+    begin_call(ctx);
+    // 1. seed g = -(S_L^+)^T K_N [dU; dOmega]
+    CK(completion_stokes(dUi.d, dWi.d, nrhs, P, ctx->rot64_d, ctx->eye6_d, ctx->shape_id_d, ctx->src_local64_d,
+                         ctx->src_off_d, ctx->sumN, ctx->lam_d, st));
+    CKS(precondT_dev(ctx, ctx->lam_d, ctx->tmpM_d, 0, nrhs, st));
+    combine_raw_kernel<<<(unsigned)((nM + 255) / 256), 256, 0, st>>>(ctx->tmpM_d, nullptr, 0.0, -1.0, ctx->b_d, nM);
+    CK(cudaGetLastError());
+    // 2. A^T w = g
+    SolveStats ss;
+    CKS(gmres_solve(ctx, nrhs, st, ss, true));
+    if (ss.breakdown || !ss.converged) {
+        ctx->last_error = "adjoint GMRES did not converge";
+        return ss.breakdown ? MFS_ERR_BREAKDOWN : MFS_ERR_NOT_CONVERGED;
+    }
+    // 3. mu = lambda_0 + (I - L) S_L^+ gamma  (lambda_0 rebuilt from the kept F, T)
+    double *lam0 = ctx->tmpM_d;  // [nrhs][sum_N][3] fits: sum_N < sum_M
+    CK(completion_stokes(ctx->keep_lam0, ctx->keep_lam0 + nb, nrhs, P, ctx->rot64_d, ctx->G0inv_d, ctx->shape_id_d,
+                         ctx->src_local64_d, ctx->src_off_d, ctx->sumN, lam0, st));
+    CKS(precond_apply_dev(ctx, ctx->keep_gamma, ctx->lam_d, 1, nrhs, st));
+    const size_t nN = (size_t)nrhs * ctx->sumN * 3;
+    combine_raw_kernel<<<(unsigned)((nN + 255) / 256), 256, 0, st>>>(lam0, ctx->lam_d, 1.0, 1.0, ctx->lam_d, nN);
+    CK(cudaGetLastError());
+    // 4. centre gradient: pair kernel over off-diagonal pairs with target strengths w, source strengths mu
+    int vc = 0, gv = -1;
+    const PairVariant *vv = pair_variants(&vc);
+    for (int i = 0; i < vc; ++i)
+        if (vv[i].grad && vv[i].nrhs == nrhs) gv = i;
+    if (gv < 0) {
+        ctx->last_error = "no gradient kernel for this nrhs";
+        return MFS_ERR_INVALID_ARG;
+    }
+    to_f32_kernel<<<1024, 256, 0, st>>>(ctx->x_d, ctx->w32_d, nM);
+    CK(pack_sources(3, nrhs, 0, ctx->src_pos_d, ctx->rec_pt_d, ctx->lam_d, ctx->sumN, ctx->nrec, ctx->rec_d, st));
+    CK(cudaMemsetAsync(ctx->src_grad_d, 0, sizeof(double) * 3 * P, st));
+    PairPlan *plan = nullptr;
+    CKS(get_plan(ctx, gv, 0, &plan));
+    PairGeom g = geom_of(ctx);
+    g.tgt_w = ctx->w32_d;
+    PairWork wk = work_of(*plan);
+    wk.src_grad = ctx->src_grad_d;
+    if (wk.total_units > 0) CK(pair_launch(gv, g, wk, ctx->err_d, st));
+    CK(pair_epilogue(3, 1, wk, nullptr, 0.0, kernel_scale(ctx), ctx->gradT_d, ctx->sumM, st));
+    centre_grad_kernel<<<P, 128, 0, st>>>(ctx->gradT_d, ctx->tgt_off_d, ctx->src_grad_d, kernel_scale(ctx), dco.d);
+    CK(cudaGetLastError());
+    ctx->launches += 6;
+    // 5. force and torque cotangents
+    if (dF) {
+        CKS(pair_apply_T(ctx, ctx->x_d, ctx->lam_d, nrhs, 1, st));
+        CK(extract_stokes(ctx->lam_d, nrhs, P, ctx->src_local64_d, ctx->src_off_d, ctx->sumN, ctx->six_d,
+                          ctx->six_d + nb, st));
+        gram_solve_kernel<<<(unsigned)((P * nrhs + 127) / 128), 128, 0, st>>>(
+            ctx->six_d, ctx->six_d + nb, P, nrhs, ctx->rot64_d, ctx->G0inv_d, ctx->shape_id_d, dFo.d, dTo.d);
+        CK(cudaGetLastError());
+        ctx->launches += 2;
+        CKS(stage_out_finish(ctx, dFo, st));
+        CKS(stage_out_finish(ctx, dTo, st));
+    }
+    CKS(stage_out_finish(ctx, dco, st));
+    CK(cudaStreamSynchronize(st));
+    return check_device_error(ctx, st);
 }
 
 }  // extern "C"

@@ -127,8 +127,14 @@ __device__ __forceinline__ Stage make_stage(const PairTile *tiles, int ntiles, c
 // ---------------------------------------------------------------------------
 // Compute policies
 // ---------------------------------------------------------------------------
+// Hooks every policy has; the gradient policy overrides them (target strengths, source-side sums).
+struct PolicyBase {
+    __device__ __forceinline__ void load_extra(int, int, const PairGeom &) {}
+    __device__ __forceinline__ void source_side(int, bool, double *) {}
+};
+
 template <int D, int NRHS, int T, int NT>
-struct Scalar {
+struct Scalar : PolicyBase {
     static constexpr int C = D * NRHS;
     static constexpr int REC = rec_floats(D, NRHS, false);
     static constexpr int TPT = T;  // targets per thread
@@ -226,7 +232,7 @@ struct Scalar {
 };
 
 template <int NRHS, int TP, int NT>
-struct PackedStokes {
+struct PackedStokes : PolicyBase {
     static constexpr int D = 3;
     static constexpr int C = 3 * NRHS;
     static constexpr int REC = rec_floats(3, NRHS, true);
@@ -347,7 +353,7 @@ struct PackedStokes {
 // The same packed Stokeslet arithmetic with all per-target state in registers (more registers,
 // more freedom for the compiler to interleave sources; the autotuner picks per geometry).
 template <int NRHS, int TP, int NT>
-struct PackedStokesReg {
+struct PackedStokesReg : PolicyBase {
     static constexpr int D = 3;
     static constexpr int C = 3 * NRHS;
     static constexpr int REC = rec_floats(3, NRHS, true);
@@ -453,6 +459,134 @@ struct PackedStokesReg {
     }
 };
 
+// Centre gradient for the adjoint: per pair, the gradient with respect to r = x_i - y_j of
+// w_i^T G(r) mu_j summed over right-hand sides,
+//   [ w_c (r.mu) + mu_c (w.r) - (w.mu) r_c - 3 (w.r)(r.mu) r_c / r^2 ] / r^3   (x 1/(8 pi mu) later),
+// accumulated per target like the pair sums (self pairs left out) and, at every source-body
+// boundary, reduced over the CTA's targets into src_grad[body] (one FP64 atomic per component).
+template <int NRHS, int T, int NT>
+struct GradStokes : PolicyBase {
+    static constexpr int D = 3;
+    static constexpr int C = 3;  // one gradient 3-vector per target
+    static constexpr int REC = rec_floats(3, NRHS, false);
+    static constexpr int TPT = T;
+    static constexpr int PSM = 0;
+    float3 tp[T];
+    int tb[T];
+    float w[T][3 * NRHS];
+    float hi[T][3], lo[T][3], bsum[T][3];
+
+    __device__ __forceinline__ void init(float *, int) {}
+    __device__ __forceinline__ void set_target(int j, float4 p) {
+        tp[j] = make_float3(p.x, p.y, p.z);
+        tb[j] = __float_as_int(p.w);
+    }
+    __device__ __forceinline__ void load_extra(int j, int idx, const PairGeom &geo) {
+#pragma unroll
+        for (int h = 0; h < NRHS; ++h)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                w[j][3 * h + c] = idx >= 0 ? geo.tgt_w[((size_t)h * geo.ntargets + idx) * 3 + c] : 0.f;
+    }
+    __device__ __forceinline__ void reset() {
+#pragma unroll
+        for (int j = 0; j < T; ++j)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) hi[j][c] = lo[j][c] = bsum[j][c] = 0.f;
+    }
+    __device__ __forceinline__ void compute(const float *sb, int nrec, const float (*dc)[3], int kb0) {
+        float3 xt[T];
+#pragma unroll
+        for (int j = 0; j < T; ++j) {
+            const int r = tb[j] - kb0;
+            xt[j] = make_float3(dc[r][0] + tp[j].x, dc[r][1] + tp[j].y, dc[r][2] + tp[j].z);
+        }
+        for (int s0 = 0; s0 < nrec; s0 += MFS_BS) {
+            const int s1 = min(s0 + MFS_BS, nrec);
+            float blk[T][3];
+#pragma unroll
+            for (int j = 0; j < T; ++j)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) blk[j][c] = 0.f;
+            for (int s = s0; s < s1; ++s) {
+                float rec[REC];
+#pragma unroll
+                for (int v = 0; v < REC / 4; ++v) {
+                    const float4 f = reinterpret_cast<const float4 *>(sb + s * REC)[v];
+                    rec[4 * v + 0] = f.x;
+                    rec[4 * v + 1] = f.y;
+                    rec[4 * v + 2] = f.z;
+                    rec[4 * v + 3] = f.w;
+                }
+#pragma unroll
+                for (int j = 0; j < T; ++j) {
+                    const float dx = xt[j].x - rec[0], dy = xt[j].y - rec[1], dz = xt[j].z - rec[2];
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    const float ri = rsqrtf(r2);
+                    const float ri2 = ri * ri, ri3 = ri * ri2;
+#pragma unroll
+                    for (int h = 0; h < NRHS; ++h) {
+                        const float mx = rec[3 + 3 * h], my = rec[4 + 3 * h], mz = rec[5 + 3 * h];
+                        const float wx = w[j][3 * h], wy = w[j][3 * h + 1], wz = w[j][3 * h + 2];
+                        const float wm = fmaf(wx, mx, fmaf(wy, my, wz * mz));
+                        const float wr = fmaf(wx, dx, fmaf(wy, dy, wz * dz));
+                        const float rm = fmaf(dx, mx, fmaf(dy, my, dz * mz));
+                        const float q = -fmaf(3.f * wr * rm, ri2, wm);
+                        blk[j][0] = fmaf(fmaf(dx, q, fmaf(wx, rm, mx * wr)), ri3, blk[j][0]);
+                        blk[j][1] = fmaf(fmaf(dy, q, fmaf(wy, rm, my * wr)), ri3, blk[j][1]);
+                        blk[j][2] = fmaf(fmaf(dz, q, fmaf(wz, rm, mz * wr)), ri3, blk[j][2]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < T; ++j)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) bsum[j][c] += blk[j][c];
+        }
+    }
+    // All threads of the CTA call this together (the source-body boundary is CTA-uniform).
+    __device__ __forceinline__ void source_side(int body, bool include_self, double *src_grad) {
+        __shared__ float red[NT / 32][3];
+        float s[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < T; ++j)
+            if (include_self || tb[j] != body)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) s[c] += bsum[j][c];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            for (int o = 16; o > 0; o >>= 1) s[c] += __shfl_xor_sync(0xffffffffu, s[c], o);
+        if ((threadIdx.x & 31) == 0)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) red[threadIdx.x >> 5][c] = s[c];
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            float v = 0.f;
+            for (int q = 0; q < NT / 32; ++q) v += red[q][threadIdx.x];
+            atomicAdd(&src_grad[3 * body + threadIdx.x], (double)v);
+        }
+        __syncthreads();
+    }
+    __device__ __forceinline__ void end_body(int body, bool include_self) {
+#pragma unroll
+        for (int j = 0; j < T; ++j) {
+            const bool keep = include_self || (tb[j] != body);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float s, e;
+                two_sum(hi[j][c], keep ? bsum[j][c] : 0.f, s, e);
+                hi[j][c] = s;
+                lo[j][c] += e;
+                bsum[j][c] = 0.f;
+            }
+        }
+    }
+    __device__ __forceinline__ float result(int j, int c, float &l) const {
+        l = lo[j][c];
+        return hi[j][c];
+    }
+};
+
 // ---------------------------------------------------------------------------
 // The persistent stream-K kernel
 // ---------------------------------------------------------------------------
@@ -505,8 +639,10 @@ __global__ void __launch_bounds__(NT) pair_sum_kernel(PairGeom geo, PairWork wor
 #pragma unroll
         for (int j = 0; j < TPT; ++j) {
             int idx = t_.t0 + tid + j * NT;
-            if (idx >= t_.t1) idx = t_.t1 - 1;
+            const bool in_tile = idx < t_.t1;
+            if (!in_tile) idx = t_.t1 - 1;  // a clamped duplicate: computed, never written
             pol.set_target(j, geo.tgt[idx]);
+            pol.load_extra(j, in_tile ? idx : -1, geo);
         }
         pol.reset();
     };
@@ -547,7 +683,10 @@ __global__ void __launch_bounds__(NT) pair_sum_kernel(PairGeom geo, PairWork wor
         pol.compute(smem + buf * SREC * REC, cur.nrec, dcs[buf], tl.kb0);
 
         // end of a source body (for this tile): fold into (hi, lo), leaving self pairs out
-        if ((nxt.tile < 0) || nxt.tile != cur.tile || nxt.body != cur.body) pol.end_body(cur.body, work.include_self);
+        if ((nxt.tile < 0) || nxt.tile != cur.tile || nxt.body != cur.body) {
+            pol.source_side(cur.body, work.include_self, work.src_grad);  // CTA-uniform (may synchronise)
+            pol.end_body(cur.body, work.include_self);
+        }
         // end of this CTA's segment of the tile: write the tile's result
         if ((nxt.tile < 0) || nxt.tile != cur.tile) {
             const long long seg_end = cur.u + cur.nblk;
@@ -689,7 +828,9 @@ static int occupancy_variant() {
 }
 
 // Scalar S(D, nrhs, targets per thread, threads); packed Stokes P(nrhs, target pairs per thread, threads)
-#define MFS_VARIANTS(S, P)  \
+// Scalar S(D, nrhs, T, NT); packed Stokes P(policy, nrhs, target pairs per thread, NT);
+// centre-gradient G(nrhs, T, NT) for the adjoint
+#define MFS_VARIANTS(S, P, G)  \
     S(3, 1, 4, 128)         \
     S(3, 1, 2, 128)         \
     S(3, 1, 4, 256)         \
@@ -713,14 +854,20 @@ static int occupancy_variant() {
     P(PackedStokes, 1, 2, 256)    \
     P(PackedStokes, 1, 3, 128)    \
     P(PackedStokes, 2, 1, 128)    \
-    P(PackedStokes, 4, 1, 128)
+    P(PackedStokes, 4, 1, 128)    \
+    G(1, 4, 128)                  \
+    G(2, 2, 128)                  \
+    G(3, 2, 128)                  \
+    G(4, 2, 128)
 
 static const PairVariant kVariants[] = {
-#define S(D_, R_, T_, N_) {D_, R_, T_, N_, N_ * T_, 0},
-#define P(POL_, R_, TP_, N_) {3, R_, 2 * TP_, N_, N_ * 2 * TP_, 1},
-    MFS_VARIANTS(S, P)
+#define S(D_, R_, T_, N_) {D_, R_, T_, N_, N_ * T_, 0, 0},
+#define P(POL_, R_, TP_, N_) {3, R_, 2 * TP_, N_, N_ * 2 * TP_, 1, 0},
+#define G(R_, T_, N_) {3, R_, T_, N_, N_ * T_, 0, 1},
+    MFS_VARIANTS(S, P, G)
 #undef S
 #undef P
+#undef G
 };
 
 const PairVariant *pair_variants(int *count) {
@@ -736,9 +883,12 @@ int pair_occupancy(int vi) {
     if (vi == i++) return occupancy_variant<Scalar<D_, R_, T_, N_>, N_>();
 #define P(POL_, R_, TP_, N_) \
     if (vi == i++) return occupancy_variant<POL_<R_, TP_, N_>, N_>();
-    MFS_VARIANTS(S, P)
+#define G(R_, T_, N_) \
+    if (vi == i++) return occupancy_variant<GradStokes<R_, T_, N_>, N_>();
+    MFS_VARIANTS(S, P, G)
 #undef S
 #undef P
+#undef G
     return 0;
 }
 
@@ -748,9 +898,12 @@ cudaError_t pair_launch(int vi, const PairGeom &geo, const PairWork &work, int *
     if (vi == i++) return launch_variant<Scalar<D_, R_, T_, N_>, N_>(geo, work, err, st);
 #define P(POL_, R_, TP_, N_) \
     if (vi == i++) return launch_variant<POL_<R_, TP_, N_>, N_>(geo, work, err, st);
-    MFS_VARIANTS(S, P)
+#define G(R_, T_, N_) \
+    if (vi == i++) return launch_variant<GradStokes<R_, T_, N_>, N_>(geo, work, err, st);
+    MFS_VARIANTS(S, P, G)
 #undef S
 #undef P
+#undef G
     return cudaErrorInvalidValue;
 }
 

@@ -356,6 +356,7 @@ __global__ void __launch_bounds__(256) gemm_rm_kernel(int m, int n, int k, const
 // per-output (hi, lo) pair by TwoSum, so the rounding of a long sequential FP32 sum (which, over
 // k = 3600, limits the solved velocities to ~2e-5) never builds up; the chunk results are
 // written in FP64 and added in FP64 by splitk_reduce_kernel.
+template <bool TRANS_B>  // TRANS_B: B is stored [n][k] (C = A B^T)
 __global__ void __launch_bounds__(256) gemm_splitk_kernel(int m, int n, int k, int kchunk,
                                                           const float *__restrict__ A,
                                                           const float *__restrict__ B, double *__restrict__ P) {
@@ -377,9 +378,15 @@ __global__ void __launch_bounds__(256) gemm_splitk_kernel(int m, int n, int k, i
             As[c][r] = (gm < m && gk < ke) ? A[(size_t)gm * k + gk] : 0.f;
         }
         for (int e = threadIdx.x; e < BK * BN; e += 256) {
-            const int r = e / BN, c = e % BN;
-            const int gk = k0 + r, gn = n0 + c;
-            Bs[r][c] = (gk < ke && gn < n) ? B[(size_t)gk * n + gn] : 0.f;
+            if (TRANS_B) {  // consecutive threads read consecutive k of one row of B[n][k]
+                const int c = e / BK, r = e % BK;
+                const int gk = k0 + r, gn = n0 + c;
+                Bs[r][c] = (gk < ke && gn < n) ? B[(size_t)gn * k + gk] : 0.f;
+            } else {
+                const int r = e / BN, c = e % BN;
+                const int gk = k0 + r, gn = n0 + c;
+                Bs[r][c] = (gk < ke && gn < n) ? B[(size_t)gk * n + gn] : 0.f;
+            }
         }
         __syncthreads();
         float s[4][4];
@@ -440,12 +447,15 @@ int gemm_splitk_chunks(int m, int n, int k, int sm_count) {
 }
 
 cudaError_t gemm_splitk(int m, int n, int k, int S, const float *A, const float *B, double *P, float *C32,
-                        double *C64, cudaStream_t st) {
+                        double *C64, cudaStream_t st, bool trans_b) {
     if (m == 0 || n == 0) return cudaSuccess;
     const int kchunk = ((k + S - 1) / S + 15) / 16 * 16;
     const int Sz = (k + kchunk - 1) / kchunk;
     dim3 grid((n + 63) / 64, (m + 63) / 64, Sz);
-    gemm_splitk_kernel<<<grid, 256, 0, st>>>(m, n, k, kchunk, A, B, P);
+    if (trans_b)
+        gemm_splitk_kernel<true><<<grid, 256, 0, st>>>(m, n, k, kchunk, A, B, P);
+    else
+        gemm_splitk_kernel<false><<<grid, 256, 0, st>>>(m, n, k, kchunk, A, B, P);
     const size_t mn = (size_t)m * n;
     splitk_reduce_kernel<<<(unsigned)std::min<size_t>((mn + 255) / 256, 4096), 256, 0, st>>>(Sz, mn, P, C32, C64);
     return cudaGetLastError();
