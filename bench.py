@@ -58,6 +58,11 @@ def _args():
     ap.add_argument("--cpu-sample-bodies", type=int, default=12)
     ap.add_argument("--small", action="store_true",
                     help="profiling case: 24 spheres with the same M, N and volume fraction (not a bench line)")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "batched256_mobility", "sphere200_adjoint", "spheroid1000_mobility"],
+                    help="secondary measurements (their own JSON line); the default is the benchmark")
+    ap.add_argument("--compare-fp64", action="store_true",
+                    help="secondary workloads: also time the FP64 reference GPU solve (precision = 1)")
     return ap.parse_args()
 
 
@@ -168,8 +173,92 @@ def reference_arm(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def secondary(args):
+    """Batched, adjoint and large-suspension measurements: one JSON line each (not the benchmark line)."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from mfs_inputs import make_workload
+    from paper_2409_04215_gb300 import MFS
+
+    dev = torch.device("cuda", 0)
+    name = args.workload
+    wl = make_workload(name)
+    t0 = time.perf_counter()
+    opts = {"max_iter": 100, "restart": 100} if name == "batched256_mobility" else {}
+    ctx = MFS.from_workload(wl, profile=1, **opts)
+    setup_s = time.perf_counter() - t0
+    F = torch.tensor(wl.F, device=dev)
+    T = torch.tensor(wl.T, device=dev)
+    for _ in range(args.warmup):
+        U, W, info = ctx.solve_mobility(F, T)
+        if name == "sphere200_adjoint":
+            ctx.mobility_vjp(2.0 * U, torch.zeros_like(W))
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    infos, vjp_ms = [], []
+    for _ in range(args.steps):
+        U, W, info = ctx.solve_mobility(F, T)
+        infos.append(info)
+        if name == "sphere200_adjoint":
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            ctx.mobility_vjp(2.0 * U, torch.zeros_like(W))
+            torch.cuda.synchronize()
+            vjp_ms.append(1e3 * (time.perf_counter() - t1))
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    solve_ms = statistics.median(i.ms_solve for i in infos)
+    pairs = infos[-1].pairs * wl.nrhs
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = 2 * 128 * sms * 2070e6 / 1e12
+    pair_ms = sum(i.ms_pairs for i in infos) / len(infos)
+    # algorithmic flops per point pair: the geometry (r, r^2, rsqrt, r^-2: 10) once, then 18 per rhs
+    flops = infos[-1].pairs * (10 + 18 * wl.nrhs)
+    line = {
+        "metric": f"Stokeslet pair-interactions/s ({name})",
+        "value": pairs / (solve_ms / 1e3),
+        "unit": UNIT,
+        "n_gpus": 1,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": solve_ms,
+        "higher_is_better": True,
+        "dtype": "f32 pair sums, f64 GMRES",
+        "data": "synthetic",
+        "config": {"workload": wl.description, "bodies": wl.num_bodies, "suspensions": wl.num_suspensions,
+                   "nrhs": wl.nrhs, "gmres_tol": 1e-7, **opts},
+        "setup_s": setup_s,
+        "gmres_iters": infos[-1].iters,
+        "lanes": infos[-1].lanes,
+        "pair_kernel_tflops": flops / (pair_ms / 1e3) / 1e12 if pair_ms > 0 else None,
+        "pair_kernel_frac_of_fp32_peak": (flops / (pair_ms / 1e3) / 1e12) / peak if pair_ms > 0 else None,
+        "flops_per_pair": 10 + 18 * wl.nrhs,
+        "gpu_launches": infos[-1].launches,
+        "clocks": ck,
+    }
+    if vjp_ms:
+        line["vjp_ms"] = statistics.median(vjp_ms)
+    if args.compare_fp64:
+        ref = MFS.from_workload(wl, precision=1, autotune=0, **opts)
+        t1 = time.perf_counter()
+        Ur, Wr, rinfo = ref.solve_mobility(F, T)
+        torch.cuda.synchronize()
+        got = torch.cat([U, W], dim=-1).cpu().numpy().ravel()
+        refv = torch.cat([Ur, Wr], dim=-1).cpu().numpy().ravel()
+        line["fp64_gpu_solve"] = {"ms": rinfo.ms_solve, "wall_s": time.perf_counter() - t1, "iters": rinfo.iters,
+                                  "rel_diff_fp32_vs_fp64": float(np.linalg.norm(got - refv) / np.linalg.norm(refv)),
+                                  "speedup_fp32_path": rinfo.ms_solve / solve_ms}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = _args()
+    if args.impl == "gpu" and args.workload != WORKLOAD:
+        secondary(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

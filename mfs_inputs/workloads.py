@@ -252,7 +252,10 @@ def batched_suspensions(
         radii = np.array([shapes[i].bounding_radius for i in ids])
         vol = sum(shapes[i].volume for i in ids)
         side = (vol / volume_fraction) ** (1.0 / 3.0)
-        side = max(side, 2.0 * radii.max() + 1e-9)
+        # keep random sequential addition far from jamming: the bounding spheres (grown by half the
+        # gap) fill at most a quarter of the box their centres may occupy
+        excl = sum(4.0 / 3.0 * np.pi * (r + 0.5 * min_gap) ** 3 for r in radii)
+        side = max(side, (excl / 0.25) ** (1.0 / 3.0) + 2.0 * radii.max())
         centres[b0:b1] = rsa_in_cube(rng, radii, side, min_gap)
     F = rng.standard_normal((nrhs, total, 3))
     T = rng.standard_normal((nrhs, total, 3))

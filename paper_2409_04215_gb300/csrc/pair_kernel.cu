@@ -61,6 +61,14 @@ __device__ __forceinline__ u64 f2_pack(float lo, float hi) {
 __device__ __forceinline__ void f2_unpack(u64 v, float &lo, float &hi) {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
 }
+// 1/sqrt(x) by the hardware approximation with subnormals flushed: r^2 here is never subnormal
+// (r >= Delta_sep or a padding distance), so the flush never triggers and the subnormal handling
+// of the non-flushing form is pure overhead in the pair loop.
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 // ---------------------------------------------------------------------------
 // Record layouts
@@ -129,6 +137,7 @@ __device__ __forceinline__ Stage make_stage(const PairTile *tiles, int ntiles, c
 // ---------------------------------------------------------------------------
 // Hooks every policy has; the gradient policy overrides them (target strengths, source-side sums).
 struct PolicyBase {
+    static constexpr int MINB = 1;  // minimum resident CTAs per SM requested from the compiler
     __device__ __forceinline__ void load_extra(int, int, const PairGeom &) {}
     __device__ __forceinline__ void source_side(int, bool, double *) {}
 };
@@ -186,7 +195,7 @@ struct Scalar : PolicyBase {
                         const float dy = xt[j].y - rec[1];
                         const float dz = xt[j].z - rec[2];
                         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        const float ri = rsqrtf(r2);
+                        const float ri = rsqrt_ftz(r2);
                         if (D == 1) {
 #pragma unroll
                             for (int h = 0; h < NRHS; ++h) blk[j][h] = fmaf(rec[3 + h], ri, blk[j][h]);
@@ -304,7 +313,7 @@ struct PackedStokes : PolicyBase {
                         const u64 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
                         float a, b;
                         f2_unpack(r2, a, b);
-                        const u64 ri = f2_pack(rsqrtf(a), rsqrtf(b));
+                        const u64 ri = f2_pack(rsqrt_ftz(a), rsqrt_ftz(b));
                         const u64 ri2 = f2_mul(ri, ri);
 #pragma unroll
                         for (int h = 0; h < NRHS; ++h) {
@@ -414,7 +423,7 @@ struct PackedStokesReg : PolicyBase {
                         const u64 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
                         float a, b;
                         f2_unpack(r2, a, b);
-                        const u64 ri = f2_pack(rsqrtf(a), rsqrtf(b));
+                        const u64 ri = f2_pack(rsqrt_ftz(a), rsqrt_ftz(b));
                         const u64 ri2 = f2_mul(ri, ri);
 #pragma unroll
                         for (int h = 0; h < NRHS; ++h) {
@@ -522,7 +531,7 @@ struct GradStokes : PolicyBase {
                 for (int j = 0; j < T; ++j) {
                     const float dx = xt[j].x - rec[0], dy = xt[j].y - rec[1], dz = xt[j].z - rec[2];
                     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const float ri = rsqrtf(r2);
+                    const float ri = rsqrt_ftz(r2);
                     const float ri2 = ri * ri, ri3 = ri * ri2;
 #pragma unroll
                     for (int h = 0; h < NRHS; ++h) {
@@ -600,8 +609,20 @@ struct StageCfg {
     static constexpr int SMEM = 2 * STAGE_REC * REC * 4 + Pol::PSM * NT * 4;
 };
 
-template <class Pol, int NT>
-__global__ void __launch_bounds__(NT) pair_sum_kernel(PairGeom geo, PairWork work, int *err) {
+// The same register-state policy compiled for more resident CTAs per SM: at most
+// 65536 / (NT * MINB) registers per thread (more warps, possibly less interleaving); the autotuner
+// decides per geometry.
+template <int NRHS, int TP, int NT>
+struct PackedStokesRegB4 : PackedStokesReg<NRHS, TP, NT> {
+    static constexpr int MINB = 4;
+};
+template <int NRHS, int TP, int NT>
+struct PackedStokesRegB5 : PackedStokesReg<NRHS, TP, NT> {
+    static constexpr int MINB = 5;
+};
+
+template <class Pol, int NT, int MINB = Pol::MINB>
+__global__ void __launch_bounds__(NT, MINB) pair_sum_kernel(PairGeom geo, PairWork work, int *err) {
     using Cfg = StageCfg<Pol, NT>;
     constexpr int REC = Cfg::REC, SREC = Cfg::STAGE_REC, C = Pol::C, TPT = Pol::TPT;
     extern __shared__ __align__(128) float smem[];
@@ -803,10 +824,10 @@ __global__ void pack_sources_kernel(const float4 *src_pos, const int *src_pt_of_
 // ---------------------------------------------------------------------------
 // Host side: variant table
 // ---------------------------------------------------------------------------
-template <class Pol, int NT>
+template <class Pol, int NT, int MINB = Pol::MINB>
 static cudaError_t launch_variant(const PairGeom &geo, const PairWork &work, int *err, cudaStream_t st) {
     using Cfg = StageCfg<Pol, NT>;
-    auto kern = pair_sum_kernel<Pol, NT>;
+    auto kern = pair_sum_kernel<Pol, NT, MINB>;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
@@ -817,10 +838,10 @@ static cudaError_t launch_variant(const PairGeom &geo, const PairWork &work, int
     return cudaGetLastError();
 }
 
-template <class Pol, int NT>
+template <class Pol, int NT, int MINB = Pol::MINB>
 static int occupancy_variant() {
     using Cfg = StageCfg<Pol, NT>;
-    auto kern = pair_sum_kernel<Pol, NT>;
+    auto kern = pair_sum_kernel<Pol, NT, MINB>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
     int blocks = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, NT, Cfg::SMEM) != cudaSuccess) return 0;
@@ -847,6 +868,10 @@ static int occupancy_variant() {
     S(1, 4, 4, 128)         \
     P(PackedStokesReg, 1, 1, 128) \
     P(PackedStokesReg, 1, 2, 128) \
+    P(PackedStokesRegB4, 1, 2, 128) \
+    P(PackedStokesRegB5, 1, 2, 128) \
+    P(PackedStokesRegB4, 2, 1, 128) \
+    P(PackedStokesRegB4, 4, 1, 128) \
     P(PackedStokesReg, 1, 1, 256) \
     P(PackedStokesReg, 2, 1, 128) \
     P(PackedStokesReg, 4, 1, 128) \
