@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define MFS_ABI_VERSION 1
+#define MFS_ABI_VERSION 2
 
 typedef struct mfs_ctx mfs_ctx; /* opaque; owns all internal device memory */
 
@@ -82,6 +82,8 @@ typedef struct {
     int32_t max_rhs;   /* largest nrhs any later call will use (1..4); default 4 */
     int32_t profile;   /* 1: bracket every pair-kernel launch with CUDA events (no host sync) and report
                           their summed device time in mfs_solve_info.ms_pairs; default 0 */
+    int32_t tensor_cores; /* 1: precision-0 one-body apply on the tensor cores (tcgen05, split 3xTF32 products,
+                             FP32 accumulation in short K chunks summed in FP64); 0: CUDA-core split-K GEMM */
 } mfs_options;
 
 typedef struct {

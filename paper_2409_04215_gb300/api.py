@@ -81,6 +81,7 @@ class Options(ctypes.Structure):
         ("autotune", ctypes.c_int32),
         ("max_rhs", ctypes.c_int32),
         ("profile", ctypes.c_int32),
+        ("tensor_cores", ctypes.c_int32),
     ]
 
 
@@ -116,6 +117,9 @@ class SolveInfo:
     status: int
 
 
+ABI_VERSION = 2  # MFS_ABI_VERSION of the header these structures mirror
+
+
 def load_library(path: Optional[str] = None):
     """Load libmfs.so (raises if it is missing: there is no fallback path)."""
     global _lib
@@ -148,6 +152,8 @@ def load_library(path: Optional[str] = None):
     for name in EXPORTED:
         if not hasattr(lib, name):
             raise RuntimeError(f"libmfs.so lacks {name}")
+    if lib.mfs_abi_version() != ABI_VERSION:
+        raise RuntimeError(f"libmfs.so ABI {lib.mfs_abi_version()} != {ABI_VERSION}: rebuild the library")
     _lib = lib
     return lib
 

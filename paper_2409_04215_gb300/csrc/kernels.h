@@ -54,6 +54,22 @@ cudaError_t gemm_rm(int m, int n, int k, const float *A, const float *B, float *
 // Split-K FP32 GEMM with TwoSum-compensated slices; chunk results (FP64, P [S][m][n]) summed in FP64
 // into C32 (FP32) or C64 (FP64).  S from gemm_splitk_chunks; P must hold S*m*n doubles.
 int gemm_splitk_chunks(int m, int n, int k, int sm_count);
+cudaError_t splitk_reduce(int S, size_t mn, const double *P, float *C32, double *C64, cudaStream_t st);
+
+// ---- tensor-core one-body apply (tc_gemm.cu): split-K 3xTF32 tcgen05 GEMM ----
+struct alignas(64) TcMap {
+    unsigned char bytes[128];  // an encoded CUtensorMap
+};
+bool make_tc_map(TcMap &out, const float *ptr, int rows, int ld, int box_rows);
+int tc_gemm_bn(int m);
+int tc_gemm_chunks(int m, int n, int k, int sm_count);
+int tc_gemm_sz(int k, int S);
+cudaError_t tc_gemm(const TcMap &b_hi, const TcMap &b_lo, const TcMap &a_hi, const TcMap &a_lo, int m, int n, int k,
+                    int S, double *P, int *err, cudaStream_t st);
+cudaError_t split_tf32(const float *src, int rows, int cols, int ld_src, float *hi, float *lo, int ld_dst,
+                       cudaStream_t st);
+cudaError_t split_tf32_transpose(const float *src, int rows, int cols, float *hi, float *lo, int ld_dst,
+                                 cudaStream_t st);
 cudaError_t gemm_splitk(int m, int n, int k, int S, const float *A, const float *B, double *P, float *C32,
                         double *C64, cudaStream_t st, bool trans_b = false);  // trans_b: B stored [n][k]
 cudaError_t gemm_rm64(int m, int n, int k, const double *A, const double *B, double *C, cudaStream_t st);

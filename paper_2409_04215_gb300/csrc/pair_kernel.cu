@@ -620,6 +620,14 @@ template <int NRHS, int TP, int NT>
 struct PackedStokesRegB5 : PackedStokesReg<NRHS, TP, NT> {
     static constexpr int MINB = 5;
 };
+template <int NRHS, int TP, int NT>
+struct PackedStokesB4 : PackedStokes<NRHS, TP, NT> {
+    static constexpr int MINB = 4;
+};
+template <int NRHS, int TP, int NT>
+struct PackedStokesB5 : PackedStokes<NRHS, TP, NT> {
+    static constexpr int MINB = 5;
+};
 
 template <class Pol, int NT, int MINB = Pol::MINB>
 __global__ void __launch_bounds__(NT, MINB) pair_sum_kernel(PairGeom geo, PairWork work, int *err) {
@@ -876,6 +884,9 @@ static int occupancy_variant() {
     P(PackedStokesReg, 2, 1, 128) \
     P(PackedStokesReg, 4, 1, 128) \
     P(PackedStokes, 1, 2, 128)    \
+    P(PackedStokesB4, 1, 2, 128)  \
+    P(PackedStokesB5, 1, 2, 128)  \
+    P(PackedStokesB4, 1, 3, 128)  \
     P(PackedStokes, 1, 2, 256)    \
     P(PackedStokes, 1, 3, 128)    \
     P(PackedStokes, 2, 1, 128)    \

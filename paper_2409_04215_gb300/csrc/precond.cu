@@ -437,6 +437,12 @@ __global__ void splitk_reduce_kernel(int S, size_t mn, const double *__restrict_
     }
 }
 
+cudaError_t splitk_reduce(int S, size_t mn, const double *P, float *C32, double *C64, cudaStream_t st) {
+    if (mn == 0) return cudaSuccess;
+    splitk_reduce_kernel<<<(unsigned)std::min<size_t>((mn + 255) / 256, 4096), 256, 0, st>>>(S, mn, P, C32, C64);
+    return cudaGetLastError();
+}
+
 int gemm_splitk_chunks(int m, int n, int k, int sm_count) {
     const long long tiles = (long long)((n + 63) / 64) * ((m + 63) / 64);
     long long s = (4LL * sm_count + tiles - 1) / tiles;  // about four resident waves of CTAs

@@ -39,11 +39,14 @@ def test_library_exports_every_declared_symbol(lib_path):
 def test_library_loads_and_reports(lib_path):
     from paper_2409_04215_gb300.api import EXPORTED, Options, load_library
 
+    from paper_2409_04215_gb300.api import ABI_VERSION
+
     lib = load_library(lib_path)
-    assert lib.mfs_abi_version() == 1
+    assert lib.mfs_abi_version() == ABI_VERSION
     o = Options()
     lib.mfs_default_options(o)
     assert o.mu == 1.0 and o.gmres_tol == 1e-7 and o.max_rhs == 4 and o.precision == 0
+    assert o.tensor_cores == 0 and o.autotune == 1 and o.profile == 0
     assert set(EXPORTED) == set(_declared())
 
 
@@ -58,3 +61,30 @@ def test_setup_rejects_bad_input_without_gpu(lib_path):
     rc = lib.mfs_setup(ctypes.byref(out), 1, None, 1, None, None, None, None)
     assert rc == 1  # MFS_ERR_INVALID_ARG
     assert b"invalid" in lib.mfs_setup_error()
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors have the header's field offsets and sizes (a C probe compiled with gcc)."""
+    import ctypes
+
+    from paper_2409_04215_gb300.api import Options, _Bodies, _Info, _PointSet
+
+    mirrors = {"mfs_options": Options, "mfs_solve_info": _Info, "mfs_bodies": _Bodies, "mfs_pointset": _PointSet}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "mfs.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        cname, field, val = line.split()
+        got[(cname, field)] = int(val)
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
