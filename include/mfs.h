@@ -82,8 +82,11 @@ typedef struct {
     int32_t max_rhs;   /* largest nrhs any later call will use (1..4); default 4 */
     int32_t profile;   /* 1: bracket every pair-kernel launch with CUDA events (no host sync) and report
                           their summed device time in mfs_solve_info.ms_pairs; default 0 */
-    int32_t tensor_cores; /* 1: precision-0 one-body apply on the tensor cores (tcgen05, split 3xTF32 products,
-                             FP32 accumulation in short K chunks summed in FP64); 0: CUDA-core split-K GEMM */
+    int32_t tensor_cores; /* precision-0 one-body apply (Eq. pseudo) on the tensor cores (tcgen05 TF32 MMAs,
+                             FP32 accumulation over short K runs, sums in FP64), operands cut from FP64 into
+                             TF32 pieces: 1 = three pieces, six products (FP32-level products);
+                             2 = two pieces, three products (3xTF32, ~2^-21 products);
+                             0 = CUDA-core split-K FP32 GEMM (TwoSum-compensated slices).  Default 1 */
 } mfs_options;
 
 typedef struct {

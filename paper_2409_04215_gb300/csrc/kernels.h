@@ -56,20 +56,36 @@ cudaError_t gemm_rm(int m, int n, int k, const float *A, const float *B, float *
 int gemm_splitk_chunks(int m, int n, int k, int sm_count);
 cudaError_t splitk_reduce(int S, size_t mn, const double *P, float *C32, double *C64, cudaStream_t st);
 
-// ---- tensor-core one-body apply (tc_gemm.cu): split-K 3xTF32 tcgen05 GEMM ----
+// ---- tensor-core one-body apply (tc_gemm.cu): split-K multi-piece TF32 tcgen05 GEMM ----
 struct alignas(64) TcMap {
     unsigned char bytes[128];  // an encoded CUtensorMap
 };
+struct TcOperands {  // kernel parameter: TF32 pieces of the factor (b) and of the columns (a)
+    TcMap b[3];
+    TcMap a[3];
+};
+// 2-D FP32 tensor [rows][ld], ld % 32 == 0, box 32 x box_rows, 128-byte swizzle; false if not encodable.
 bool make_tc_map(TcMap &out, const float *ptr, int rows, int ld, int box_rows);
-int tc_gemm_bn(int m);
-int tc_gemm_chunks(int m, int n, int k, int sm_count);
+int tc_gemm_bn(int m, int pieces);
+int tc_gemm_chunks(int m, int n, int k, int sm_count, int pieces);
 int tc_gemm_sz(int k, int S);
-cudaError_t tc_gemm(const TcMap &b_hi, const TcMap &b_lo, const TcMap &a_hi, const TcMap &a_lo, int m, int n, int k,
-                    int S, double *P, int *err, cudaStream_t st);
-cudaError_t split_tf32(const float *src, int rows, int cols, int ld_src, float *hi, float *lo, int ld_dst,
-                       cudaStream_t st);
-cudaError_t split_tf32_transpose(const float *src, int rows, int cols, float *hi, float *lo, int ld_dst,
-                                 cudaStream_t st);
+// P[z][m][n] = sum_{k in chunk z} A[m][k] B[n][k] as (hi, lo) float pairs, from `pieces` (2 or 3) TF32
+// pieces of each operand (maps b[0..pieces), a[0..pieces)); S from tc_gemm_chunks, P holds
+// tc_gemm_sz(k, S) * m * n pairs.
+cudaError_t tc_gemm(int pieces, const TcMap *b, const TcMap *a, int m, int n, int k, int S, float2 *P, int *err,
+                    cudaStream_t st);
+// FP64 [rows][cols] -> pieces dst[p][cols][ld_dst] (transposed, zero K padding), p at offset p * pstride.
+cudaError_t split_pieces_transpose(const double *src, int rows, int cols, float *dst, int ld_dst, size_t pstride,
+                                   int pieces, cudaStream_t st);
+// sum_z P[z] ([rows][cols], (hi, lo) pairs, double-float sums) -> pieces dst[p][rows][ld_dst].
+cudaError_t reduce_pieces(int S, int rows, int cols, const float2 *P, float *dst, int ld_dst, size_t pstride,
+                          int pieces, cudaStream_t st);
+// sum_z P[z] ((hi, lo) pairs, double-float sums) -> C (FP64), mn entries.
+cudaError_t reduce_f64(int S, size_t mn, const float2 *P, double *C, cudaStream_t st);
+// gather_rotate with the FP64 values written as pieces dst[p][ncols][ld_dst].
+cudaError_t gather_rotate_pieces(int D, const double *gamma, int sum_MD, const int *col_body, const int *col_rhs,
+                                 const int *body_tgt_off, const double *rot, int ncols, int dM, float *dst, int ld_dst,
+                                 size_t pstride, int pieces, cudaStream_t st);
 cudaError_t gemm_splitk(int m, int n, int k, int S, const float *A, const float *B, double *P, float *C32,
                         double *C64, cudaStream_t st, bool trans_b = false);  // trans_b: B stored [n][k]
 cudaError_t gemm_rm64(int m, int n, int k, const double *A, const double *B, double *C, cudaStream_t st);

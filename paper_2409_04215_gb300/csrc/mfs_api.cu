@@ -50,14 +50,16 @@ struct ShapeHost {
     double *Pk = nullptr;                              // split-K chunk results
     size_t Pk_count = 0;
     double *O64 = nullptr, *PkT = nullptr;             // adjoint: transposed-apply output and chunks
-    // tensor-core apply: K-major TF32 (hi, lo) factors, activations, tensor maps
+    // tensor-core apply: K-major TF32 pieces of the factors and the columns, tensor maps
     bool tc_ready = false;
+    int pieces = 0;        // TF32 pieces per operand (3: 6xTF32 products, 2: 3xTF32)
     int ld1 = 0, ld2 = 0;  // K extents padded to 32: roundup(dM, 32), roundup(r, 32)
-    float *Ut_h = nullptr, *Ut_l = nullptr, *Wpt_h = nullptr, *Wpt_l = nullptr, *Wrt_h = nullptr, *Wrt_l = nullptr;
-    float *Ah = nullptr, *Al = nullptr, *Th = nullptr, *Tl = nullptr;
-    double *Ptc = nullptr;
-    TcMap mUh, mUl, mWph, mWpl, mWrh, mWrl;
-    std::map<int, std::array<TcMap, 4>> amaps;  // per column count: Ah, Al, Th, Tl
+    float *Utp = nullptr, *Wptp = nullptr, *Wrtp = nullptr;  // [piece][r or dN][ld]
+    float *Ap = nullptr, *Tp = nullptr;                      // [piece][columns][ld1 or ld2]
+    size_t ut_stride = 0, wt_stride = 0, ap_stride = 0, tp_stride = 0;
+    float2 *Ptc = nullptr;  // chunk results as (hi, lo) pairs
+    TcMap mU[3], mWp[3], mWr[3];
+    std::map<int, std::array<TcMap, 6>> amaps;  // per column count: A pieces, T pieces
     double *A64 = nullptr, *T64 = nullptr, *L64 = nullptr;
     ShapeDev dev{};
 };
@@ -513,35 +515,36 @@ mfs_status precond_apply_dev(mfs_ctx *ctx, const double *gamma, double *lambda, 
             CK(gemm_rm64(ncols, sd.dN, sd.r, sh.T64, project ? sd.Wp64 : sd.Wr64, sh.L64, st));
             CK(scatter_rotate(D, nullptr, sh.L64, sh.col_body, sh.col_rhs, ctx->src_off_d, ctx->rot_d, ctx->rot64_d,
                               ncols, sd.dN, ctx->sumN, lambda, st));
-        } else if (sh.tc_ready) {  // tensor cores: 3xTF32 tcgen05 GEMMs, FP32 chunk sums added in FP64
-            CK(gather_rotate(D, gamma, ctx->sumM * D, sh.col_body, sh.col_rhs, ctx->tgt_off_d, ctx->rot64_d, ncols,
-                             sd.dM, sh.A, nullptr, st));
+        } else if (sh.tc_ready) {  // tensor cores: multi-piece TF32 tcgen05 GEMMs, double-float chunk sums
+            const int np = sh.pieces;
             auto it = sh.amaps.find(ncols);
             if (it == sh.amaps.end()) {
-                std::array<TcMap, 4> mp;
-                const int bn = tc_gemm_bn(ncols);
-                if (!make_tc_map(mp[0], sh.Ah, ncols, sh.ld1, bn) || !make_tc_map(mp[1], sh.Al, ncols, sh.ld1, bn) ||
-                    !make_tc_map(mp[2], sh.Th, ncols, sh.ld2, bn) || !make_tc_map(mp[3], sh.Tl, ncols, sh.ld2, bn)) {
+                std::array<TcMap, 6> mp;
+                const int bn = tc_gemm_bn(ncols, np);
+                bool enc = true;
+                for (int p = 0; p < np; ++p)
+                    enc = enc && make_tc_map(mp[p], sh.Ap + p * sh.ap_stride, ncols, sh.ld1, bn) &&
+                          make_tc_map(mp[3 + p], sh.Tp + p * sh.tp_stride, ncols, sh.ld2, bn);
+                if (!enc) {
                     ctx->last_error = "tensor-map encoding for the tensor-core apply failed";
                     return MFS_ERR_CUDA;
                 }
                 it = sh.amaps.emplace(ncols, mp).first;
             }
-            const std::array<TcMap, 4> &mp = it->second;
-            // t = U^T g  (FP32 result, Eq. pseudo)
-            const int S1 = tc_gemm_chunks(ncols, sd.r, sd.dM, ctx->sm_count);
-            CK(split_tf32(sh.A, ncols, sd.dM, sd.dM, sh.Ah, sh.Al, sh.ld1, st));
-            CK(tc_gemm(sh.mUh, sh.mUl, mp[0], mp[1], ncols, sd.r, sd.dM, S1, sh.Ptc, ctx->err_d, st));
-            CK(splitk_reduce(tc_gemm_sz(sd.dM, S1), (size_t)ncols * sd.r, sh.Ptc, sh.Tm, nullptr, st));
+            const std::array<TcMap, 6> &mp = it->second;
+            // t = U^T g (Eq. pseudo): gathered columns as pieces, chunk sums re-cut into pieces of t
+            CK(gather_rotate_pieces(D, gamma, ctx->sumM * D, sh.col_body, sh.col_rhs, ctx->tgt_off_d, ctx->rot64_d,
+                                    ncols, sd.dM, sh.Ap, sh.ld1, sh.ap_stride, np, st));
+            const int S1 = tc_gemm_chunks(ncols, sd.r, sd.dM, ctx->sm_count, np);
+            CK(tc_gemm(np, sh.mU, mp.data(), ncols, sd.r, sd.dM, S1, sh.Ptc, ctx->err_d, st));
+            CK(reduce_pieces(tc_gemm_sz(sd.dM, S1), ncols, sd.r, sh.Ptc, sh.Tp, sh.ld2, sh.tp_stride, np, st));
             // lambda = W t, kept in FP64
-            const int S2 = tc_gemm_chunks(ncols, sd.dN, sd.r, ctx->sm_count);
-            CK(split_tf32(sh.Tm, ncols, sd.r, sd.r, sh.Th, sh.Tl, sh.ld2, st));
-            CK(tc_gemm(project ? sh.mWph : sh.mWrh, project ? sh.mWpl : sh.mWrl, mp[2], mp[3], ncols, sd.dN, sd.r, S2,
-                       sh.Ptc, ctx->err_d, st));
-            CK(splitk_reduce(tc_gemm_sz(sd.r, S2), (size_t)ncols * sd.dN, sh.Ptc, nullptr, sh.L64, st));
+            const int S2 = tc_gemm_chunks(ncols, sd.dN, sd.r, ctx->sm_count, np);
+            CK(tc_gemm(np, project ? sh.mWp : sh.mWr, mp.data() + 3, ncols, sd.dN, sd.r, S2, sh.Ptc, ctx->err_d, st));
+            CK(reduce_f64(tc_gemm_sz(sd.r, S2), (size_t)ncols * sd.dN, sh.Ptc, sh.L64, st));
             CK(scatter_rotate(D, nullptr, sh.L64, sh.col_body, sh.col_rhs, ctx->src_off_d, ctx->rot_d, ctx->rot64_d,
                               ncols, sd.dN, ctx->sumN, lambda, st));
-            ctx->launches += 6;
+            ctx->launches += 2;
         } else {
             CK(gather_rotate(D, gamma, ctx->sumM * D, sh.col_body, sh.col_rhs, ctx->tgt_off_d, ctx->rot64_d, ncols,
                              sd.dM, sh.A, nullptr, st));
@@ -811,7 +814,7 @@ void mfs_default_options(mfs_options *opt) {
     opt->autotune = 1;
     opt->max_rhs = 4;
     opt->profile = 0;
-    opt->tensor_cores = 0;
+    opt->tensor_cores = 1;
 }
 
 int32_t mfs_abi_version(void) { return MFS_ABI_VERSION; }
@@ -1082,7 +1085,8 @@ static mfs_status setup_impl(mfs_ctx *ctx, mfs_kind kind, const mfs_bodies *bodi
         // apply factors
         bool ok = ctx->alloc(&sd.U, (size_t)m * n) == cudaSuccess && ctx->alloc(&sd.Wp, (size_t)n * n) == cudaSuccess &&
                   ctx->alloc(&sd.Wr, (size_t)n * n) == cudaSuccess;
-        if (ok && ctx->opt.precision >= 1)
+        const bool want_tc = ctx->opt.tensor_cores != 0 && ctx->opt.precision == 0;
+        if (ok && (ctx->opt.precision >= 1 || want_tc))  // the tensor-core pieces are cut from FP64 factors
             ok = ctx->alloc(&sd.U64, (size_t)m * n) == cudaSuccess &&
                  ctx->alloc(&sd.Wp64, (size_t)n * n) == cudaSuccess &&
                  ctx->alloc(&sd.Wr64, (size_t)n * n) == cudaSuccess;
@@ -1128,48 +1132,57 @@ static mfs_status setup_impl(mfs_ctx *ctx, mfs_kind kind, const mfs_bodies *bodi
                 sh.Pk_count = need;
                 ok = ctx->alloc(&sh.Pk, need) == cudaSuccess;
             }
-            if (ok && ctx->opt.tensor_cores && ctx->opt.precision == 0) {
-                // K-major (hi, lo) TF32 factors: U^T [r][ld1], Wp^T and Wr^T [dN][ld2]; zero K padding
+            if (ok && want_tc) {
+                // K-major TF32 pieces: U^T [r][ld1], Wp^T and Wr^T [dN][ld2], from the FP64 factors; zero K padding
+                sh.pieces = ctx->opt.tensor_cores == 2 ? 2 : 3;
+                const int np = sh.pieces;
                 sh.ld1 = (m + 31) / 32 * 32;
                 sh.ld2 = (n + 31) / 32 * 32;
                 const size_t cap = (size_t)R * nb;
+                sh.ut_stride = (size_t)n * sh.ld1;
+                sh.wt_stride = (size_t)n * sh.ld2;
+                sh.ap_stride = cap * sh.ld1;
+                sh.tp_stride = cap * sh.ld2;
                 size_t need = 0;
                 for (int h = 1; h <= R; ++h) {
                     const int cols = h * nb;
-                    need = std::max(need, (size_t)tc_gemm_sz(m, tc_gemm_chunks(cols, n, m, ctx->sm_count)) * cols * n);
-                    need = std::max(need, (size_t)tc_gemm_sz(n, tc_gemm_chunks(cols, n, n, ctx->sm_count)) * cols * n);
+                    need = std::max(need,
+                                    (size_t)tc_gemm_sz(m, tc_gemm_chunks(cols, n, m, ctx->sm_count, np)) * cols * n);
+                    need = std::max(need,
+                                    (size_t)tc_gemm_sz(n, tc_gemm_chunks(cols, n, n, ctx->sm_count, np)) * cols * n);
                 }
-                ok = ctx->alloc(&sh.Ut_h, (size_t)n * sh.ld1) == cudaSuccess &&
-                     ctx->alloc(&sh.Ut_l, (size_t)n * sh.ld1) == cudaSuccess &&
-                     ctx->alloc(&sh.Wpt_h, (size_t)n * sh.ld2) == cudaSuccess &&
-                     ctx->alloc(&sh.Wpt_l, (size_t)n * sh.ld2) == cudaSuccess &&
-                     ctx->alloc(&sh.Wrt_h, (size_t)n * sh.ld2) == cudaSuccess &&
-                     ctx->alloc(&sh.Wrt_l, (size_t)n * sh.ld2) == cudaSuccess &&
-                     ctx->alloc(&sh.Ah, cap * sh.ld1) == cudaSuccess && ctx->alloc(&sh.Al, cap * sh.ld1) == cudaSuccess &&
-                     ctx->alloc(&sh.Th, cap * sh.ld2) == cudaSuccess && ctx->alloc(&sh.Tl, cap * sh.ld2) == cudaSuccess &&
-                     ctx->alloc(&sh.Ptc, need) == cudaSuccess;
+                ok = ctx->alloc(&sh.Utp, np * sh.ut_stride) == cudaSuccess &&
+                     ctx->alloc(&sh.Wptp, np * sh.wt_stride) == cudaSuccess &&
+                     ctx->alloc(&sh.Wrtp, np * sh.wt_stride) == cudaSuccess &&
+                     ctx->alloc(&sh.Ap, np * sh.ap_stride) == cudaSuccess &&
+                     ctx->alloc(&sh.Tp, np * sh.tp_stride) == cudaSuccess && ctx->alloc(&sh.Ptc, need) == cudaSuccess;
                 if (ok) {
-                    // padding columns of the activations stay zero: the splits write the whole padded rows
-                    ok = cudaMemsetAsync(sh.Ah, 0, sizeof(float) * cap * sh.ld1, st) == cudaSuccess &&
-                         cudaMemsetAsync(sh.Al, 0, sizeof(float) * cap * sh.ld1, st) == cudaSuccess &&
-                         cudaMemsetAsync(sh.Th, 0, sizeof(float) * cap * sh.ld2, st) == cudaSuccess &&
-                         cudaMemsetAsync(sh.Tl, 0, sizeof(float) * cap * sh.ld2, st) == cudaSuccess &&
-                         split_tf32_transpose(sd.U, m, n, sh.Ut_h, sh.Ut_l, sh.ld1, st) == cudaSuccess &&
-                         split_tf32_transpose(sd.Wp, n, n, sh.Wpt_h, sh.Wpt_l, sh.ld2, st) == cudaSuccess &&
-                         split_tf32_transpose(sd.Wr, n, n, sh.Wrt_h, sh.Wrt_l, sh.ld2, st) == cudaSuccess;
+                    // the padding columns of the column pieces stay zero: the kernels write only the first dM / r
+                    ok = cudaMemsetAsync(sh.Ap, 0, sizeof(float) * np * sh.ap_stride, st) == cudaSuccess &&
+                         cudaMemsetAsync(sh.Tp, 0, sizeof(float) * np * sh.tp_stride, st) == cudaSuccess &&
+                         split_pieces_transpose(sd.U64, m, n, sh.Utp, sh.ld1, sh.ut_stride, np, st) == cudaSuccess &&
+                         split_pieces_transpose(sd.Wp64, n, n, sh.Wptp, sh.ld2, sh.wt_stride, np, st) == cudaSuccess &&
+                         split_pieces_transpose(sd.Wr64, n, n, sh.Wrtp, sh.ld2, sh.wt_stride, np, st) == cudaSuccess &&
+                         cudaStreamSynchronize(st) == cudaSuccess;
                 }
                 if (ok) {
                     const int box = 128;  // factor rows per CTA (MMA M)
-                    sh.tc_ready = make_tc_map(sh.mUh, sh.Ut_h, n, sh.ld1, box) &&
-                                  make_tc_map(sh.mUl, sh.Ut_l, n, sh.ld1, box) &&
-                                  make_tc_map(sh.mWph, sh.Wpt_h, n, sh.ld2, box) &&
-                                  make_tc_map(sh.mWpl, sh.Wpt_l, n, sh.ld2, box) &&
-                                  make_tc_map(sh.mWrh, sh.Wrt_h, n, sh.ld2, box) &&
-                                  make_tc_map(sh.mWrl, sh.Wrt_l, n, sh.ld2, box);
-                    if (!sh.tc_ready) {
+                    bool enc = true;
+                    for (int p = 0; p < np; ++p)
+                        enc = enc && make_tc_map(sh.mU[p], sh.Utp + p * sh.ut_stride, n, sh.ld1, box) &&
+                              make_tc_map(sh.mWp[p], sh.Wptp + p * sh.wt_stride, n, sh.ld2, box) &&
+                              make_tc_map(sh.mWr[p], sh.Wrtp + p * sh.wt_stride, n, sh.ld2, box);
+                    if (!enc) {
                         fail("tensor-map encoding for the tensor-core apply failed", MFS_ERR_CUDA);
                         break;
                     }
+                    sh.tc_ready = true;
+                }
+                if (ok && ctx->opt.precision == 0) {  // the FP64 factors were only the source of the pieces
+                    ctx->release(sd.U64);
+                    ctx->release(sd.Wp64);
+                    ctx->release(sd.Wr64);
+                    sd.U64 = sd.Wp64 = sd.Wr64 = nullptr;
                 }
             }
             if (!ok) {

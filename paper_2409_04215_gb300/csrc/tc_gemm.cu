@@ -1,20 +1,28 @@
-// One-body apply on the 5th-generation tensor cores: split-K 3xTF32 GEMM with tcgen05.
+// One-body apply on the 5th-generation tensor cores: split-K multi-piece TF32 GEMM with tcgen05.
 //
-//   P[z][m][n] = sum_{k in chunk z} A[m][k] B[n][k]   (both operands K-major, FP32 in memory)
+//   P[z][m][n] = sum_{k in chunk z} A[m][k] B[n][k]   (both operands K-major, FP32 pieces in memory)
 //
-// Each operand x is held as hi = tf32(x) and lo = x - hi; the product is formed as
-// hi*hi + hi*lo + lo*hi by three tcgen05.mma.kind::tf32 per K step, accumulated in FP32 in tensor
-// memory (TMEM).  The factor (B: U^T or W^T of the one-body SVD, Eq. pseudo) is the MMA's M side
-// (128 rows per CTA), the gathered columns (A) its N side (<= 256), so few columns still fill the
-// 128-row MMA.  K is split over CTAs (grid.z) in chunks of a few hundred, and the FP32 chunk results
-// are summed in FP64 afterwards (the same reduction as the CUDA-core split-K path), which keeps the
-// FP32 accumulation short.
+// Every operand value x (an FP64 number) is stored as TF32 pieces, x ~ x0 + x1 (+ x2), each piece
+// the round-to-nearest TF32 value of what the earlier pieces leave over.  Two pieces hold x to about
+// 2^-22 and the product is formed from the three terms of order >= 2^-11 (3xTF32); three pieces hold
+// it to about 2^-33 and the product keeps the six terms of order >= 2^-22 (6xTF32).  Each term is one
+// tcgen05.mma.kind::tf32 per K step of 8, accumulated in FP32 in tensor memory (TMEM).  Plain FP32
+// accumulation, not the product split, limits the accuracy, so the accumulations are kept short:
+// the leading term x0*y0 goes to one of up to four "main" accumulators in turn (one per K stage), the
+// correction terms (2^-11 smaller, so their rounding is negligible) to a separate one, the epilogue
+// adds them with TwoSum into a (hi, lo) float pair, and K is split over CTAs (grid.z) in chunks of a
+// few hundred whose pairs are summed in double-float arithmetic afterwards.  No FP64 arithmetic runs
+// on the way (GB300's FP64 rate is a small fraction of its FP32 rate).
+//
+// The factor (B: U^T or W^T of the one-body SVD, Eq. pseudo) is the MMA's M side (128 rows per CTA),
+// the gathered columns (A) its N side (<= 256), so a handful of bodies still fills the 128-row MMA.
 //
 // Per CTA (128 threads): warp 0 lane 0 issues TMA loads (cp.async.bulk.tensor, 128-byte swizzle)
 // into a two-stage ring, warp 1 lane 0 issues the MMAs and commits each stage back to the loader,
-// warp 2 owns the TMEM allocation, and all four warps read the 128 x N accumulator with tcgen05.ld
-// (warp w reads TMEM lanes 32w..32w+31) and write FP64 partials.  Every wait is bounded; on a
-// timeout the CTA agrees (block vote), records an error flag, frees its TMEM and returns.
+// warp 2 owns the TMEM allocation, and all four warps read the accumulators with tcgen05.ld (warp w
+// reads TMEM lanes 32w..32w+31) and write the (hi, lo) partials.  Every wait is bounded; on a timeout the
+// CTA records an error flag, waits for the MMAs it issued, agrees (block vote), frees its TMEM and
+// returns.
 #include <cuda.h>
 
 #include <cstring>
@@ -25,10 +33,10 @@
 namespace mfs {
 
 namespace tc {
-constexpr int BM = 128;            // factor rows per CTA (MMA M)
-constexpr int BK = 32;             // K elements per stage (128 bytes: one swizzle row)
+constexpr int BM = 128;              // factor rows per CTA (MMA M)
+constexpr int BK = 32;               // K elements per stage (128 bytes: one swizzle row)
 constexpr int STAGES = 2;
-constexpr int A_TILE = BM * BK * 4;  // bytes of one 128 x 32 FP32 tile (16 KB)
+constexpr int B_TILE = BM * BK * 4;  // bytes of one 128 x 32 FP32 factor tile (16 KB)
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     // K-major operand, 128-byte swizzle: start address >> 4 (bits 0-13), leading byte offset unused
@@ -83,22 +91,80 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+
+// The products kept: factor piece fa[t] times column piece fb[t], largest first.
+template <int PIECES>
+struct Terms;
+template <>
+struct Terms<2> {
+    static constexpr int N = 3;
+    __device__ static constexpr int fa(int t) { return t == 2 ? 1 : 0; }
+    __device__ static constexpr int fb(int t) { return t == 1 ? 1 : 0; }
+};
+template <>
+struct Terms<3> {
+    static constexpr int N = 6;  // x0y0, x0y1, x1y0, x1y1, x0y2, x2y0
+    __device__ static constexpr int fa(int t) { return t == 2 || t == 3 ? 1 : (t == 5 ? 2 : 0); }
+    __device__ static constexpr int fb(int t) { return t == 1 || t == 3 ? 1 : (t == 4 ? 2 : 0); }
+};
+
+// (hi, lo) += v exactly up to the final rounding of lo (Knuth's TwoSum on the high part).
+__device__ __forceinline__ void df_add(float &hi, float &lo, float v) {
+    const float s = hi + v;
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (v - bb);
+    hi = s;
+}
+
+// (hi, lo) += (h, l), renormalised (double-float addition).
+__device__ __forceinline__ void df_add2(float &hi, float &lo, float h, float l) {
+    df_add(hi, lo, h);
+    lo += l;
+    const float s = hi + lo;
+    lo = lo - (s - hi);
+    hi = s;
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t t;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(x));
+    return __uint_as_float(t);
+}
+
+// (hi + lo) ~ p[0] + p[1] (+ p[2]) with FP32 arithmetic only: hi - tf32(hi) is exact.
+__device__ __forceinline__ void split_pieces_df(float hi, float lo, int pieces, float *p) {
+    p[0] = tf32_rna(hi);
+    const float rem = (hi - p[0]) + lo;
+    p[1] = tf32_rna(rem);
+    p[2] = pieces == 3 ? tf32_rna(rem - p[1]) : 0.f;
+}
+
+// x ~ p[0] + p[1] (+ p[2]), each the nearest TF32 value of the remainder left by the earlier pieces.
+__device__ __forceinline__ void split_pieces(double x, int pieces, float *p) {
+    double rem = x;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        p[i] = i < pieces ? tf32_rna((float)rem) : 0.f;
+        rem -= (double)p[i];
+    }
+}
 }  // namespace tc
 
-// grid: (ceil(n / 128), ceil(m / BN), chunks); block 128; dynamic smem = STAGES * (2*A_TILE + 2*BN*128) + 1024
+// grid: (ceil(n / 128), ceil(m / BN), chunks); block 128; dynamic smem tc_gemm_smem(BN, PIECES)
+template <int PIECES>
 __global__ void __launch_bounds__(128, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap map_b_hi, const __grid_constant__ CUtensorMap map_b_lo,
-                   const __grid_constant__ CUtensorMap map_a_hi, const __grid_constant__ CUtensorMap map_a_lo, int m,
-                   int n, int k, int kchunk, int BN, int tmem_cols, double *P, int *err) {
+    tc_gemm_kernel(const __grid_constant__ TcOperands ops, int m, int n, int k, int kchunk, int BN, int tmem_cols,
+                   int nacc, float2 *P, int *err) {
     using namespace tc;
+    using TT = Terms<PIECES>;
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
     __shared__ uint32_t tmem_base_sh;
     // 1024-byte aligned tiles (128-byte swizzle atoms are 8 rows x 128 bytes)
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
-    const uint32_t b_tile = A_TILE, a_tile = (uint32_t)BN * BK * 4;
-    const uint32_t stage_bytes = 2 * b_tile + 2 * a_tile;
+    const uint32_t a_tile = (uint32_t)BN * BK * 4;
+    const uint32_t stage_bytes = PIECES * (B_TILE + a_tile);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n0 = blockIdx.x * BM, m0 = blockIdx.y * BN;
     const int kb0 = blockIdx.z * kchunk;
@@ -126,7 +192,7 @@ __global__ void __launch_bounds__(128, 1)
     const uint32_t tmem = tmem_base_sh;
 
     bool ok = true;
-    if (warp == 0 && lane == 0) {  // TMA producer
+    if (warp == 0 && lane == 0) {  // TMA producer: factor pieces, then column pieces, per stage
         for (int i = 0; i < nk && ok; ++i) {
             const int s = i % STAGES;
             if (i >= STAGES) ok = mbar_wait_bounded(&empty_bar[s], (uint32_t)(((i / STAGES) - 1) & 1), err, limit);
@@ -135,15 +201,20 @@ __global__ void __launch_bounds__(128, 1)
             const uint32_t fb = smem_u32(&full_bar[s]);
             mbar_arrive_expect_tx(&full_bar[s], stage_bytes);
             const int kx = kb0 + i * BK;
-            tma_load_2d(st, &map_b_hi, kx, n0, fb);
-            tma_load_2d(st + b_tile, &map_b_lo, kx, n0, fb);
-            tma_load_2d(st + 2 * b_tile, &map_a_hi, kx, m0, fb);
-            tma_load_2d(st + 2 * b_tile + a_tile, &map_a_lo, kx, m0, fb);
+#pragma unroll
+            for (int p = 0; p < PIECES; ++p) {
+                tma_load_2d(st + p * B_TILE, reinterpret_cast<const CUtensorMap *>(&ops.b[p]), kx, n0, fb);
+                tma_load_2d(st + PIECES * B_TILE + p * a_tile, reinterpret_cast<const CUtensorMap *>(&ops.a[p]), kx,
+                            m0, fb);
+            }
         }
     } else if (warp == 1 && lane == 0) {  // MMA issuer
         const uint32_t idesc = instr_desc_tf32(BM, BN);
+        const uint32_t dcorr = tmem + (uint32_t)(BN * nacc);  // correction terms, columns BN * nacc ...
         for (int i = 0; i < nk && ok; ++i) {
             const int s = i % STAGES;
+            // the leading term of stage i goes to main accumulator i % nacc (TMEM columns BN * (i % nacc) ...)
+            const uint32_t dmain = tmem + (uint32_t)(BN * (i % nacc));
             ok = mbar_wait_bounded(&full_bar[s], (uint32_t)((i / STAGES) & 1), err, limit);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -151,11 +222,15 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
             for (int kk = 0; kk < BK / 8; ++kk) {  // 8 TF32 = 32 bytes per MMA K step
                 const uint32_t off = kk * 32;
-                const uint64_t bh = smem_desc(st + off), bl = smem_desc(st + b_tile + off);
-                const uint64_t ah = smem_desc(st + 2 * b_tile + off), al = smem_desc(st + 2 * b_tile + a_tile + off);
-                mma_tf32(tmem, bh, ah, idesc, (i > 0 || kk > 0) ? 1u : 0u);
-                mma_tf32(tmem, bh, al, idesc, 1u);
-                mma_tf32(tmem, bl, ah, idesc, 1u);
+#pragma unroll
+                for (int t = 0; t < TT::N; ++t) {
+                    const uint64_t fdesc = smem_desc(st + TT::fa(t) * B_TILE + off);
+                    const uint64_t cdesc = smem_desc(st + PIECES * B_TILE + TT::fb(t) * a_tile + off);
+                    if (t == 0)
+                        mma_tf32(dmain, fdesc, cdesc, idesc, (i >= nacc || kk > 0) ? 1u : 0u);
+                    else
+                        mma_tf32(dcorr, fdesc, cdesc, idesc, (i > 0 || kk > 0 || t > 1) ? 1u : 0u);
+                }
             }
             mma_commit(smem_u32(&empty_bar[s]));  // stage free once these MMAs have read it
         }
@@ -164,21 +239,31 @@ __global__ void __launch_bounds__(128, 1)
         mma_commit(smem_u32(&done_bar));
     }
     __syncwarp();
-    // everybody: wait for the accumulator (bounded), then agree on success
+    // everybody: wait for the accumulators (bounded), then agree on success
     bool good = mbar_wait_bounded(&done_bar, 0u, err, limit);
     good = __syncthreads_and(good && ok) != 0;
     if (good) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int row = n0 + 32 * warp + lane;  // TMEM lane = factor row
-        double *Pz = P + (size_t)blockIdx.z * m * n;
+        const int used = min(nacc, nk);          // main accumulators written by at least one stage
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+        float2 *Pz = P + (size_t)blockIdx.z * m * n;
         for (int c0 = 0; c0 < BN; c0 += 16) {
-            float v[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+            float hi[16], lo[16];
+            tc::tmem_ld16(lane_base + (uint32_t)(BN * nacc + c0), hi);  // corrections first (smallest)
+#pragma unroll
+            for (int i = 0; i < 16; ++i) lo[i] = 0.f;
+            for (int a = 0; a < used; ++a) {
+                float v[16];
+                tc::tmem_ld16(lane_base + (uint32_t)(BN * a + c0), v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) tc::df_add(hi[i], lo[i], v[i]);
+            }
             if (row < n) {
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     const int col = m0 + c0 + i;
-                    if (col < m) Pz[(size_t)col * n + row] = (double)v[i];
+                    if (col < m) Pz[(size_t)col * n + row] = make_float2(hi[i], lo[i]);
                 }
             }
         }
@@ -189,57 +274,123 @@ __global__ void __launch_bounds__(128, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
 }
 
-__device__ __forceinline__ float tf32_rna(float x) {
-    uint32_t t;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(x));
-    return __uint_as_float(t);
-}
-
-// hi = tf32(x), lo = tf32(x - hi) (round to nearest, ties away), rows x cols from a [rows][ld_src] array
-// into [rows][ld_dst] arrays with zero padding columns cols..ld_dst.
-__global__ void split_tf32_kernel(const float *src, int rows, int cols, int ld_src, float *hi, float *lo, int ld_dst) {
-    const size_t total = (size_t)rows * ld_dst;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const int r = (int)(i / ld_dst), c = (int)(i % ld_dst);
-        float h = 0.f, l = 0.f;
-        if (c < cols) {
-            const float x = src[(size_t)r * ld_src + c];
-            h = tf32_rna(x);
-            l = tf32_rna(x - h);
-        }
-        hi[i] = h;
-        lo[i] = l;
-    }
-}
-
-// Transposed split: dst[c][r] from src[r][c] (a factor stored [k][n] becomes K-major [n][k]).
-__global__ void split_tf32_transpose_kernel(const float *src, int rows, int cols, float *hi, float *lo, int ld_dst) {
-    // src [rows][cols] -> dst [cols][ld_dst] with dst[c][r] = src[r][c]
+// ---------------------------------------------------------------------------
+// Operand pieces
+// ---------------------------------------------------------------------------
+// dst[p][c][r] = piece p of src[r][c] (an FP64 factor stored [rows][cols] becomes K-major [cols][ld_dst]);
+// columns rows..ld_dst of each piece are zero.
+__global__ void split_pieces_transpose_kernel(const double *src, int rows, int cols, float *dst, int ld_dst,
+                                              size_t pstride, int pieces) {
     const size_t total = (size_t)cols * ld_dst;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const int c = (int)(i / ld_dst), r = (int)(i % ld_dst);
-        float h = 0.f, l = 0.f;
-        if (r < rows) {
-            const float x = src[(size_t)r * cols + c];
-            h = tf32_rna(x);
-            l = tf32_rna(x - h);
-        }
-        hi[i] = h;
-        lo[i] = l;
+        float p[3] = {0.f, 0.f, 0.f};
+        if (r < rows) tc::split_pieces(src[(size_t)r * cols + c], pieces, p);  // zero K padding otherwise
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            if (q < pieces) dst[q * pstride + i] = p[q];
     }
 }
 
-cudaError_t split_tf32(const float *src, int rows, int cols, int ld_src, float *hi, float *lo, int ld_dst,
-                       cudaStream_t st) {
-    if (rows == 0) return cudaSuccess;
-    split_tf32_kernel<<<1024, 256, 0, st>>>(src, rows, cols, ld_src, hi, lo, ld_dst);
+// Double-float sum over the chunks of P[z] = (hi, lo) pairs, [rows][cols].
+__device__ __forceinline__ void df_chunk_sum(int S, size_t mn, size_t i, const float2 *__restrict__ P, float &hi,
+                                             float &lo) {
+    hi = 0.f;
+    lo = 0.f;
+    for (int z = 0; z < S; ++z) {
+        const float2 v = P[(size_t)z * mn + i];
+        tc::df_add2(hi, lo, v.x, v.y);
+    }
+}
+
+// C = sum_z P[z], written as pieces dst[p][row][col] (leading dimension ld_dst).
+__global__ void reduce_pieces_kernel(int S, int rows, int cols, const float2 *__restrict__ P, float *dst, int ld_dst,
+                                     size_t pstride, int pieces) {
+    const size_t mn = (size_t)rows * cols;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < mn; i += (size_t)gridDim.x * blockDim.x) {
+        float hi, lo, p[3];
+        df_chunk_sum(S, mn, i, P, hi, lo);
+        tc::split_pieces_df(hi, lo, pieces, p);
+        const size_t o = (i / cols) * ld_dst + (i % cols);
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            if (q < pieces) dst[q * pstride + o] = p[q];
+    }
+}
+
+// C = sum_z P[z] as FP64.
+__global__ void reduce_f64_kernel(int S, size_t mn, const float2 *__restrict__ P, double *C) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < mn; i += (size_t)gridDim.x * blockDim.x) {
+        float hi, lo;
+        df_chunk_sum(S, mn, i, P, hi, lo);
+        C[i] = (double)hi + (double)lo;
+    }
+}
+
+// Gather and rotate into the body frame (as gather_rotate), written directly as pieces
+// dst[p][col][ld_dst] of the FP64 values.
+__global__ void gather_rotate_pieces_kernel(int D, const double *gamma, int sum_MD, const int *col_body,
+                                            const int *col_rhs, const int *body_tgt_off, const double *rot, int ncols,
+                                            int dM, float *dst, int ld_dst, size_t pstride, int pieces) {
+    const int col = blockIdx.y;
+    const int M = dM / D;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= M || col >= ncols) return;
+    const int k = col_body[col], h = col_rhs[col];
+    const double *gk = gamma + (size_t)h * sum_MD + (size_t)body_tgt_off[k] * D;
+    float q[3];
+    float *out = dst + (size_t)col * ld_dst;
+    if (D == 1) {
+        tc::split_pieces(gk[p], pieces, q);
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            if (j < pieces) out[j * pstride + p] = q[j];
+    } else {
+        const double *R = rot + 9 * k;  // row-major R; (R^T g)_a = sum_b R[b][a] g_b
+        const double g0 = gk[3 * p], g1 = gk[3 * p + 1], g2 = gk[3 * p + 2];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            tc::split_pieces(R[a] * g0 + R[3 + a] * g1 + R[6 + a] * g2, pieces, q);
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                if (j < pieces) out[j * pstride + 3 * p + a] = q[j];
+        }
+    }
+}
+
+cudaError_t split_pieces_transpose(const double *src, int rows, int cols, float *dst, int ld_dst, size_t pstride,
+                                   int pieces, cudaStream_t st) {
+    if (cols == 0) return cudaSuccess;
+    if (pieces < 2 || pieces > 3) return cudaErrorInvalidValue;
+    split_pieces_transpose_kernel<<<1024, 256, 0, st>>>(src, rows, cols, dst, ld_dst, pstride, pieces);
     return cudaGetLastError();
 }
 
-cudaError_t split_tf32_transpose(const float *src, int rows, int cols, float *hi, float *lo, int ld_dst,
-                                 cudaStream_t st) {
-    if (cols == 0) return cudaSuccess;
-    split_tf32_transpose_kernel<<<1024, 256, 0, st>>>(src, rows, cols, hi, lo, ld_dst);
+cudaError_t reduce_pieces(int S, int rows, int cols, const float2 *P, float *dst, int ld_dst, size_t pstride,
+                          int pieces, cudaStream_t st) {
+    const size_t mn = (size_t)rows * cols;
+    if (mn == 0) return cudaSuccess;
+    if (pieces < 2 || pieces > 3) return cudaErrorInvalidValue;
+    reduce_pieces_kernel<<<(unsigned)std::min<size_t>((mn + 255) / 256, 4096), 256, 0, st>>>(S, rows, cols, P, dst,
+                                                                                               ld_dst, pstride, pieces);
+    return cudaGetLastError();
+}
+
+cudaError_t reduce_f64(int S, size_t mn, const float2 *P, double *C, cudaStream_t st) {
+    if (mn == 0) return cudaSuccess;
+    reduce_f64_kernel<<<(unsigned)std::min<size_t>((mn + 255) / 256, 4096), 256, 0, st>>>(S, mn, P, C);
+    return cudaGetLastError();
+}
+
+cudaError_t gather_rotate_pieces(int D, const double *gamma, int sum_MD, const int *col_body, const int *col_rhs,
+                                 const int *body_tgt_off, const double *rot, int ncols, int dM, float *dst, int ld_dst,
+                                 size_t pstride, int pieces, cudaStream_t st) {
+    if (ncols == 0) return cudaSuccess;
+    if (pieces < 2 || pieces > 3) return cudaErrorInvalidValue;
+    const int M = dM / D;
+    dim3 grid((M + 127) / 128, ncols);
+    gather_rotate_pieces_kernel<<<grid, 128, 0, st>>>(D, gamma, sum_MD, col_body, col_rhs, body_tgt_off, rot, ncols,
+                                                       dM, dst, ld_dst, pstride, pieces);
     return cudaGetLastError();
 }
 
@@ -269,8 +420,10 @@ static EncodeTiledFn encode_fn() {
 
 // 2-D FP32 tensor [rows][ld] (ld a multiple of 32), box 32 x box_rows, 128-byte swizzle, zero fill.
 bool make_tc_map(TcMap &out, const float *ptr, int rows, int ld, int box_rows) {
+    static_assert(sizeof(CUtensorMap) == sizeof(TcMap), "tensor map size");
     EncodeTiledFn fn = encode_fn();
-    if (!fn || !ptr || ld % 32 != 0 || box_rows < 8 || box_rows > 256 || (reinterpret_cast<uintptr_t>(ptr) & 15))
+    if (!fn || !ptr || rows < 1 || ld % 32 != 0 || box_rows < 8 || box_rows > 256 ||
+        (reinterpret_cast<uintptr_t>(ptr) & 15))
         return false;
     CUtensorMap m;
     std::memset(&m, 0, sizeof(m));
@@ -282,57 +435,89 @@ bool make_tc_map(TcMap &out, const float *ptr, int rows, int ld, int box_rows) {
            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return false;
-    static_assert(sizeof(CUtensorMap) == sizeof(TcMap), "tensor map size");
     std::memcpy(&out, &m, sizeof(m));
     return true;
 }
 
-int tc_gemm_bn(int m) {  // MMA N: columns per CTA, a multiple of 16, at most 256
+int tc_gemm_bn(int m, int pieces) {  // MMA N: columns per CTA, a multiple of 16; 128 at most for 3 pieces
+    const int cap = pieces == 3 ? 128 : 256;
     const int b = ((m + 15) / 16) * 16;
-    return b > 256 ? 256 : (b < 16 ? 16 : b);
+    return b > cap ? cap : (b < 16 ? 16 : b);
 }
 
-int tc_gemm_chunks(int m, int n, int k, int sm_count) {
-    const int tiles = ((n + tc::BM - 1) / tc::BM) * ((m + tc_gemm_bn(m) - 1) / tc_gemm_bn(m));
+int tc_gemm_chunks(int m, int n, int k, int sm_count, int pieces) {
+    const int bn = tc_gemm_bn(m, pieces);
+    const int tiles = ((n + tc::BM - 1) / tc::BM) * ((m + bn - 1) / bn);
     int s = (2 * sm_count + tiles - 1) / tiles;  // about two CTAs per SM in total
     const int smax = (k + 255) / 256;            // chunks of at least 256 K
     if (s > smax) s = smax;
     return s < 1 ? 1 : s;
 }
 
-size_t tc_gemm_smem(int BN) { return (size_t)tc::STAGES * (2 * tc::A_TILE + 2 * (size_t)BN * tc::BK * 4) + 1024; }
-
-// C partials P[z][m][n] = sum_{k in chunk z} A[m][k] B[n][k], A and B given as (hi, lo) tensor maps.
-cudaError_t tc_gemm(const TcMap &b_hi, const TcMap &b_lo, const TcMap &a_hi, const TcMap &a_lo, int m, int n, int k,
-                    int S, double *P, int *err, cudaStream_t st) {
-    if (m == 0 || n == 0) return cudaSuccess;
-    if (k <= 0 || S <= 0) return cudaErrorInvalidValue;
-    const int BN = tc_gemm_bn(m);
-    int cols = 32;
-    while (cols < BN) cols <<= 1;
-    const int kchunk = ((k + S - 1) / S + tc::BK - 1) / tc::BK * tc::BK;
-    const int Sz = (k + kchunk - 1) / kchunk;
-    const size_t smem = tc_gemm_smem(BN);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)tc_gemm_smem(256));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    dim3 grid((n + tc::BM - 1) / tc::BM, (m + BN - 1) / BN, Sz);
-    CUtensorMap mb_hi, mb_lo, ma_hi, ma_lo;
-    std::memcpy(&mb_hi, &b_hi, sizeof(mb_hi));
-    std::memcpy(&mb_lo, &b_lo, sizeof(mb_lo));
-    std::memcpy(&ma_hi, &a_hi, sizeof(ma_hi));
-    std::memcpy(&ma_lo, &a_lo, sizeof(ma_lo));
-    tc_gemm_kernel<<<grid, 128, smem, st>>>(mb_hi, mb_lo, ma_hi, ma_lo, m, n, k, kchunk, BN, cols, P, err);
-    return cudaGetLastError();
+size_t tc_gemm_smem(int BN, int pieces) {
+    return (size_t)tc::STAGES * pieces * (tc::B_TILE + (size_t)BN * tc::BK * 4) + 1024;
 }
 
 int tc_gemm_sz(int k, int S) {
     const int kchunk = ((k + S - 1) / S + tc::BK - 1) / tc::BK * tc::BK;
     return (k + kchunk - 1) / kchunk;
+}
+
+// FP32 accumulators of BN columns (at most 4 main ones and the correction one) such that the CTAs
+// resident on one SM together allocate
+// no more than its 512 TMEM columns (an allocation beyond that would wait for a neighbour to finish).
+template <int PIECES>
+static cudaError_t tc_layout(int BN, int &nacc, int &cols) {
+    static int cache[17] = {0};  // resident CTAs per SM, by BN / 16
+    static bool attr = false;
+    if (!attr) {  // the largest tile's shared memory, once: every BN then launches under it
+        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<PIECES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)tc_gemm_smem(tc_gemm_bn(1 << 20, PIECES), PIECES));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const size_t smem = tc_gemm_smem(BN, PIECES);
+    int &resident = cache[BN / 16];
+    if (resident == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, tc_gemm_kernel<PIECES>, 128, smem);
+        if (e != cudaSuccess) return e;
+        if (resident < 1) return cudaErrorInvalidConfiguration;
+    }
+    int cols_max = 512;
+    while (cols_max * resident > 512) cols_max >>= 1;
+    nacc = cols_max / BN - 1;  // main accumulators; one more holds the correction terms
+    if (nacc > 4) nacc = 4;
+    if (nacc < 1) return cudaErrorInvalidConfiguration;
+    cols = 32;
+    while (cols < (nacc + 1) * BN) cols <<= 1;
+    return cudaSuccess;
+}
+
+template <int PIECES>
+static cudaError_t tc_gemm_launch(const TcMap *b, const TcMap *a, int m, int n, int k, int S, float2 *P, int *err,
+                                  cudaStream_t st) {
+    const int BN = tc_gemm_bn(m, PIECES);
+    int nacc = 1, cols = 32;
+    cudaError_t e = tc_layout<PIECES>(BN, nacc, cols);
+    if (e != cudaSuccess) return e;
+    const int kchunk = ((k + S - 1) / S + tc::BK - 1) / tc::BK * tc::BK;
+    const int Sz = (k + kchunk - 1) / kchunk;
+    TcOperands ops;
+    std::memset(&ops, 0, sizeof(ops));
+    std::memcpy(ops.b, b, PIECES * sizeof(TcMap));
+    std::memcpy(ops.a, a, PIECES * sizeof(TcMap));
+    dim3 grid((n + tc::BM - 1) / tc::BM, (m + BN - 1) / BN, Sz);
+    tc_gemm_kernel<PIECES><<<grid, 128, tc_gemm_smem(BN, PIECES), st>>>(ops, m, n, k, kchunk, BN, cols, nacc, P, err);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_gemm(int pieces, const TcMap *b, const TcMap *a, int m, int n, int k, int S, float2 *P, int *err,
+                    cudaStream_t st) {
+    if (m == 0 || n == 0) return cudaSuccess;
+    if (k <= 0 || S <= 0) return cudaErrorInvalidValue;
+    if (pieces == 2) return tc_gemm_launch<2>(b, a, m, n, k, S, P, err, st);
+    if (pieces == 3) return tc_gemm_launch<3>(b, a, m, n, k, S, P, err, st);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace mfs

@@ -46,7 +46,7 @@ def test_library_loads_and_reports(lib_path):
     o = Options()
     lib.mfs_default_options(o)
     assert o.mu == 1.0 and o.gmres_tol == 1e-7 and o.max_rhs == 4 and o.precision == 0
-    assert o.tensor_cores == 0 and o.autotune == 1 and o.profile == 0
+    assert o.tensor_cores == 1 and o.autotune == 1 and o.profile == 0
     assert set(EXPORTED) == set(_declared())
 
 

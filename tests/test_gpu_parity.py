@@ -91,9 +91,10 @@ def test_pair_sum(kind, include_self, nrhs):
         assert _rel(u[h].reshape(-1), ref) < 1e-6
 
 
+@pytest.mark.parametrize("tensor_cores", [0, 1])
 @pytest.mark.parametrize("kind", ["stokes", "laplace"])
 @pytest.mark.parametrize("smooth", [True, False])
-def test_precond_apply_backward(kind, smooth):
+def test_precond_apply_backward(kind, smooth, tensor_cores):
     """S_L^(k) (lambda_gpu - lambda_oracle) is small: the FP32 two-step apply is backward stable (Eq. pseudo).
 
     smooth: gamma is the field that the other bodies induce on each body (what GMRES feeds the
@@ -104,7 +105,7 @@ def test_precond_apply_backward(kind, smooth):
     (Eq. 2esysprec), and test_matvec holds the matvec to 1e-6.
     """
     wl = _mixed(kind)
-    ctx = _ctx(wl)
+    ctx = _ctx(wl, tensor_cores=tensor_cores)
     pr = Problem(wl)
     rng = np.random.default_rng(3)
     bodies = list(range(pr.P))
@@ -133,11 +134,12 @@ def test_precond_apply_backward(kind, smooth):
             assert abs(lk.sum()) < 1e-5 * np.abs(lk).sum()
 
 
+@pytest.mark.parametrize("tensor_cores", [0, 1])
 @pytest.mark.parametrize("kind", ["stokes", "laplace"])
 @pytest.mark.parametrize("nrhs", [1, 4])
-def test_matvec(kind, nrhs):
+def test_matvec(kind, nrhs, tensor_cores):
     wl = _mixed(kind, nsusp=2)
-    ctx = _ctx(wl)
+    ctx = _ctx(wl, tensor_cores=tensor_cores)
     pr = Problem(wl)
     rng = np.random.default_rng(5)
     gam = rng.standard_normal((nrhs, ctx.sum_M, pr.d))

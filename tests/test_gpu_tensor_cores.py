@@ -1,7 +1,10 @@
-"""Tensor-core one-body apply (tensor_cores = 1: tcgen05 3xTF32 GEMMs) against the FP64 oracle.
+"""Tensor-core one-body apply (tcgen05 TF32 GEMMs on operand pieces) against the FP64 oracle.
 
-The same bars as the CUDA-core path: the apply is backward stable to 1e-5 on a smooth field
-(Eq. pseudo), the matvec within 1e-6 and solved velocities within 1e-5 (relative 2-norms).
+tensor_cores = 1 (three TF32 pieces, six products: FP32-level products) meets the bars of the
+CUDA-core path: the apply is backward stable to 1e-5 on a smooth field (Eq. pseudo), the matvec
+is within 1e-6 and solved velocities within 1e-5 (relative 2-norms).  tensor_cores = 2 (two
+pieces, three products: 3xTF32, products to ~2^-21) is held to 3e-5 and 3e-6 on the first two
+and to the same 1e-5 on solutions.
 Sizes are ragged for the GEMM tiles: K = dM not a multiple of 32 (zero-padded K), factor rows
 dN not a multiple of 128, column counts (bodies x rhs) not a multiple of 16 and above 256 (two
 column tiles, the second ragged).
@@ -46,11 +49,16 @@ def _backward_err(pr, bodies, lam, gam):
     return worst
 
 
+BACKWARD_TOL = {1: 1e-5, 2: 3e-5}
+MATVEC_TOL = {1: 1e-6, 2: 3e-6}
+
+
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("kind", ["stokes", "laplace"])
 @pytest.mark.parametrize("P,m,n,nrhs", [(7, 150, 75, 1), (7, 150, 75, 3), (150, 64, 30, 4)])
-def test_tc_apply_backward_stable(kind, P, m, n, nrhs):
+def test_tc_apply_backward_stable(kind, P, m, n, nrhs, mode):
     wl = _mixed(kind, P=P, m=m, n=n, seed=31)
-    ctx = _ctx(wl, tensor_cores=1)
+    ctx = _ctx(wl, tensor_cores=mode)
     pr = Problem(wl)
     rng = np.random.default_rng(7)
     bodies = list(range(pr.P))
@@ -61,7 +69,7 @@ def test_tc_apply_backward_stable(kind, P, m, n, nrhs):
     gam = np.stack(gams).reshape(nrhs, -1, pr.d)
     lam = ctx.precond_apply(torch.tensor(gam, device="cuda"), project=False).cpu().numpy().reshape(nrhs, -1)
     for h in range(nrhs):
-        assert _backward_err(pr, bodies, lam[h], gam[h].reshape(-1)) < 1e-5
+        assert _backward_err(pr, bodies, lam[h], gam[h].reshape(-1)) < BACKWARD_TOL[mode]
     # projected apply: zero net charge / force and torque on every body (Sec. 3.3)
     lamp = ctx.precond_apply(torch.tensor(gam, device="cuda"), project=True).cpu().numpy().reshape(nrhs, -1)
     for h in range(nrhs):
@@ -88,11 +96,12 @@ def test_tc_apply_agrees_with_cuda_core_apply():
     b.close()
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("kind", ["stokes", "laplace"])
 @pytest.mark.parametrize("nrhs", [1, 4])
-def test_tc_matvec(kind, nrhs):
+def test_tc_matvec(kind, nrhs, mode):
     wl = _mixed(kind, nsusp=2)
-    ctx = _ctx(wl, tensor_cores=1)
+    ctx = _ctx(wl, tensor_cores=mode)
     pr = Problem(wl)
     gam = np.random.default_rng(5).standard_normal((nrhs, ctx.sum_M, pr.d))
     y = ctx.matvec(torch.tensor(gam, device="cuda")).cpu().numpy()
@@ -100,7 +109,7 @@ def test_tc_matvec(kind, nrhs):
         ref = np.concatenate([pr.matvec(list(pr.suspension_bodies(s)),
                                         gam[h].reshape(-1)[_seg(pr, list(pr.suspension_bodies(s)), "colloc")])
                               for s in range(wl.num_suspensions)])
-        assert _rel(y[h].reshape(-1), ref) < 1e-6
+        assert _rel(y[h].reshape(-1), ref) < MATVEC_TOL[mode]
     ctx.close()
 
 
@@ -127,7 +136,8 @@ def test_tc_solve_elastance_small():
     ctx.close()
 
 
-def test_tc_sphere100_mobility_matches_oracle():
+@pytest.mark.parametrize("mode", [1, 2])
+def test_tc_sphere100_mobility_matches_oracle(mode):
     """The benchmark geometry (100 spheres, M = 1200, N = 600) against the stored FP64 oracle solve."""
     from mfs_inputs import make_workload
     from paper_2409_04215_gb300 import MFS
@@ -135,7 +145,7 @@ def test_tc_sphere100_mobility_matches_oracle():
     g = json.load(open(GOLDEN))
     ref = np.concatenate([np.array(g["U"]), np.array(g["Omega"])], axis=1)
     wl = make_workload("sphere100_mobility")
-    ctx = MFS.from_workload(wl, tensor_cores=1)
+    ctx = MFS.from_workload(wl, tensor_cores=mode)
     U, W, info = ctx.solve_mobility(torch.tensor(wl.F, device="cuda"), torch.tensor(wl.T, device="cuda"))
     got = np.concatenate([U.cpu().numpy()[0], W.cpu().numpy()[0]], axis=1)
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
