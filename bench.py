@@ -49,13 +49,20 @@ THROTTLE_BITS = {
 }
 
 
+# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the pair kernel,
+# the first of a timed solve (cold L2 after the flush), by variant, for the kernel source as captured;
+# a variant not listed reports null.
+PAIR_DRAM_BYTES = {"PackedStokes<1,3,128>": 4845312 + 0}
+
+
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--cpu-sample-bodies", type=int, default=12)
+    ap.add_argument("--cpu-sample-bodies", type=int, default=25,
+                    help="target bodies per step of the oracle arm (--impl reference)")
     ap.add_argument("--small", action="store_true",
                     help="profiling case: 24 spheres with the same M, N and volume fraction (not a bench line)")
     ap.add_argument("--workload", default=WORKLOAD,
@@ -326,8 +333,10 @@ def main():
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = 2 * 128 * sms * 2070e6 / 1e12
     achieved = FLOPS_PER_PAIR * pairs_step * args.steps / (pair_ms / 1e3) / 1e12
+    variant = ctx.pair_variant(wl.nrhs)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "mfs::pair_sum_kernel<3,1,*,*> (Stokeslet, FP32)",
+                "traffic": PAIR_DRAM_BYTES.get(variant), "traffic_unit": "bytes per launch (ncu dram read + write)",
+                "kernel": f"mfs::pair_sum_kernel<{variant}> (Stokeslet, FP32)",
                 "peak_note": f"FP32 FMA: 2 x 128 lanes x {sms} SMs x 2070 MHz (max SM clock)",
                 "avg_launch_ms": pair_ms / pair_launches,
                 "pair_share_of_step": pair_ms / ms}
@@ -360,10 +369,11 @@ def main():
         return
     cpu = None
     if world == 1:
-        pairs_c, times_c, cores, threads, sample = _oracle_sample(wl, args.cpu_sample_bodies, repeats=1)
-        cpu = {"value": pairs_c / times_c[0], "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"FP64 oracle matvec rows of {len(sample)} of 100 target bodies ({pairs_c:.3g} pairs, "
-                         f"{times_c[0]:.1f} s)"}
+        # two full oracle matvecs (all 100 target bodies): about 10 s of host work
+        pairs_c, times_c, cores, threads, sample = _oracle_sample(wl, wl.num_bodies, repeats=2)
+        cpu = {"value": pairs_c * len(times_c) / sum(times_c), "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{len(times_c)} FP64 oracle matvecs, all {len(sample)} target bodies "
+                         f"({pairs_c:.3g} pairs each, {sum(times_c):.1f} s)"}
     line = {
         "metric": METRIC,
         "value": value,

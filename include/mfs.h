@@ -205,6 +205,13 @@ mfs_status mfs_stokeslet_sum_noalloc(const double *targets, int32_t num_targets,
                                      const double *strengths, int32_t num_sources, double mu, double *u,
                                      void *stream);
 
+/* The pair-kernel variant the forward pair sums of this context use for `nrhs` right-hand sides
+ * (1..max_rhs): the autotuner's pick once a solve or matvec with that nrhs has run (autotune = 1),
+ * else the built-in default.  A policy name with its template arguments, e.g.
+ * "PackedStokes<1,3,128>" (rhs, target pairs per thread, threads per CTA).  Never NULL; "" for an
+ * invalid ctx or nrhs.  Static storage.  Not in the paper: a profiling aid. */
+const char *mfs_pair_variant(const mfs_ctx *ctx, int32_t nrhs);
+
 /* Text of the last error on this context (never NULL; "" when none).  Valid until the next call. */
 const char *mfs_last_error(const mfs_ctx *ctx);
 

@@ -43,6 +43,7 @@ EXPORTED = [
     "mfs_solve_mobility",
     "mfs_mobility_vjp",
     "mfs_stokeslet_sum_noalloc",
+    "mfs_pair_variant",
     "mfs_last_error",
     "mfs_setup_error",
     "mfs_destroy",
@@ -144,6 +145,8 @@ def load_library(path: Optional[str] = None):
     lib.mfs_solve_elastance.argtypes = [vp, vp, vp, i32, ctypes.POINTER(_Info), vp]
     lib.mfs_solve_mobility.argtypes = [vp, vp, vp, vp, vp, i32, ctypes.POINTER(_Info), vp]
     lib.mfs_mobility_vjp.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
+    lib.mfs_pair_variant.argtypes = [vp, i32]
+    lib.mfs_pair_variant.restype = ctypes.c_char_p
     lib.mfs_last_error.argtypes = [vp]
     lib.mfs_last_error.restype = ctypes.c_char_p
     lib.mfs_setup_error.restype = ctypes.c_char_p
@@ -285,6 +288,9 @@ class MFS:
         return torch.empty(shape, dtype=torch.float64, device=dev)
 
     # -- entry points (same names as the C ABI) ------------------------------------------
+    def pair_variant(self, nrhs: int = 1) -> str:
+        return self._lib.mfs_pair_variant(self._ctx, int(nrhs)).decode()
+
     def update_centers(self, centres, stream=None):
         a = _Arg(centres)
         self._check(self._lib.mfs_update_centers(self._ctx, a.ptr, _stream_ptr(stream, a.device)))

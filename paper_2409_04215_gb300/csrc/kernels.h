@@ -11,6 +11,7 @@ struct PairVariant {
     int D, nrhs, T, NT, tile_targets;
     int packed;  // 1: f32x2 Stokes policy with duplicated source records
     int grad;    // 1: centre-gradient kernel of the adjoint (not a pair sum)
+    const char *name;  // policy and template arguments, e.g. "PackedStokes<1,3,128>"
 };
 const PairVariant *pair_variants(int *count);
 int pair_occupancy(int variant);  // resident CTAs per SM

@@ -819,6 +819,15 @@ void mfs_default_options(mfs_options *opt) {
 
 int32_t mfs_abi_version(void) { return MFS_ABI_VERSION; }
 
+const char *mfs_pair_variant(const mfs_ctx *ctx, int32_t nrhs) {
+    if (!ctx || nrhs < 1 || nrhs > 4 || nrhs > ctx->opt.max_rhs) return "";
+    const int tuned = ctx->best_variant[ctx->D == 3][nrhs];
+    const int v = tuned >= 0 ? tuned : default_variant(ctx->D, nrhs);
+    int count = 0;
+    const PairVariant *vv = pair_variants(&count);
+    return (v >= 0 && v < count) ? vv[v].name : "";
+}
+
 const char *mfs_last_error(const mfs_ctx *ctx) { return ctx ? ctx->last_error.c_str() : ""; }
 
 const char *mfs_setup_error(void) { return g_setup_error.c_str(); }

@@ -897,9 +897,9 @@ static int occupancy_variant() {
     G(4, 2, 128)
 
 static const PairVariant kVariants[] = {
-#define S(D_, R_, T_, N_) {D_, R_, T_, N_, N_ * T_, 0, 0},
-#define P(POL_, R_, TP_, N_) {3, R_, 2 * TP_, N_, N_ * 2 * TP_, 1, 0},
-#define G(R_, T_, N_) {3, R_, T_, N_, N_ * T_, 0, 1},
+#define S(D_, R_, T_, N_) {D_, R_, T_, N_, N_ * T_, 0, 0, "Scalar<" #D_ "," #R_ "," #T_ "," #N_ ">"},
+#define P(POL_, R_, TP_, N_) {3, R_, 2 * TP_, N_, N_ * 2 * TP_, 1, 0, #POL_ "<" #R_ "," #TP_ "," #N_ ">"},
+#define G(R_, T_, N_) {3, R_, T_, N_, N_ * T_, 0, 1, "GradStokes<" #R_ "," #T_ "," #N_ ">"},
     MFS_VARIANTS(S, P, G)
 #undef S
 #undef P
