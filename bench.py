@@ -66,7 +66,8 @@ def _args():
     ap.add_argument("--small", action="store_true",
                     help="profiling case: 24 spheres with the same M, N and volume fraction (not a bench line)")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "batched256_mobility", "sphere200_adjoint", "spheroid1000_mobility"],
+                    choices=[WORKLOAD, "batched256_mobility", "sphere200_adjoint", "spheroid1000_mobility",
+                             "sphere100_elastance"],
                     help="secondary measurements (their own JSON line); the default is the benchmark")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="secondary workloads: also time the FP64 reference GPU solve (precision = 1)")
@@ -197,22 +198,34 @@ def secondary(args):
     opts = {"max_iter": 100, "restart": 100} if name == "batched256_mobility" else {}
     ctx = MFS.from_workload(wl, profile=1, **opts)
     setup_s = time.perf_counter() - t0
-    F = torch.tensor(wl.F, device=dev)
-    T = torch.tensor(wl.T, device=dev)
-    for _ in range(args.warmup):
+    laplace = wl.kind == "laplace"
+    if laplace:
+        Q = torch.tensor(wl.Q[None], device=dev)
+    else:
+        F = torch.tensor(wl.F, device=dev)
+        T = torch.tensor(wl.T, device=dev)
+
+    def solve():
+        if laplace:
+            V, info = ctx.solve_elastance(Q)
+            return (V,), info
         U, W, info = ctx.solve_mobility(F, T)
+        return (U, W), info
+
+    for _ in range(args.warmup):
+        out, info = solve()
         if name == "sphere200_adjoint":
-            ctx.mobility_vjp(2.0 * U, torch.zeros_like(W))
+            ctx.mobility_vjp(2.0 * out[0], torch.zeros_like(out[1]))
     torch.cuda.synchronize()
     clocks = Clocks(0)
     infos, vjp_ms = [], []
     for _ in range(args.steps):
-        U, W, info = ctx.solve_mobility(F, T)
+        out, info = solve()
         infos.append(info)
         if name == "sphere200_adjoint":
             torch.cuda.synchronize()
             t1 = time.perf_counter()
-            ctx.mobility_vjp(2.0 * U, torch.zeros_like(W))
+            ctx.mobility_vjp(2.0 * out[0], torch.zeros_like(out[1]))
             torch.cuda.synchronize()
             vjp_ms.append(1e3 * (time.perf_counter() - t1))
     torch.cuda.synchronize()
@@ -222,10 +235,12 @@ def secondary(args):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = 2 * 128 * sms * 2070e6 / 1e12
     pair_ms = sum(i.ms_pairs for i in infos) / len(infos)
-    # algorithmic flops per point pair: the geometry (r, r^2, rsqrt, r^-2: 10) once, then 18 per rhs
-    flops = infos[-1].pairs * (10 + 18 * wl.nrhs)
+    # algorithmic flops per point pair: Stokeslet, the geometry (r, r^2, rsqrt, r^-2: 10) once, then 18
+    # per rhs; Laplace, the geometry (r, r^2, rsqrt: 9) once, then 2 per rhs
+    fpp = (9 + 2 * wl.nrhs) if laplace else (10 + 18 * wl.nrhs)
+    flops = infos[-1].pairs * fpp
     line = {
-        "metric": f"Stokeslet pair-interactions/s ({name})",
+        "metric": f"{'Laplace' if laplace else 'Stokeslet'} pair-interactions/s ({name})",
         "value": pairs / (solve_ms / 1e3),
         "unit": UNIT,
         "n_gpus": 1,
@@ -237,27 +252,40 @@ def secondary(args):
         "data": "synthetic",
         "config": {"workload": wl.description, "bodies": wl.num_bodies, "suspensions": wl.num_suspensions,
                    "nrhs": wl.nrhs, "gmres_tol": 1e-7, **opts},
+        "pair_kernel": ctx.pair_variant(wl.nrhs),
         "setup_s": setup_s,
         "gmres_iters": infos[-1].iters,
         "lanes": infos[-1].lanes,
         "pair_kernel_tflops": flops / (pair_ms / 1e3) / 1e12 if pair_ms > 0 else None,
         "pair_kernel_frac_of_fp32_peak": (flops / (pair_ms / 1e3) / 1e12) / peak if pair_ms > 0 else None,
-        "flops_per_pair": 10 + 18 * wl.nrhs,
+        "flops_per_pair": fpp,
         "gpu_launches": infos[-1].launches,
         "clocks": ck,
     }
     if vjp_ms:
         line["vjp_ms"] = statistics.median(vjp_ms)
     if args.compare_fp64:
-        ref = MFS.from_workload(wl, precision=1, autotune=0, **opts)
+        # the all-FP64 GPU path (precision = 1) on the same problem; for many suspensions on the first
+        # 16 of them (independent problems: the batched solve's rows for those bodies are comparable)
+        sub = wl.first_suspensions(16) if wl.num_suspensions > 16 else wl
+        nb = sub.num_bodies
+        ref = MFS.from_workload(sub, precision=1, autotune=0, **opts)
         t1 = time.perf_counter()
-        Ur, Wr, rinfo = ref.solve_mobility(F, T)
+        if laplace:
+            Vr, rinfo = ref.solve_elastance(torch.tensor(sub.Q[None], device=dev))
+            refs = (Vr,)
+        else:
+            Ur, Wr, rinfo = ref.solve_mobility(torch.tensor(sub.F, device=dev), torch.tensor(sub.T, device=dev))
+            refs = (Ur, Wr)
         torch.cuda.synchronize()
-        got = torch.cat([U, W], dim=-1).cpu().numpy().ravel()
-        refv = torch.cat([Ur, Wr], dim=-1).cpu().numpy().ravel()
-        line["fp64_gpu_solve"] = {"ms": rinfo.ms_solve, "wall_s": time.perf_counter() - t1, "iters": rinfo.iters,
+        got = torch.cat([x[:, :nb].reshape(x.shape[0], -1) for x in out], dim=-1).cpu().numpy().ravel()
+        refv = torch.cat([x.reshape(x.shape[0], -1) for x in refs], dim=-1).cpu().numpy().ravel()
+        ref_rate = rinfo.pairs * sub.nrhs / (rinfo.ms_solve / 1e3)
+        line["fp64_gpu_solve"] = {"workload": sub.description if sub is not wl else "same",
+                                  "ms": rinfo.ms_solve, "wall_s": time.perf_counter() - t1, "iters": rinfo.iters,
+                                  "pairs_per_s": ref_rate,
                                   "rel_diff_fp32_vs_fp64": float(np.linalg.norm(got - refv) / np.linalg.norm(refv)),
-                                  "speedup_fp32_path": rinfo.ms_solve / solve_ms}
+                                  "speedup_fp32_path_pairs_per_s": line["value"] / ref_rate}
     print(json.dumps(line), flush=True)
 
 

@@ -86,6 +86,18 @@ class Workload:
     def num_bodies(self) -> int:
         return int(self.centres.shape[0])
 
+    def first_suspensions(self, k: int) -> "Workload":
+        """The workload restricted to its first k suspensions (bodies [0, body_offsets[k]))."""
+        k = min(k, self.num_suspensions)
+        nb = int(self.body_offsets[k])
+        cut = lambda a: None if a is None else a[..., :nb, :] if a.ndim == 3 else a[:nb]  # noqa: E731
+        return Workload(
+            name=f"{self.name}[:{k}]", kind=self.kind, shapes=self.shapes, centres=self.centres[:nb],
+            quats=None if self.quats is None else self.quats[:nb], shape_id=self.shape_id[:nb],
+            body_offsets=self.body_offsets[: k + 1].copy(), Q=cut(self.Q), F=cut(self.F), T=cut(self.T),
+            mu=self.mu, seed=self.seed, description=f"first {k} suspensions of {self.name}",
+        )
+
     @property
     def num_suspensions(self) -> int:
         return int(len(self.body_offsets) - 1)
@@ -293,6 +305,10 @@ WORKLOADS: dict = {
         }
     ),
     "batched256_mobility": batched_suspensions,
+    # the 100-sphere geometry as an elastance problem (Laplace kernel), Q ~ N(0, 1)
+    "sphere100_elastance": lambda **kw: sphere_suspension(
+        **{"kind": "laplace", "name": "sphere100_elastance", **kw}
+    ),
 }
 
 

@@ -57,6 +57,7 @@ def test_setup_rejects_bad_input_without_gpu(lib_path):
     from paper_2409_04215_gb300.api import load_library
 
     lib = load_library(lib_path)
+    assert lib.mfs_pair_variant(None, 1) == b""
     out = ctypes.c_void_p()
     rc = lib.mfs_setup(ctypes.byref(out), 1, None, 1, None, None, None, None)
     assert rc == 1  # MFS_ERR_INVALID_ARG

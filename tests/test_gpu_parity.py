@@ -188,6 +188,8 @@ def test_solve_mobility_small():
     got = np.concatenate([U.cpu().numpy()[0], W.cpu().numpy()[0]], axis=1)
     assert _rel(got, np.concatenate([Ur, Wr], axis=1)) < 1e-5
     assert info.converged and info.iters > 1
+    # the autotuned pair-kernel policy is reported by name
+    assert ctx.pair_variant(1).startswith(("PackedStokes", "Scalar<3,1,"))
 
 
 def test_solve_mobility_host_buffers():
