@@ -23,9 +23,12 @@ with NumPy/LAPACK and plain-C direct sums (``direct_sum.c``):
 * the preconditioned square system (Eq. 2esysprec): y = gamma + sum_{k' != k}
   S^(kk') (I - L^(k')) S_L^(k')+ gamma^(k'), solved by GMRES from a zero guess
   (Algorithm 1 SOLVE); recovery lambda = S_L^+ gamma and extraction
-  U = -K_N^T lambda (Eq. getU) or phi = -mean(alpha) (Eq. vkal).
+  U = -K_N^T lambda (Eq. getU) or phi = -mean(alpha) (Eq. vkal);
+* the Dirichlet problems, capacitance (Sec. 2.1) and resistance (Sec. 2.2), one-body
+  preconditioned with the pseudo-inverse of the bare self block (Sec. 2.3, Eq. 2sysprec,
+  Algorithm 1), charges q = sum alpha (Eq. qkgauss), forces [f; t] = K_N^T lambda (Eq. force_def).
 
-Readings where the paper is silent or inconsistent (listed in the design doc too):
+Readings where the paper is silent or inconsistent:
 the off-diagonal projector acts on the SOURCE body, L^(k') (as Eq. 2esysprec;
 the block rows of Prop. 3.2 print L^(k)); viscosity mu defaults to 1; the
 truncation eps_trunc defaults to 0 (Sec. 4: no truncation needed in FP64);
@@ -199,6 +202,23 @@ def shape_factors(shape, kind: str, mu: float = 1.0, eps_trunc: float = 0.0) -> 
     return ShapeFactors(kind, S0, L, Lr, SL, U, s, Vt, sinv, KN0, KM0)
 
 
+@dataclasses.dataclass
+class DirichletFactors:
+    """SVD of the bare self block S^(00) = U Sigma V^T of one shape (Sec. 2.3, Eq. pseudo)."""
+
+    U: np.ndarray  # dM x r
+    sigma: np.ndarray  # r
+    Vt: np.ndarray  # r x dN
+    sigma_pinv: np.ndarray  # r, 1/sigma or 0 below sigma_1 * eps_trunc
+
+
+def dirichlet_factors(f: ShapeFactors, eps_trunc: float = 0.0) -> DirichletFactors:
+    U, s, Vt = np.linalg.svd(f.S0, full_matrices=False)
+    keep = s > s[0] * eps_trunc
+    sinv = np.where(keep, 1.0 / np.where(keep, s, 1.0), 0.0)
+    return DirichletFactors(U, s, Vt, sinv)
+
+
 # ---------------------------------------------------------------------------
 # GMRES (Algorithm 1 SOLVE uses GMRES; zero initial guess, no restart)
 # ---------------------------------------------------------------------------
@@ -273,6 +293,8 @@ class Problem:
 
     def __init__(self, wl, eps_trunc: float = 0.0, use_c: bool = True):
         self.wl = wl
+        self.eps_trunc = eps_trunc
+        self._dfactors: Optional[List[DirichletFactors]] = None
         self.kind = wl.kind
         self.d = 1 if wl.kind == "laplace" else 3
         self.mu = float(wl.mu)
@@ -538,6 +560,57 @@ class Problem:
     def surface_field(self, bodies, strengths, targets=None):
         """The representation evaluated at collocation points: all pairs including self."""
         return self.pair_sum(bodies, strengths, include_self=True, target_bodies=targets)
+
+    # -- Dirichlet problems: capacitance (Sec. 2.1) and resistance (Sec. 2.2) -------------
+    #
+    # One-body right preconditioning with the pseudo-inverse of the bare self block S^(kk)
+    # (Sec. 2.3): gamma^(k) = S^(kk) alpha^(k), diagonal blocks replaced by the identity, giving the
+    # square system Eq. 2sysprec with the Dirichlet data as right-hand side; alpha = S^+ gamma after.
+    def dirichlet_factors(self, k: int) -> "DirichletFactors":
+        if self._dfactors is None:
+            self._dfactors = [dirichlet_factors(f, self.eps_trunc) for f in self.factors]
+        return self._dfactors[self.wl.shape_id[k]]
+
+    def pinv_apply_dirichlet(self, k: int, gamma_k: np.ndarray) -> np.ndarray:
+        """S^(kk)+ gamma = R_N V (Sigma^+ (U^T (R_M^T gamma))) from the SVD of S^(00) (Eq. pseudo,
+        Remark congruent: S^(kk) = R_M S^(00) R_N^T for a rotated copy)."""
+        f = self.dirichlet_factors(k)
+        g = self.rotate_points(k, gamma_k, transpose=True)
+        t = f.sigma_pinv * (f.U.T @ g)
+        return self.rotate_points(k, f.Vt.T @ t, transpose=False)
+
+    def matvec_dirichlet(self, bodies: Sequence[int], gamma: np.ndarray) -> np.ndarray:
+        """y = gamma + sum_{k' != k} S^(kk') S^(k'k')+ gamma^(k')  (Eq. 2sysprec; Algorithm 1 MATVEC:
+        the self contribution evaluated and subtracted there is simply never added here)."""
+        g = self.split(bodies, gamma)
+        alpha_hat = [self.pinv_apply_dirichlet(k, gk) for k, gk in zip(bodies, g)]
+        return gamma + np.concatenate(self.pair_sum(bodies, alpha_hat, include_self=False))
+
+    def _solve_dirichlet(self, eta_of, tol: float, max_iter: int):
+        """Algorithm 1 SOLVE per suspension: gamma = GMRES(MATVEC, eta), alpha^(k) = S^(kk)+ gamma^(k)."""
+        strengths: List[Optional[np.ndarray]] = [None] * self.P
+        info = []
+        for s in range(self.wl.num_suspensions):
+            bodies = list(self.suspension_bodies(s))
+            eta = np.concatenate([eta_of(k) for k in bodies])
+            res = gmres(lambda v: self.matvec_dirichlet(bodies, v), eta, tol, max_iter)
+            for k, gk in zip(bodies, self.split(bodies, res.x)):
+                strengths[k] = self.pinv_apply_dirichlet(k, gk)
+            info.append(res)
+        return strengths, info
+
+    def solve_capacitance(self, phi: np.ndarray, tol: float = 1e-12, max_iter: int = 200):
+        """(q, info): net charges of conductors held at potentials phi (P,): eta^(k) = phi^(k) 1_M
+        (Sec. 2.1), q^(k) = sum_j alpha_j^(k) (Eq. qkgauss)."""
+        alpha, info = self._solve_dirichlet(lambda k: np.full(self.X[k].shape[0], float(phi[k])), tol, max_iter)
+        return np.array([a.sum() for a in alpha]), info
+
+    def solve_resistance(self, U: np.ndarray, W: np.ndarray, tol: float = 1e-12, max_iter: int = 200):
+        """(F, T, info) for rigid-body velocities U, W (P, 3): b = K_M [v; omega] (Sec. 2.2, Eq. Kdef,
+        Eq. Kbig), [f; t] = K_N^T lambda (Eq. force_def)."""
+        lam, info = self._solve_dirichlet(lambda k: self.K_M(k) @ np.concatenate([U[k], W[k]]), tol, max_iter)
+        FT = np.array([self.K_N(k).T @ lk for k, lk in enumerate(lam)])
+        return FT[:, :3], FT[:, 3:], info
 
     def assemble_dense(self, bodies: Sequence[int]) -> np.ndarray:
         """Eq. 2esysprec as a dense matrix, with S^(kk') from explicit kernel matrices (tiny problems only)."""
