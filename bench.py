@@ -67,7 +67,7 @@ def _args():
                     help="profiling case: 24 spheres with the same M, N and volume fraction (not a bench line)")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "batched256_mobility", "sphere200_adjoint", "spheroid1000_mobility",
-                             "sphere100_elastance"],
+                             "sphere100_elastance", "sphere100_resistance"],
                     help="secondary measurements (their own JSON line); the default is the benchmark")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="secondary workloads: also time the FP64 reference GPU solve (precision = 1)")
@@ -177,6 +177,75 @@ def reference_arm(args, rank):
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"{len(sample)} of 100 target bodies x 99 source bodies per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def resistance_two_way(args):
+    """Resistance solve on the 100-sphere geometry (timed) and the 2-way error (Eq. 2way): rigid motions
+    U_ref -> forces (resistance, R_p = 0.7) -> velocities (mobility with the proxy offset x 1.05)."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from mfs_inputs import make_workload
+    from mfs_inputs.workloads import sphere_shape
+    from paper_2409_04215_gb300 import MFS
+
+    dev = torch.device("cuda", 0)
+    wl = make_workload(WORKLOAD)
+    rng = np.random.default_rng(21)
+    U_ref = torch.tensor(rng.standard_normal((1, wl.num_bodies, 3)), device=dev)
+    W_ref = torch.tensor(rng.standard_normal((1, wl.num_bodies, 3)), device=dev)
+    t0 = time.perf_counter()
+    ctx = MFS.from_workload(wl, profile=1)
+    F, T, info = ctx.solve_resistance(U_ref, W_ref)  # builds the Dirichlet factors (setup)
+    setup_s = time.perf_counter() - t0
+    for _ in range(max(0, args.warmup - 1)):
+        ctx.solve_resistance(U_ref, W_ref)
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    infos = []
+    for _ in range(args.steps):
+        F, T, info = ctx.solve_resistance(U_ref, W_ref)
+        infos.append(info)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    solve_ms = statistics.median(i.ms_solve for i in infos)
+    pair_ms = sum(i.ms_pairs for i in infos) / len(infos)
+    mob_wl = make_workload(WORKLOAD)
+    mob_wl.shapes = [sphere_shape(1200, 600, rp=1 - 1.05 * 0.3)]
+    mob = MFS.from_workload(mob_wl)
+    U, W, minfo = mob.solve_mobility(F, T)
+    ref = torch.cat([U_ref, W_ref], -1).cpu().numpy()
+    got = torch.cat([U, W], -1).cpu().numpy()
+    two_way = float(np.abs(got - ref).max() / np.abs(ref).max())
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = 2 * 128 * sms * 2070e6 / 1e12
+    tflops = FLOPS_PER_PAIR * infos[-1].pairs / (pair_ms / 1e3) / 1e12 if pair_ms > 0 else None
+    line = {
+        "metric": "Stokeslet pair-interactions/s (sphere100_resistance)",
+        "value": infos[-1].pairs / (solve_ms / 1e3),
+        "unit": UNIT,
+        "n_gpus": 1,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": solve_ms,
+        "higher_is_better": True,
+        "dtype": "f32 pair sums, f64 GMRES",
+        "data": "synthetic (rigid motions U, Omega ~ N(0, 1), seed 21)",
+        "config": {"workload": wl.description + "; resistance problem (Sec. 2.2), GMRES tol 1e-7",
+                   "pair_kernel": ctx.pair_variant(1)},
+        "setup_s": setup_s,
+        "gmres_iters": infos[-1].iters,
+        "pair_kernel_tflops": tflops,
+        "pair_kernel_frac_of_fp32_peak": tflops / peak if tflops else None,
+        "two_way_error": two_way,
+        "two_way": {"R_p_resistance": 0.7, "R_p_mobility": 1 - 1.05 * 0.3, "mobility_iters": minfo.iters,
+                    "norm": "max-norm over the 6P velocities (Eq. 2way)"},
+        "gpu_launches": infos[-1].launches,
+        "clocks": ck,
     }
     print(json.dumps(line), flush=True)
 
@@ -291,6 +360,9 @@ def secondary(args):
 
 def main():
     args = _args()
+    if args.impl == "gpu" and args.workload == "sphere100_resistance":
+        resistance_two_way(args)
+        return
     if args.impl == "gpu" and args.workload != WORKLOAD:
         secondary(args)
         return
@@ -397,8 +469,8 @@ def main():
         return
     cpu = None
     if world == 1:
-        # two full oracle matvecs (all 100 target bodies): about 10 s of host work
-        pairs_c, times_c, cores, threads, sample = _oracle_sample(wl, wl.num_bodies, repeats=2)
+        # four full oracle matvecs (all 100 target bodies): about 12 s of host work
+        pairs_c, times_c, cores, threads, sample = _oracle_sample(wl, wl.num_bodies, repeats=4)
         cpu = {"value": pairs_c * len(times_c) / sum(times_c), "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{len(times_c)} FP64 oracle matvecs, all {len(sample)} target bodies "
                          f"({pairs_c:.3g} pairs each, {sum(times_c):.1f} s)"}

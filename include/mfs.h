@@ -205,6 +205,32 @@ mfs_status mfs_stokeslet_sum_noalloc(const double *targets, int32_t num_targets,
                                      const double *strengths, int32_t num_sources, double mu, double *u,
                                      void *stream);
 
+/*
+ * The Dirichlet problems (Sec. 2): capacitance (Sec. 2.1, Laplace) and resistance (Sec. 2.2, Stokes),
+ * one-body preconditioned with the pseudo-inverse of the bare self block S^(kk) = R_M S^(00) R_N^T
+ * (Sec. 2.3): GMRES on Eq. 2sysprec with the Dirichlet data as right-hand side (Algorithm 1).  The
+ * first call of any of the four functions below computes the extra per-shape SVD of S^(00) (FP64,
+ * on the device) and keeps its apply factors; the precision and tensor_cores options apply as for
+ * the recompleted problems.  Layouts and pointer rules as everywhere in this header.
+ *
+ * mfs_dirichlet_apply -- alpha^(k) = S^(kk)+ gamma^(k) = R_N V Sigma^+ U^T R_M^T gamma^(k)
+ *   (Eq. pseudo, two steps), gamma [nrhs][sum_M][d] -> alpha [nrhs][sum_N][d].
+ * mfs_dirichlet_matvec -- y = gamma + sum_{k' != k} S^(kk') S^(k'k')+ gamma^(k') (Eq. 2sysprec;
+ *   Algorithm 1 MATVEC, self pairs never added instead of subtracted).
+ * mfs_solve_capacitance -- net charges q [nrhs][P] of conductors held at potentials phi [nrhs][P]:
+ *   eta^(k) = phi^(k) 1_M, q^(k) = sum_j alpha_j^(k) (Eq. qkgauss).  Laplace contexts only.
+ * mfs_solve_resistance -- forces F and torques T [nrhs][P][3] (about the body centres) on bodies
+ *   moving rigidly with velocities U and angular velocities Omega [nrhs][P][3]: b = K_M [v; omega]
+ *   (Eq. Kdef, Eq. Kbig), [f; t] = K_N^T lambda (Eq. force_def).  Stokes contexts only.
+ * Errors as for the recompleted solves; info may be NULL.
+ */
+mfs_status mfs_dirichlet_apply(mfs_ctx *ctx, const double *gamma, double *alpha, int32_t nrhs, void *stream);
+mfs_status mfs_dirichlet_matvec(mfs_ctx *ctx, const double *gamma, double *y, int32_t nrhs, void *stream);
+mfs_status mfs_solve_capacitance(mfs_ctx *ctx, const double *phi, double *q, int32_t nrhs, mfs_solve_info *info,
+                                 void *stream);
+mfs_status mfs_solve_resistance(mfs_ctx *ctx, const double *U, const double *Omega, double *F, double *T,
+                                int32_t nrhs, mfs_solve_info *info, void *stream);
+
 /* The pair-kernel variant the forward pair sums of this context use for `nrhs` right-hand sides
  * (1..max_rhs): the autotuner's pick once a solve or matvec with that nrhs has run (autotune = 1),
  * else the built-in default.  A policy name with its template arguments, e.g.

@@ -44,6 +44,10 @@ EXPORTED = [
     "mfs_mobility_vjp",
     "mfs_stokeslet_sum_noalloc",
     "mfs_pair_variant",
+    "mfs_dirichlet_apply",
+    "mfs_dirichlet_matvec",
+    "mfs_solve_capacitance",
+    "mfs_solve_resistance",
     "mfs_last_error",
     "mfs_setup_error",
     "mfs_destroy",
@@ -145,6 +149,10 @@ def load_library(path: Optional[str] = None):
     lib.mfs_solve_elastance.argtypes = [vp, vp, vp, i32, ctypes.POINTER(_Info), vp]
     lib.mfs_solve_mobility.argtypes = [vp, vp, vp, vp, vp, i32, ctypes.POINTER(_Info), vp]
     lib.mfs_mobility_vjp.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
+    lib.mfs_dirichlet_apply.argtypes = [vp, vp, vp, i32, vp]
+    lib.mfs_dirichlet_matvec.argtypes = [vp, vp, vp, i32, vp]
+    lib.mfs_solve_capacitance.argtypes = [vp, vp, vp, i32, ctypes.POINTER(_Info), vp]
+    lib.mfs_solve_resistance.argtypes = [vp, vp, vp, vp, vp, i32, ctypes.POINTER(_Info), vp]
     lib.mfs_pair_variant.argtypes = [vp, i32]
     lib.mfs_pair_variant.restype = ctypes.c_char_p
     lib.mfs_last_error.argtypes = [vp]
@@ -340,6 +348,45 @@ class MFS:
                                            _stream_ptr(stream, q.device))
         self._check(rc, allow_not_converged)
         return V, _info(info, rc)
+
+    # -- Dirichlet problems (Sec. 2): capacitance and resistance ------------------------------
+    def dirichlet_apply(self, gamma, stream=None):
+        a = _Arg(gamma)
+        nrhs = a.obj.shape[0] if a.obj.ndim == 3 else 1
+        shape = (nrhs, self.sum_N, self.d) if a.obj.ndim == 3 else (self.sum_N, self.d)
+        alpha = self._out(shape, a)
+        self._check(self._lib.mfs_dirichlet_apply(self._ctx, a.ptr, alpha.data_ptr(), nrhs,
+                                                  _stream_ptr(stream, a.device)))
+        return alpha
+
+    def dirichlet_matvec(self, gamma, stream=None):
+        a = _Arg(gamma)
+        nrhs = a.obj.shape[0] if a.obj.ndim == 3 else 1
+        y = self._out(tuple(a.obj.shape), a)
+        self._check(self._lib.mfs_dirichlet_matvec(self._ctx, a.ptr, y.data_ptr(), nrhs,
+                                                   _stream_ptr(stream, a.device)))
+        return y
+
+    def solve_capacitance(self, phi, stream=None, allow_not_converged=False):
+        p = _Arg(phi)
+        nrhs = p.obj.shape[0] if p.obj.ndim == 2 else 1
+        q = self._out(tuple(p.obj.shape), p)
+        info = _Info()
+        rc = self._lib.mfs_solve_capacitance(self._ctx, p.ptr, q.data_ptr(), nrhs, ctypes.byref(info),
+                                             _stream_ptr(stream, p.device))
+        self._check(rc, allow_not_converged)
+        return q, _info(info, rc)
+
+    def solve_resistance(self, U, Omega, stream=None, allow_not_converged=False):
+        u, w = _Arg(U), _Arg(Omega)
+        nrhs = u.obj.shape[0] if u.obj.ndim == 3 else 1
+        F = self._out(tuple(u.obj.shape), u)
+        T = self._out(tuple(u.obj.shape), u)
+        info = _Info()
+        rc = self._lib.mfs_solve_resistance(self._ctx, u.ptr, w.ptr, F.data_ptr(), T.data_ptr(), nrhs,
+                                            ctypes.byref(info), _stream_ptr(stream, u.device))
+        self._check(rc, allow_not_converged)
+        return F, T, _info(info, rc)
 
     def mobility_vjp(self, dU, dOmega, want_force_grads: bool = False, stream=None):
         a, b = _Arg(dU), _Arg(dOmega)

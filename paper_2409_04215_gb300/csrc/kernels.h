@@ -38,12 +38,14 @@ struct ShapeDev {
     double sigma1, sigma_min;   // largest / smallest kept singular value
 };
 
-// Build S_L = S0 (I - L) + L_r column-major (dM x dN) in FP64 on the device (Sec. 3.3).
+// Build S_L = S0 (I - L) + L_r column-major (dM x dN) in FP64 on the device (Sec. 3.3); with bare,
+// the self block S0 itself (the Dirichlet problems, Sec. 2.3).
 cudaError_t build_SL(int kind, int M, int N, const double *X0, const double *Y0, double mu, const double *G0inv,
-                     double *SL, cudaStream_t st);
-// From the SVD (U col-major dM x r, sigma, VT col-major r x dN) write the FP32 / FP64 apply factors.
+                     int bare, double *SL, cudaStream_t st);
+// From the SVD (U col-major dM x r, sigma, VT col-major r x dN) write the FP32 / FP64 apply factors;
+// with bare, Wp = Wr = (V Sigma^+)^T (no projector).
 cudaError_t build_apply_factors(int kind, int M, int N, const double *Ucm, const double *sigma, const double *VTcm,
-                                const double *Y0, const double *G0inv, double eps_trunc, ShapeDev &sd,
+                                const double *Y0, const double *G0inv, double eps_trunc, int bare, ShapeDev &sd,
                                 cudaStream_t st);
 
 // Gather: A[col][i] = (R_k^T gamma_k)[i] as FP32 for the columns (body, rhs) of one shape.
@@ -101,10 +103,17 @@ cudaError_t completion_stokes(const double *F, const double *T, int nrhs, int P,
                               const int *body_src_off, int sum_N, double *lam0, cudaStream_t st);
 cudaError_t completion_laplace(const double *Q, int nrhs, int P, const int *body_src_off, int sum_N, double *alpha0,
                                cudaStream_t st);
+// sign -1: velocities (Eq. getU); +1: forces and torques (Eq. force_def).
 cudaError_t extract_stokes(const double *lam, int nrhs, int P, const double *src_local64, const int *body_src_off,
-                           int sum_N, double *U, double *Om, cudaStream_t st);
+                           int sum_N, double *U, double *Om, cudaStream_t st, double sign = -1.0);
+// sum 0: potentials -mean(alpha) (Eq. vkal); 1: net charges sum(alpha) (Eq. qkgauss).
 cudaError_t extract_laplace(const double *alpha, int nrhs, int P, const int *body_src_off, int sum_N, double *V,
-                            cudaStream_t st);
+                            cudaStream_t st, int sum = 0);
+// Dirichlet data: rigid motion K_M U at the collocation points (Sec. 2.2) / phi 1_M (Sec. 2.1).
+cudaError_t dirichlet_rhs_stokes(const double *U, const double *Om, int nrhs, int P, const double *tgt_local64,
+                                 const int *body_tgt_off, int sum_M, double *b, cudaStream_t st);
+cudaError_t dirichlet_rhs_laplace(const double *phi, int nrhs, int P, const int *body_tgt_off, int sum_M, double *b,
+                                  cudaStream_t st);
 
 // ---- GMRES (gmres.cu): L independent lanes, lane l owns vector entries [seg_off[l], seg_off[l+1]) ----
 struct GmresDev {

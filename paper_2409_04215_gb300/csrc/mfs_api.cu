@@ -40,6 +40,16 @@ struct PairPlan {
     size_t partial_bytes = 0, direct_bytes = 0;
 };
 
+// The one-body apply factors of one formulation for one shape, FP32 / FP64 and as tensor-core pieces.
+struct FactorSet {
+    bool built = false;
+    ShapeDev dev{};
+    bool tc_ready = false;
+    float *Utp = nullptr, *Wptp = nullptr, *Wrtp = nullptr;  // [piece][r or dN][ld]
+    size_t ut_stride = 0, wt_stride = 0;
+    TcMap mU[3], mWp[3], mWr[3];
+};
+
 struct ShapeHost {
     int M = 0, N = 0;
     std::vector<double> X0, Y0;  // body frame
@@ -50,24 +60,24 @@ struct ShapeHost {
     double *Pk = nullptr;                              // split-K chunk results
     size_t Pk_count = 0;
     double *O64 = nullptr, *PkT = nullptr;             // adjoint: transposed-apply output and chunks
-    // tensor-core apply: K-major TF32 pieces of the factors and the columns, tensor maps
-    bool tc_ready = false;
+    // tensor-core apply scratch: K-major TF32 pieces of the columns, chunk results
     int pieces = 0;        // TF32 pieces per operand (3: 6xTF32 products, 2: 3xTF32)
     int ld1 = 0, ld2 = 0;  // K extents padded to 32: roundup(dM, 32), roundup(r, 32)
-    float *Utp = nullptr, *Wptp = nullptr, *Wrtp = nullptr;  // [piece][r or dN][ld]
-    float *Ap = nullptr, *Tp = nullptr;                      // [piece][columns][ld1 or ld2]
-    size_t ut_stride = 0, wt_stride = 0, ap_stride = 0, tp_stride = 0;
+    float *Ap = nullptr, *Tp = nullptr;  // [piece][columns][ld1 or ld2]
+    size_t ap_stride = 0, tp_stride = 0;
     float2 *Ptc = nullptr;  // chunk results as (hi, lo) pairs
-    TcMap mU[3], mWp[3], mWr[3];
     std::map<int, std::array<TcMap, 6>> amaps;  // per column count: A pieces, T pieces
     double *A64 = nullptr, *T64 = nullptr, *L64 = nullptr;
-    ShapeDev dev{};
+    // one-body factors per formulation: [0] recompleted S_L (Sec. 3.3), [1] bare self block S^(00)
+    // of the Dirichlet problems (Sec. 2.3), built on first use
+    FactorSet fs[2];
 };
 
 }  // namespace
 
 struct mfs_ctx {
     int kind = 0, D = 1;
+    int fset = 0;  // factor set of the one-body apply: 0 recompleted (Sec. 3.3), 1 bare self block (Sec. 2.3)
     mfs_options opt{};
     int P = 0, S = 0, nshapes = 0;
     std::vector<double> centres, quats;
@@ -507,7 +517,8 @@ mfs_status precond_apply_dev(mfs_ctx *ctx, const double *gamma, double *lambda, 
         const int nb = (int)sh.bodies.size();
         if (nb == 0) continue;
         const int ncols = nb * nrhs;
-        const ShapeDev &sd = sh.dev;
+        const FactorSet &fx = sh.fs[ctx->fset];
+        const ShapeDev &sd = fx.dev;
         if (ctx->opt.precision >= 1) {  // FP64 one-body apply (reference and mixed modes)
             CK(gather_rotate(D, gamma, ctx->sumM * D, sh.col_body, sh.col_rhs, ctx->tgt_off_d, ctx->rot64_d, ncols,
                              sd.dM, sh.A, sh.A64, st));
@@ -515,7 +526,7 @@ mfs_status precond_apply_dev(mfs_ctx *ctx, const double *gamma, double *lambda, 
             CK(gemm_rm64(ncols, sd.dN, sd.r, sh.T64, project ? sd.Wp64 : sd.Wr64, sh.L64, st));
             CK(scatter_rotate(D, nullptr, sh.L64, sh.col_body, sh.col_rhs, ctx->src_off_d, ctx->rot_d, ctx->rot64_d,
                               ncols, sd.dN, ctx->sumN, lambda, st));
-        } else if (sh.tc_ready) {  // tensor cores: multi-piece TF32 tcgen05 GEMMs, double-float chunk sums
+        } else if (fx.tc_ready) {  // tensor cores: multi-piece TF32 tcgen05 GEMMs, double-float chunk sums
             const int np = sh.pieces;
             auto it = sh.amaps.find(ncols);
             if (it == sh.amaps.end()) {
@@ -536,11 +547,11 @@ mfs_status precond_apply_dev(mfs_ctx *ctx, const double *gamma, double *lambda, 
             CK(gather_rotate_pieces(D, gamma, ctx->sumM * D, sh.col_body, sh.col_rhs, ctx->tgt_off_d, ctx->rot64_d,
                                     ncols, sd.dM, sh.Ap, sh.ld1, sh.ap_stride, np, st));
             const int S1 = tc_gemm_chunks(ncols, sd.r, sd.dM, ctx->sm_count, np);
-            CK(tc_gemm(np, sh.mU, mp.data(), ncols, sd.r, sd.dM, S1, sh.Ptc, ctx->err_d, st));
+            CK(tc_gemm(np, fx.mU, mp.data(), ncols, sd.r, sd.dM, S1, sh.Ptc, ctx->err_d, st));
             CK(reduce_pieces(tc_gemm_sz(sd.dM, S1), ncols, sd.r, sh.Ptc, sh.Tp, sh.ld2, sh.tp_stride, np, st));
             // lambda = W t, kept in FP64
             const int S2 = tc_gemm_chunks(ncols, sd.dN, sd.r, ctx->sm_count, np);
-            CK(tc_gemm(np, project ? sh.mWp : sh.mWr, mp.data() + 3, ncols, sd.dN, sd.r, S2, sh.Ptc, ctx->err_d, st));
+            CK(tc_gemm(np, project ? fx.mWp : fx.mWr, mp.data() + 3, ncols, sd.dN, sd.r, S2, sh.Ptc, ctx->err_d, st));
             CK(reduce_f64(tc_gemm_sz(sd.r, S2), (size_t)ncols * sd.dN, sh.Ptc, sh.L64, st));
             CK(scatter_rotate(D, nullptr, sh.L64, sh.col_body, sh.col_rhs, ctx->src_off_d, ctx->rot_d, ctx->rot64_d,
                               ncols, sd.dN, ctx->sumN, lambda, st));
@@ -682,7 +693,7 @@ mfs_status ensure_transposed(mfs_ctx *ctx) {
     for (auto &sh : ctx->shapes) {  // transposed-apply buffers
         const int nb = (int)sh.bodies.size();
         if (nb == 0) continue;
-        const int m = sh.dev.dM, n = sh.dev.dN;
+        const int m = sh.fs[0].dev.dM, n = sh.fs[0].dev.dN;
         size_t need = 0;
         for (int h = 1; h <= R; ++h) {
             const int rows = h * nb;
@@ -730,7 +741,7 @@ mfs_status precondT_dev(mfs_ctx *ctx, const double *z, double *out, int project,
         const int nb = (int)sh.bodies.size();
         if (nb == 0) continue;
         const int ncols = nb * nrhs;
-        const ShapeDev &sd = sh.dev;
+        const ShapeDev &sd = sh.fs[0].dev;
         CK(gather_rotate(3, z, ctx->sumN * 3, sh.col_body, sh.col_rhs, ctx->src_off_d, ctx->rot64_d, ncols, sd.dN,
                          sh.A, nullptr, st));
         const int S1 = gemm_splitk_chunks(ncols, sd.r, sd.dN, ctx->sm_count);
@@ -835,6 +846,198 @@ const char *mfs_setup_error(void) { return g_setup_error.c_str(); }
 void mfs_destroy(mfs_ctx *ctx) { delete ctx; }
 
 }  // extern "C"
+
+// One formulation's one-body factors for shape s: the block (S_L, or the bare S^(00) when set = 1),
+// its thin SVD in FP64 (cuSOLVER gesvd, Eq. pseudo), the FP32 / FP64 apply factors and, for the
+// tensor cores, their TF32 pieces and tensor maps.
+static mfs_status build_shape_factors(mfs_ctx *ctx, cusolverDnHandle_t solver, int s, int set, cudaStream_t st) {
+    ShapeHost &sh = ctx->shapes[s];
+    FactorSet &fx = sh.fs[set];
+    ShapeDev &sd = fx.dev;
+    const int D = ctx->D, kind = ctx->kind;
+    sd.M = sh.M;
+    sd.N = sh.N;
+    sd.dM = D * sh.M;
+    sd.dN = D * sh.N;
+    sd.r = sd.dN;
+    const int m = sd.dM, n = sd.dN;
+    double *X0 = nullptr, *Y0 = nullptr, *G0i = nullptr, *SL = nullptr, *Ucm = nullptr, *sig = nullptr, *VT = nullptr,
+           *work = nullptr;
+    int *info_d = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(X0); cudaFree(Y0); cudaFree(G0i); cudaFree(SL); cudaFree(Ucm); cudaFree(sig); cudaFree(VT);
+        cudaFree(work); cudaFree(info_d);
+    };
+    auto fail = [&](const std::string &msg, mfs_status code) {
+        cleanup();
+        cudaGetLastError();
+        ctx->last_error = msg;
+        return code;
+    };
+    if (cudaMalloc(&X0, sizeof(double) * 3 * sh.M) != cudaSuccess ||
+        cudaMalloc(&Y0, sizeof(double) * 3 * sh.N) != cudaSuccess ||
+        cudaMalloc(&G0i, sizeof(double) * 36) != cudaSuccess ||
+        cudaMalloc(&SL, sizeof(double) * (size_t)m * n) != cudaSuccess ||
+        cudaMalloc(&Ucm, sizeof(double) * (size_t)m * n) != cudaSuccess ||
+        cudaMalloc(&sig, sizeof(double) * n) != cudaSuccess ||
+        cudaMalloc(&VT, sizeof(double) * (size_t)n * n) != cudaSuccess ||
+        cudaMalloc(&info_d, sizeof(int)) != cudaSuccess)
+        return fail("device allocation for the one-body SVD failed", MFS_ERR_OOM);
+    cudaMemcpy(X0, sh.X0.data(), sizeof(double) * 3 * sh.M, cudaMemcpyHostToDevice);
+    cudaMemcpy(Y0, sh.Y0.data(), sizeof(double) * 3 * sh.N, cudaMemcpyHostToDevice);
+    cudaMemcpy(G0i, sh.G0inv, sizeof(double) * 36, cudaMemcpyHostToDevice);
+    cudaError_t ce = build_SL(kind, sh.M, sh.N, X0, Y0, ctx->opt.mu, G0i, set, SL, st);
+    int lwork = 0;
+    if (ce == cudaSuccess && cusolverDnDgesvd_bufferSize(solver, m, n, &lwork) != CUSOLVER_STATUS_SUCCESS)
+        ce = cudaErrorUnknown;
+    if (ce == cudaSuccess) ce = cudaMalloc(&work, sizeof(double) * std::max(lwork, 1));
+    if (ce == cudaSuccess) {
+        signed char jobu = 'S', jobvt = 'S';
+        cusolverStatus_t cs =
+            cusolverDnDgesvd(solver, jobu, jobvt, m, n, SL, m, sig, Ucm, m, VT, n, work, lwork, nullptr, info_d);
+        if (cs != CUSOLVER_STATUS_SUCCESS) ce = cudaErrorUnknown;
+    }
+    int info_h = 0;
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&info_h, info_d, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess || info_h != 0)
+        return fail(std::string("one-body SVD failed: ") + (ce != cudaSuccess ? cudaGetErrorString(ce) : "gesvd info != 0"),
+                    MFS_ERR_CUDA);
+    // apply factors
+    const bool want_tc = ctx->opt.tensor_cores != 0 && ctx->opt.precision == 0;
+    bool ok = ctx->alloc(&sd.U, (size_t)m * n) == cudaSuccess && ctx->alloc(&sd.Wp, (size_t)n * n) == cudaSuccess &&
+              ctx->alloc(&sd.Wr, (size_t)n * n) == cudaSuccess;
+    if (ok && (ctx->opt.precision >= 1 || want_tc))  // the tensor-core pieces are cut from FP64 factors
+        ok = ctx->alloc(&sd.U64, (size_t)m * n) == cudaSuccess && ctx->alloc(&sd.Wp64, (size_t)n * n) == cudaSuccess &&
+             ctx->alloc(&sd.Wr64, (size_t)n * n) == cudaSuccess;
+    if (!ok) return fail("device allocation for the apply factors failed", MFS_ERR_OOM);
+    ce = build_apply_factors(kind, sh.M, sh.N, Ucm, sig, VT, Y0, G0i, ctx->opt.eps_trunc, set, sd, st);
+    cleanup();
+    if (ce != cudaSuccess) {
+        ctx->last_error = std::string("apply factors: ") + cudaGetErrorString(ce);
+        return MFS_ERR_CUDA;
+    }
+    if (!(sd.sigma1 > 0.0) || !std::isfinite(sd.sigma1)) {
+        ctx->last_error = "one-body SVD returned a non-finite or zero largest singular value";
+        return MFS_ERR_ILL_CONDITIONED;
+    }
+    if (want_tc) {
+        // K-major TF32 pieces: U^T [r][ld1], Wp^T and Wr^T [dN][ld2], from the FP64 factors; zero K padding
+        sh.pieces = ctx->opt.tensor_cores == 2 ? 2 : 3;
+        const int np = sh.pieces;
+        sh.ld1 = (m + 31) / 32 * 32;
+        sh.ld2 = (n + 31) / 32 * 32;
+        fx.ut_stride = (size_t)n * sh.ld1;
+        fx.wt_stride = (size_t)n * sh.ld2;
+        ok = ctx->alloc(&fx.Utp, np * fx.ut_stride) == cudaSuccess &&
+             ctx->alloc(&fx.Wptp, np * fx.wt_stride) == cudaSuccess &&
+             ctx->alloc(&fx.Wrtp, np * fx.wt_stride) == cudaSuccess;
+        if (!ok) {
+            ctx->last_error = "device allocation for the tensor-core factors failed";
+            return MFS_ERR_OOM;
+        }
+        CK(split_pieces_transpose(sd.U64, m, n, fx.Utp, sh.ld1, fx.ut_stride, np, st));
+        CK(split_pieces_transpose(sd.Wp64, n, n, fx.Wptp, sh.ld2, fx.wt_stride, np, st));
+        CK(split_pieces_transpose(sd.Wr64, n, n, fx.Wrtp, sh.ld2, fx.wt_stride, np, st));
+        CK(cudaStreamSynchronize(st));
+        const int box = 128;  // factor rows per CTA (MMA M)
+        bool enc = true;
+        for (int p = 0; p < np; ++p)
+            enc = enc && make_tc_map(fx.mU[p], fx.Utp + p * fx.ut_stride, n, sh.ld1, box) &&
+                  make_tc_map(fx.mWp[p], fx.Wptp + p * fx.wt_stride, n, sh.ld2, box) &&
+                  make_tc_map(fx.mWr[p], fx.Wrtp + p * fx.wt_stride, n, sh.ld2, box);
+        if (!enc) {
+            ctx->last_error = "tensor-map encoding for the tensor-core apply failed";
+            return MFS_ERR_CUDA;
+        }
+        fx.tc_ready = true;
+        if (ctx->opt.precision == 0) {  // the FP64 factors were only the source of the pieces
+            ctx->release(sd.U64);
+            ctx->release(sd.Wp64);
+            ctx->release(sd.Wr64);
+            sd.U64 = sd.Wp64 = sd.Wr64 = nullptr;
+        }
+    }
+    fx.built = true;
+    return MFS_OK;
+}
+
+// Column lists and GEMM scratch of one shape's one-body apply (shared by the formulations).
+static mfs_status alloc_apply_scratch(mfs_ctx *ctx, ShapeHost &sh, cudaStream_t st) {
+    const int R = ctx->opt.max_rhs;
+    const int m = sh.fs[0].dev.dM, n = sh.fs[0].dev.dN;
+    const int nb = (int)sh.bodies.size();
+    if (nb == 0) return MFS_OK;
+    std::vector<int> cb(R * nb), cr(R * nb);
+    for (int h = 0; h < R; ++h)
+        for (int i = 0; i < nb; ++i) {
+            cb[h * nb + i] = sh.bodies[i];
+            cr[h * nb + i] = h;
+        }
+    bool ok = ctx->alloc(&sh.col_body, R * nb) == cudaSuccess && ctx->alloc(&sh.col_rhs, R * nb) == cudaSuccess &&
+              ctx->alloc(&sh.A, (size_t)R * nb * m) == cudaSuccess &&
+              ctx->alloc(&sh.Tm, (size_t)R * nb * n) == cudaSuccess &&
+              ctx->alloc(&sh.Lm, (size_t)R * nb * n) == cudaSuccess;
+    if (ok && ctx->opt.precision >= 1)
+        ok = ctx->alloc(&sh.A64, (size_t)R * nb * m) == cudaSuccess &&
+             ctx->alloc(&sh.T64, (size_t)R * nb * n) == cudaSuccess;
+    if (ok) ok = ctx->alloc(&sh.L64, (size_t)R * nb * n) == cudaSuccess;
+    if (ok) {  // split-K chunk results: the largest S * rows * cols over nrhs = 1..R and both GEMMs
+        size_t need = 0;
+        for (int h = 1; h <= R; ++h) {
+            const int rows = h * nb;
+            need = std::max(need, (size_t)gemm_splitk_chunks(rows, n, m, ctx->sm_count) * rows * n);
+            need = std::max(need, (size_t)gemm_splitk_chunks(rows, n, n, ctx->sm_count) * rows * n);
+        }
+        sh.Pk_count = need;
+        ok = ctx->alloc(&sh.Pk, need) == cudaSuccess;
+    }
+    if (ok && sh.pieces > 0) {  // tensor cores: column pieces and chunk results
+        const int np = sh.pieces;
+        const size_t cap = (size_t)R * nb;
+        sh.ap_stride = cap * sh.ld1;
+        sh.tp_stride = cap * sh.ld2;
+        size_t need = 0;
+        for (int h = 1; h <= R; ++h) {
+            const int cols = h * nb;
+            need = std::max(need, (size_t)tc_gemm_sz(m, tc_gemm_chunks(cols, n, m, ctx->sm_count, np)) * cols * n);
+            need = std::max(need, (size_t)tc_gemm_sz(n, tc_gemm_chunks(cols, n, n, ctx->sm_count, np)) * cols * n);
+        }
+        ok = ctx->alloc(&sh.Ap, np * sh.ap_stride) == cudaSuccess &&
+             ctx->alloc(&sh.Tp, np * sh.tp_stride) == cudaSuccess && ctx->alloc(&sh.Ptc, need) == cudaSuccess;
+        // the padding columns of the column pieces stay zero: the kernels write only the first dM / r
+        if (ok)
+            ok = cudaMemsetAsync(sh.Ap, 0, sizeof(float) * np * sh.ap_stride, st) == cudaSuccess &&
+                 cudaMemsetAsync(sh.Tp, 0, sizeof(float) * np * sh.tp_stride, st) == cudaSuccess;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        ctx->last_error = "device allocation for the preconditioner buffers failed";
+        return MFS_ERR_OOM;
+    }
+    CK(cudaMemcpy(sh.col_body, cb.data(), sizeof(int) * cb.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(sh.col_rhs, cr.data(), sizeof(int) * cr.size(), cudaMemcpyHostToDevice));
+    return MFS_OK;
+}
+
+// The Dirichlet formulation's factors (bare self blocks), built on the first capacitance or
+// resistance solve: one more SVD per shape.
+static mfs_status ensure_dirichlet(mfs_ctx *ctx, cudaStream_t st) {
+    bool all = true;
+    for (auto &sh : ctx->shapes) all = all && sh.fs[1].built;
+    if (all) return MFS_OK;
+    cusolverDnHandle_t solver = nullptr;
+    if (cusolverDnCreate(&solver) != CUSOLVER_STATUS_SUCCESS) {
+        ctx->last_error = "cusolverDnCreate failed";
+        return MFS_ERR_CUDA;
+    }
+    cusolverDnSetStream(solver, st);
+    mfs_status status = MFS_OK;
+    for (int s = 0; s < (int)ctx->shapes.size() && status == MFS_OK; ++s)
+        if (!ctx->shapes[s].fs[1].built) status = build_shape_factors(ctx, solver, s, 1, st);
+    cusolverDnDestroy(solver);
+    return status;
+}
 
 static mfs_status setup_impl(mfs_ctx *ctx, mfs_kind kind, const mfs_bodies *bodies, int32_t num_shapes,
                              const mfs_pointset *proxy, const mfs_pointset *colloc, cudaStream_t st) {
@@ -1035,173 +1238,8 @@ static mfs_status setup_impl(mfs_ctx *ctx, mfs_kind kind, const mfs_bodies *bodi
     const int D = ctx->D;
     const int R = ctx->opt.max_rhs;
     mfs_status status = MFS_OK;
-    for (int s = 0; s < num_shapes && status == MFS_OK; ++s) {
-        ShapeHost &sh = ctx->shapes[s];
-        ShapeDev &sd = sh.dev;
-        sd.M = sh.M;
-        sd.N = sh.N;
-        sd.dM = D * sh.M;
-        sd.dN = D * sh.N;
-        sd.r = sd.dN;
-        double *X0 = nullptr, *Y0 = nullptr, *G0i = nullptr, *SL = nullptr, *Ucm = nullptr, *sig = nullptr,
-               *VT = nullptr, *work = nullptr;
-        int *info_d = nullptr;
-        auto cleanup = [&]() {
-            cudaFree(X0); cudaFree(Y0); cudaFree(G0i); cudaFree(SL); cudaFree(Ucm); cudaFree(sig); cudaFree(VT);
-            cudaFree(work); cudaFree(info_d);
-        };
-        auto fail = [&](const std::string &msg, mfs_status code) {
-            ctx->last_error = msg;
-            status = code;
-        };
-        const int m = sd.dM, n = sd.dN;
-        if (cudaMalloc(&X0, sizeof(double) * 3 * sh.M) != cudaSuccess ||
-            cudaMalloc(&Y0, sizeof(double) * 3 * sh.N) != cudaSuccess ||
-            cudaMalloc(&G0i, sizeof(double) * 36) != cudaSuccess ||
-            cudaMalloc(&SL, sizeof(double) * (size_t)m * n) != cudaSuccess ||
-            cudaMalloc(&Ucm, sizeof(double) * (size_t)m * n) != cudaSuccess ||
-            cudaMalloc(&sig, sizeof(double) * n) != cudaSuccess ||
-            cudaMalloc(&VT, sizeof(double) * (size_t)n * n) != cudaSuccess ||
-            cudaMalloc(&info_d, sizeof(int)) != cudaSuccess) {
-            cleanup();
-            cudaGetLastError();
-            fail("device allocation for the one-body SVD failed", MFS_ERR_OOM);
-            break;
-        }
-        cudaMemcpy(X0, sh.X0.data(), sizeof(double) * 3 * sh.M, cudaMemcpyHostToDevice);
-        cudaMemcpy(Y0, sh.Y0.data(), sizeof(double) * 3 * sh.N, cudaMemcpyHostToDevice);
-        cudaMemcpy(G0i, sh.G0inv, sizeof(double) * 36, cudaMemcpyHostToDevice);
-        cudaError_t ce = build_SL(kind, sh.M, sh.N, X0, Y0, ctx->opt.mu, G0i, SL, st);
-        int lwork = 0;
-        if (ce == cudaSuccess && cusolverDnDgesvd_bufferSize(solver, m, n, &lwork) != CUSOLVER_STATUS_SUCCESS)
-            ce = cudaErrorUnknown;
-        if (ce == cudaSuccess) ce = cudaMalloc(&work, sizeof(double) * std::max(lwork, 1));
-        if (ce == cudaSuccess) {
-            signed char jobu = 'S', jobvt = 'S';
-            cusolverStatus_t cs = cusolverDnDgesvd(solver, jobu, jobvt, m, n, SL, m, sig, Ucm, m, VT, n, work, lwork,
-                                                   nullptr, info_d);
-            if (cs != CUSOLVER_STATUS_SUCCESS) ce = cudaErrorUnknown;
-        }
-        int info_h = 0;
-        if (ce == cudaSuccess) ce = cudaMemcpyAsync(&info_h, info_d, sizeof(int), cudaMemcpyDeviceToHost, st);
-        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-        if (ce != cudaSuccess || info_h != 0) {
-            cleanup();
-            fail(std::string("one-body SVD failed: ") + (ce != cudaSuccess ? cudaGetErrorString(ce) : "gesvd info != 0"),
-                 MFS_ERR_CUDA);
-            break;
-        }
-        // apply factors
-        bool ok = ctx->alloc(&sd.U, (size_t)m * n) == cudaSuccess && ctx->alloc(&sd.Wp, (size_t)n * n) == cudaSuccess &&
-                  ctx->alloc(&sd.Wr, (size_t)n * n) == cudaSuccess;
-        const bool want_tc = ctx->opt.tensor_cores != 0 && ctx->opt.precision == 0;
-        if (ok && (ctx->opt.precision >= 1 || want_tc))  // the tensor-core pieces are cut from FP64 factors
-            ok = ctx->alloc(&sd.U64, (size_t)m * n) == cudaSuccess &&
-                 ctx->alloc(&sd.Wp64, (size_t)n * n) == cudaSuccess &&
-                 ctx->alloc(&sd.Wr64, (size_t)n * n) == cudaSuccess;
-        if (!ok) {
-            cleanup();
-            fail("device allocation for the apply factors failed", MFS_ERR_OOM);
-            break;
-        }
-        ce = build_apply_factors(kind, sh.M, sh.N, Ucm, sig, VT, Y0, G0i, ctx->opt.eps_trunc, sd, st);
-        cleanup();
-        if (ce != cudaSuccess) {
-            fail(std::string("apply factors: ") + cudaGetErrorString(ce), MFS_ERR_CUDA);
-            break;
-        }
-        if (!(sd.sigma1 > 0.0) || !std::isfinite(sd.sigma1)) {
-            fail("one-body SVD returned a non-finite or zero largest singular value", MFS_ERR_ILL_CONDITIONED);
-            break;
-        }
-        // GEMM column lists and buffers
-        const int nb = (int)sh.bodies.size();
-        std::vector<int> cb(R * nb), cr(R * nb);
-        for (int h = 0; h < R; ++h)
-            for (int i = 0; i < nb; ++i) {
-                cb[h * nb + i] = sh.bodies[i];
-                cr[h * nb + i] = h;
-            }
-        if (nb > 0) {
-            ok = ctx->alloc(&sh.col_body, R * nb) == cudaSuccess && ctx->alloc(&sh.col_rhs, R * nb) == cudaSuccess &&
-                 ctx->alloc(&sh.A, (size_t)R * nb * m) == cudaSuccess &&
-                 ctx->alloc(&sh.Tm, (size_t)R * nb * n) == cudaSuccess &&
-                 ctx->alloc(&sh.Lm, (size_t)R * nb * n) == cudaSuccess;
-            if (ok && ctx->opt.precision >= 1)
-                ok = ctx->alloc(&sh.A64, (size_t)R * nb * m) == cudaSuccess &&
-                     ctx->alloc(&sh.T64, (size_t)R * nb * n) == cudaSuccess;
-            if (ok) ok = ctx->alloc(&sh.L64, (size_t)R * nb * n) == cudaSuccess;
-            if (ok) {  // split-K chunk results: the largest S * rows * cols over nrhs = 1..R and both GEMMs
-                size_t need = 0;
-                for (int h = 1; h <= R; ++h) {
-                    const int rows = h * nb;
-                    need = std::max(need, (size_t)gemm_splitk_chunks(rows, n, m, ctx->sm_count) * rows * n);
-                    need = std::max(need, (size_t)gemm_splitk_chunks(rows, n, n, ctx->sm_count) * rows * n);
-                }
-                sh.Pk_count = need;
-                ok = ctx->alloc(&sh.Pk, need) == cudaSuccess;
-            }
-            if (ok && want_tc) {
-                // K-major TF32 pieces: U^T [r][ld1], Wp^T and Wr^T [dN][ld2], from the FP64 factors; zero K padding
-                sh.pieces = ctx->opt.tensor_cores == 2 ? 2 : 3;
-                const int np = sh.pieces;
-                sh.ld1 = (m + 31) / 32 * 32;
-                sh.ld2 = (n + 31) / 32 * 32;
-                const size_t cap = (size_t)R * nb;
-                sh.ut_stride = (size_t)n * sh.ld1;
-                sh.wt_stride = (size_t)n * sh.ld2;
-                sh.ap_stride = cap * sh.ld1;
-                sh.tp_stride = cap * sh.ld2;
-                size_t need = 0;
-                for (int h = 1; h <= R; ++h) {
-                    const int cols = h * nb;
-                    need = std::max(need,
-                                    (size_t)tc_gemm_sz(m, tc_gemm_chunks(cols, n, m, ctx->sm_count, np)) * cols * n);
-                    need = std::max(need,
-                                    (size_t)tc_gemm_sz(n, tc_gemm_chunks(cols, n, n, ctx->sm_count, np)) * cols * n);
-                }
-                ok = ctx->alloc(&sh.Utp, np * sh.ut_stride) == cudaSuccess &&
-                     ctx->alloc(&sh.Wptp, np * sh.wt_stride) == cudaSuccess &&
-                     ctx->alloc(&sh.Wrtp, np * sh.wt_stride) == cudaSuccess &&
-                     ctx->alloc(&sh.Ap, np * sh.ap_stride) == cudaSuccess &&
-                     ctx->alloc(&sh.Tp, np * sh.tp_stride) == cudaSuccess && ctx->alloc(&sh.Ptc, need) == cudaSuccess;
-                if (ok) {
-                    // the padding columns of the column pieces stay zero: the kernels write only the first dM / r
-                    ok = cudaMemsetAsync(sh.Ap, 0, sizeof(float) * np * sh.ap_stride, st) == cudaSuccess &&
-                         cudaMemsetAsync(sh.Tp, 0, sizeof(float) * np * sh.tp_stride, st) == cudaSuccess &&
-                         split_pieces_transpose(sd.U64, m, n, sh.Utp, sh.ld1, sh.ut_stride, np, st) == cudaSuccess &&
-                         split_pieces_transpose(sd.Wp64, n, n, sh.Wptp, sh.ld2, sh.wt_stride, np, st) == cudaSuccess &&
-                         split_pieces_transpose(sd.Wr64, n, n, sh.Wrtp, sh.ld2, sh.wt_stride, np, st) == cudaSuccess &&
-                         cudaStreamSynchronize(st) == cudaSuccess;
-                }
-                if (ok) {
-                    const int box = 128;  // factor rows per CTA (MMA M)
-                    bool enc = true;
-                    for (int p = 0; p < np; ++p)
-                        enc = enc && make_tc_map(sh.mU[p], sh.Utp + p * sh.ut_stride, n, sh.ld1, box) &&
-                              make_tc_map(sh.mWp[p], sh.Wptp + p * sh.wt_stride, n, sh.ld2, box) &&
-                              make_tc_map(sh.mWr[p], sh.Wrtp + p * sh.wt_stride, n, sh.ld2, box);
-                    if (!enc) {
-                        fail("tensor-map encoding for the tensor-core apply failed", MFS_ERR_CUDA);
-                        break;
-                    }
-                    sh.tc_ready = true;
-                }
-                if (ok && ctx->opt.precision == 0) {  // the FP64 factors were only the source of the pieces
-                    ctx->release(sd.U64);
-                    ctx->release(sd.Wp64);
-                    ctx->release(sd.Wr64);
-                    sd.U64 = sd.Wp64 = sd.Wr64 = nullptr;
-                }
-            }
-            if (!ok) {
-                fail("device allocation for the preconditioner buffers failed", MFS_ERR_OOM);
-                break;
-            }
-            cudaMemcpy(sh.col_body, cb.data(), sizeof(int) * cb.size(), cudaMemcpyHostToDevice);
-            cudaMemcpy(sh.col_rhs, cr.data(), sizeof(int) * cr.size(), cudaMemcpyHostToDevice);
-        }
-    }
+    for (int s = 0; s < num_shapes && status == MFS_OK; ++s) status = build_shape_factors(ctx, solver, s, 0, st);
+    for (int s = 0; s < num_shapes && status == MFS_OK; ++s) status = alloc_apply_scratch(ctx, ctx->shapes[s], st);
     cusolverDnDestroy(solver);
     if (status != MFS_OK) return status;
 
@@ -1381,7 +1419,8 @@ static double pair_profile_ms(mfs_ctx *ctx) {
     return total;
 }
 
-static mfs_status finish_info(mfs_ctx *ctx, mfs_solve_info *info, const SolveStats &ss, float ms, int nrhs) {
+static mfs_status finish_info(mfs_ctx *ctx, mfs_solve_info *info, const SolveStats &ss, float ms, int nrhs,
+                              bool rhs_pairs = true) {
     ctx->pair_ms_acc = pair_profile_ms(ctx);
     if (info) {
         info->launches = ctx->launches;
@@ -1394,7 +1433,7 @@ static mfs_status finish_info(mfs_ctx *ctx, mfs_solve_info *info, const SolveSta
         info->ms_setup = ctx->ms_setup;
         info->ms_solve = ms;
         info->ms_pairs = ctx->pair_ms_acc;
-        info->pairs = pair_count(ctx, 0) * ss.matvecs + pair_count(ctx, 1);
+        info->pairs = pair_count(ctx, 0) * ss.matvecs + (rhs_pairs ? pair_count(ctx, 1) : 0.0);
     }
     if (ss.breakdown) {
         ctx->last_error = "GMRES breakdown: non-finite residual";
@@ -1490,6 +1529,136 @@ mfs_status mfs_solve_elastance(mfs_ctx *ctx, const double *Q, double *V, int32_t
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
     CKS(stage_out_finish(ctx, Vo, st));
     return finish_info(ctx, info, ss, ms, nrhs);
+}
+
+}  // extern "C"
+
+namespace {
+// Selects the Dirichlet factor set for the duration of one solve, on every return path.
+struct DirichletScope {
+    mfs_ctx *ctx;
+    explicit DirichletScope(mfs_ctx *c) : ctx(c) { ctx->fset = 1; }
+    ~DirichletScope() { ctx->fset = 0; }
+};
+
+// Algorithm 1 SOLVE with the Dirichlet data already in ctx->b_d: gamma by GMRES on Eq. 2sysprec, then
+// the strengths alpha = S^+ gamma in ctx->lam_d.
+mfs_status dirichlet_solve(mfs_ctx *ctx, int nrhs, cudaStream_t st, SolveStats &ss) {
+    DirichletScope scope(ctx);
+    CKS(gmres_solve(ctx, nrhs, st, ss));
+    CKS(precond_apply_dev(ctx, ctx->x_d, ctx->lam_d, 0, nrhs, st));
+    return MFS_OK;
+}
+}  // namespace
+
+extern "C" {
+
+mfs_status mfs_dirichlet_matvec(mfs_ctx *ctx, const double *gamma, double *y, int32_t nrhs, void *stream) {
+    if (!ctx || !gamma || !y || nrhs < 1 || nrhs > ctx->opt.max_rhs) {
+        if (ctx) ctx->last_error = "mfs_dirichlet_matvec: invalid argument";
+        return MFS_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    CKS(ensure_dirichlet(ctx, st));
+    Staged gi, yo;
+    const size_t n = (size_t)nrhs * ctx->sumM * ctx->D;
+    CKS(stage_in(ctx, gi, gamma, n, st));
+    CKS(stage_out_alloc(ctx, yo, y, n));
+    {
+        DirichletScope scope(ctx);
+        CKS(matvec_dev(ctx, gi.d, yo.d, nrhs, st));
+    }
+    CKS(stage_out_finish(ctx, yo, st));
+    return check_device_error(ctx, st);
+}
+
+mfs_status mfs_dirichlet_apply(mfs_ctx *ctx, const double *gamma, double *alpha, int32_t nrhs, void *stream) {
+    if (!ctx || !gamma || !alpha || nrhs < 1 || nrhs > ctx->opt.max_rhs) {
+        if (ctx) ctx->last_error = "mfs_dirichlet_apply: invalid argument";
+        return MFS_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    CKS(ensure_dirichlet(ctx, st));
+    Staged gi, ao;
+    CKS(stage_in(ctx, gi, gamma, (size_t)nrhs * ctx->sumM * ctx->D, st));
+    CKS(stage_out_alloc(ctx, ao, alpha, (size_t)nrhs * ctx->sumN * ctx->D));
+    {
+        DirichletScope scope(ctx);
+        CKS(precond_apply_dev(ctx, gi.d, ao.d, 0, nrhs, st));
+    }
+    CKS(stage_out_finish(ctx, ao, st));
+    return check_device_error(ctx, st);
+}
+
+mfs_status mfs_solve_resistance(mfs_ctx *ctx, const double *U, const double *Omega, double *F, double *T,
+                                int32_t nrhs, mfs_solve_info *info, void *stream) {
+    if (!ctx || !U || !Omega || !F || !T || nrhs < 1 || nrhs > ctx->opt.max_rhs) {
+        if (ctx) ctx->last_error = "mfs_solve_resistance: invalid argument";
+        return MFS_ERR_INVALID_ARG;
+    }
+    if (ctx->kind != MFS_STOKES) {
+        ctx->last_error = "mfs_solve_resistance needs a Stokes context";
+        return MFS_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nb = (size_t)nrhs * ctx->P * 3;
+    Staged Ui, Oi, Fo, To;
+    CKS(stage_in(ctx, Ui, U, nb, st));
+    CKS(stage_in(ctx, Oi, Omega, nb, st));
+    CKS(stage_out_alloc(ctx, Fo, F, nb));
+    CKS(stage_out_alloc(ctx, To, T, nb));
+    CKS(ensure_dirichlet(ctx, st));
+    if (ctx->opt.autotune && ctx->opt.precision != 1 && ctx->best_variant[1][nrhs] < 0) CKS(autotune(ctx, nrhs, st));
+    CKS(ensure_gmres(ctx, nrhs));
+    begin_call(ctx);
+    CK(cudaEventRecord(ctx->ev0, st));
+    // b = K_M U (Sec. 2.2), then Algorithm 1 and [f; t] = K_N^T lambda (Eq. force_def)
+    CK(dirichlet_rhs_stokes(Ui.d, Oi.d, nrhs, ctx->P, ctx->tgt_local64_d, ctx->tgt_off_d, ctx->sumM, ctx->b_d, st));
+    SolveStats ss;
+    CKS(dirichlet_solve(ctx, nrhs, st, ss));
+    CK(extract_stokes(ctx->lam_d, nrhs, ctx->P, ctx->src_local64_d, ctx->src_off_d, ctx->sumN, Fo.d, To.d, st, 1.0));
+    ctx->launches += 2;
+    CK(cudaEventRecord(ctx->ev1, st));
+    CK(cudaEventSynchronize(ctx->ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    CKS(stage_out_finish(ctx, Fo, st));
+    CKS(stage_out_finish(ctx, To, st));
+    return finish_info(ctx, info, ss, ms, nrhs, false);
+}
+
+mfs_status mfs_solve_capacitance(mfs_ctx *ctx, const double *phi, double *q, int32_t nrhs, mfs_solve_info *info,
+                                 void *stream) {
+    if (!ctx || !phi || !q || nrhs < 1 || nrhs > ctx->opt.max_rhs) {
+        if (ctx) ctx->last_error = "mfs_solve_capacitance: invalid argument";
+        return MFS_ERR_INVALID_ARG;
+    }
+    if (ctx->kind != MFS_LAPLACE) {
+        ctx->last_error = "mfs_solve_capacitance needs a Laplace context";
+        return MFS_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nb = (size_t)nrhs * ctx->P;
+    Staged Pi, Qo;
+    CKS(stage_in(ctx, Pi, phi, nb, st));
+    CKS(stage_out_alloc(ctx, Qo, q, nb));
+    CKS(ensure_dirichlet(ctx, st));
+    if (ctx->opt.autotune && ctx->opt.precision != 1 && ctx->best_variant[0][nrhs] < 0) CKS(autotune(ctx, nrhs, st));
+    CKS(ensure_gmres(ctx, nrhs));
+    begin_call(ctx);
+    CK(cudaEventRecord(ctx->ev0, st));
+    // eta = phi 1_M (Sec. 2.1), then Algorithm 1 and q = sum alpha (Eq. qkgauss)
+    CK(dirichlet_rhs_laplace(Pi.d, nrhs, ctx->P, ctx->tgt_off_d, ctx->sumM, ctx->b_d, st));
+    SolveStats ss;
+    CKS(dirichlet_solve(ctx, nrhs, st, ss));
+    CK(extract_laplace(ctx->lam_d, nrhs, ctx->P, ctx->src_off_d, ctx->sumN, Qo.d, st, 1));
+    ctx->launches += 2;
+    CK(cudaEventRecord(ctx->ev1, st));
+    CK(cudaEventSynchronize(ctx->ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    CKS(stage_out_finish(ctx, Qo, st));
+    return finish_info(ctx, info, ss, ms, nrhs, false);
 }
 
 }  // extern "C"

@@ -66,9 +66,9 @@ __global__ void build_P_kernel(int kind, int M, int N, const double *X0, const d
     if (threadIdx.x < 6) P[(size_t)row * 6 + threadIdx.x] = red[threadIdx.x][0];
 }
 
-// SL (column-major dM x dN) = S0 - S0 L + L_r.
+// SL (column-major dM x dN) = S0 - S0 L + L_r, or the bare self block S0 (Sec. 2.3) when bare.
 __global__ void build_SL_kernel(int kind, int M, int N, const double *X0, const double *Y0, double mu,
-                                const double *G0inv, const double *P, double *SL) {
+                                const double *G0inv, const double *P, int bare, double *SL) {
     const int D = kind == 1 ? 3 : 1;
     const long long dM = (long long)D * M, dN = (long long)D * N;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -76,7 +76,9 @@ __global__ void build_SL_kernel(int kind, int M, int N, const double *X0, const 
     const int row = (int)(idx % dM), col = (int)(idx / dM);
     const int i = row / D, a = row % D, j = col / D, b = col % D;
     double v;
-    if (kind == 1) {
+    if (bare) {
+        v = kind == 1 ? stokeslet(X0 + 3 * i, Y0 + 3 * j, a, b, mu) : laplace(X0 + 3 * i, Y0 + 3 * j);
+    } else if (kind == 1) {
         const double *y = Y0 + 3 * j, *x = X0 + 3 * i;
         double kn[6];
 #pragma unroll
@@ -100,14 +102,14 @@ __global__ void build_SL_kernel(int kind, int M, int N, const double *X0, const 
 }
 
 cudaError_t build_SL(int kind, int M, int N, const double *X0, const double *Y0, double mu, const double *G0inv,
-                     double *SL, cudaStream_t st) {
+                     int bare, double *SL, cudaStream_t st) {
     const int D = kind == 1 ? 3 : 1;
     double *P = nullptr;
     cudaError_t e = cudaMallocAsync(&P, sizeof(double) * 6 * D * M, st);
     if (e != cudaSuccess) return e;
-    build_P_kernel<<<D * M, 256, 0, st>>>(kind, M, N, X0, Y0, mu, P);
+    if (!bare) build_P_kernel<<<D * M, 256, 0, st>>>(kind, M, N, X0, Y0, mu, P);
     const long long total = (long long)D * M * D * N;
-    build_SL_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(kind, M, N, X0, Y0, mu, G0inv, P, SL);
+    build_SL_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(kind, M, N, X0, Y0, mu, G0inv, P, bare, SL);
     e = cudaGetLastError();
     cudaFreeAsync(P, st);
     return e;
@@ -152,8 +154,8 @@ __global__ void vt_kn_kernel(int kind, int N, int r, const double *VTcm, const d
 }
 
 __global__ void apply_factor_kernel(int kind, int N, int dM, int r, const double *Ucm, const double *sinv,
-                                    const double *VTcm, const double *Y0, const double *Bp, float *U, float *Wp,
-                                    float *Wr, double *U64, double *Wp64, double *Wr64) {
+                                    const double *VTcm, const double *Y0, const double *Bp, int bare, float *U,
+                                    float *Wp, float *Wr, double *U64, double *Wp64, double *Wr64) {
     const int D = kind == 1 ? 3 : 1;
     const int dN = D * N;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -168,7 +170,9 @@ __global__ void apply_factor_kernel(int kind, int N, int dM, int r, const double
         const int j = (int)(idx / dN), i = (int)(idx % dN);
         const double vt = VTcm[j + (size_t)i * r];
         double proj;
-        if (kind == 1) {
+        if (bare) {  // no projector: the Dirichlet apply V Sigma^+ U^T is used unprojected throughout
+            proj = 0.0;
+        } else if (kind == 1) {
             const int p = i / 3, b = i % 3;
             proj = 0.0;
 #pragma unroll
@@ -187,7 +191,7 @@ __global__ void apply_factor_kernel(int kind, int N, int dM, int r, const double
 }
 
 cudaError_t build_apply_factors(int kind, int M, int N, const double *Ucm, const double *sigma, const double *VTcm,
-                                const double *Y0, const double *G0inv, double eps_trunc, ShapeDev &sd,
+                                const double *Y0, const double *G0inv, double eps_trunc, int bare, ShapeDev &sd,
                                 cudaStream_t st) {
     const int D = kind == 1 ? 3 : 1;
     const int dM = D * M, dN = D * N, r = dN;
@@ -212,11 +216,11 @@ cudaError_t build_apply_factors(int kind, int M, int N, const double *Ucm, const
     if (e == cudaSuccess) e = cudaMallocAsync(&Bp, sizeof(double) * 6 * r, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sinv, hsinv, sizeof(double) * r, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) {
-        vt_kn_kernel<<<r, 256, 0, st>>>(kind, N, r, VTcm, Y0, G0inv, Bp);
+        if (!bare) vt_kn_kernel<<<r, 256, 0, st>>>(kind, N, r, VTcm, Y0, G0inv, Bp);
         const long long nmax = (long long)dM * r > (long long)r * dN ? (long long)dM * r : (long long)r * dN;
         apply_factor_kernel<<<(unsigned)((nmax + 255) / 256), 256, 0, st>>>(kind, N, dM, r, Ucm, sinv, VTcm, Y0, Bp,
-                                                                             sd.U, sd.Wp, sd.Wr, sd.U64, sd.Wp64,
-                                                                             sd.Wr64);
+                                                                             bare, sd.U, sd.Wp, sd.Wr, sd.U64,
+                                                                             sd.Wp64, sd.Wr64);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -544,8 +548,47 @@ cudaError_t completion_laplace(const double *Q, int nrhs, int P, const int *body
     return cudaGetLastError();
 }
 
+// Dirichlet data of the resistance problem: b = K_M U, the rigid motion v + omega x (x - c) at every
+// collocation point (Sec. 2.2, Eq. Kdef, Eq. Kbig); tgt_local64 holds x - c.
+__global__ void dirichlet_rhs_stokes_kernel(const double *U, const double *Om, int P, const double *tgt_local64,
+                                            const int *body_tgt_off, int sum_M, double *b) {
+    const int k = blockIdx.x, h = blockIdx.y;
+    const double *v = U + ((size_t)h * P + k) * 3, *w = Om + ((size_t)h * P + k) * 3;
+    for (int i = body_tgt_off[k] + threadIdx.x; i < body_tgt_off[k + 1]; i += blockDim.x) {
+        const double *x = tgt_local64 + 3 * (size_t)i;
+        double *o = b + ((size_t)h * sum_M + i) * 3;
+        o[0] = v[0] + w[1] * x[2] - w[2] * x[1];
+        o[1] = v[1] + w[2] * x[0] - w[0] * x[2];
+        o[2] = v[2] + w[0] * x[1] - w[1] * x[0];
+    }
+}
+
+// Dirichlet data of the capacitance problem: eta^(k) = phi^(k) 1_M (Sec. 2.1).
+__global__ void dirichlet_rhs_laplace_kernel(const double *phi, int P, const int *body_tgt_off, int sum_M,
+                                             double *b) {
+    const int k = blockIdx.x, h = blockIdx.y;
+    const double v = phi[(size_t)h * P + k];
+    for (int i = body_tgt_off[k] + threadIdx.x; i < body_tgt_off[k + 1]; i += blockDim.x) b[(size_t)h * sum_M + i] = v;
+}
+
+cudaError_t dirichlet_rhs_stokes(const double *U, const double *Om, int nrhs, int P, const double *tgt_local64,
+                                 const int *body_tgt_off, int sum_M, double *b, cudaStream_t st) {
+    dim3 grid(P, nrhs);
+    dirichlet_rhs_stokes_kernel<<<grid, 128, 0, st>>>(U, Om, P, tgt_local64, body_tgt_off, sum_M, b);
+    return cudaGetLastError();
+}
+
+cudaError_t dirichlet_rhs_laplace(const double *phi, int nrhs, int P, const int *body_tgt_off, int sum_M, double *b,
+                                  cudaStream_t st) {
+    dim3 grid(P, nrhs);
+    dirichlet_rhs_laplace_kernel<<<grid, 128, 0, st>>>(phi, P, body_tgt_off, sum_M, b);
+    return cudaGetLastError();
+}
+
+// [U; Omega] = sign * K_N^T lambda: sign -1 extracts velocities (Eq. getU), +1 forces and torques
+// (Eq. force_def).
 __global__ void extract_stokes_kernel(const double *lam, int P, const double *src_local64, const int *body_src_off,
-                                      int sum_N, double *U, double *Om) {
+                                      int sum_N, double sign, double *U, double *Om) {
     const int k = blockIdx.x, h = blockIdx.y;
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int q = body_src_off[k] + threadIdx.x; q < body_src_off[k + 1]; q += blockDim.x) {
@@ -567,19 +610,21 @@ __global__ void extract_stokes_kernel(const double *lam, int P, const double *sr
         __syncthreads();
     }
     if (threadIdx.x < 3) {
-        U[((size_t)h * P + k) * 3 + threadIdx.x] = -red[threadIdx.x][0];
-        Om[((size_t)h * P + k) * 3 + threadIdx.x] = -red[3 + threadIdx.x][0];
+        U[((size_t)h * P + k) * 3 + threadIdx.x] = sign * red[threadIdx.x][0];
+        Om[((size_t)h * P + k) * 3 + threadIdx.x] = sign * red[3 + threadIdx.x][0];
     }
 }
 
 cudaError_t extract_stokes(const double *lam, int nrhs, int P, const double *src_local64, const int *body_src_off,
-                           int sum_N, double *U, double *Om, cudaStream_t st) {
+                           int sum_N, double *U, double *Om, cudaStream_t st, double sign) {
     dim3 grid(P, nrhs);
-    extract_stokes_kernel<<<grid, 128, 0, st>>>(lam, P, src_local64, body_src_off, sum_N, U, Om);
+    extract_stokes_kernel<<<grid, 128, 0, st>>>(lam, P, src_local64, body_src_off, sum_N, sign, U, Om);
     return cudaGetLastError();
 }
 
-__global__ void extract_laplace_kernel(const double *alpha, int P, const int *body_src_off, int sum_N, double *V) {
+// V = -mean(alpha) per body (Eq. vkal), or the net charge sum(alpha) when sum (Eq. qkgauss).
+__global__ void extract_laplace_kernel(const double *alpha, int P, const int *body_src_off, int sum_N, int sum,
+                                       double *V) {
     const int k = blockIdx.x, h = blockIdx.y;
     double acc = 0.0;
     const int b0 = body_src_off[k], b1 = body_src_off[k + 1];
@@ -591,13 +636,13 @@ __global__ void extract_laplace_kernel(const double *alpha, int P, const int *bo
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0) V[(size_t)h * P + k] = -red[0] / (double)(b1 - b0);
+    if (threadIdx.x == 0) V[(size_t)h * P + k] = sum ? red[0] : -red[0] / (double)(b1 - b0);
 }
 
 cudaError_t extract_laplace(const double *alpha, int nrhs, int P, const int *body_src_off, int sum_N, double *V,
-                            cudaStream_t st) {
+                            cudaStream_t st, int sum) {
     dim3 grid(P, nrhs);
-    extract_laplace_kernel<<<grid, 128, 0, st>>>(alpha, P, body_src_off, sum_N, V);
+    extract_laplace_kernel<<<grid, 128, 0, st>>>(alpha, P, body_src_off, sum_N, sum, V);
     return cudaGetLastError();
 }
 
