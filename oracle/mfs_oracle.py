@@ -557,6 +557,26 @@ class Problem:
         g = self.split(bodies, gamma)
         return [self.pinv_apply(k, gk, project=True) + self.lambda0(k, F[k], T[k]) for k, gk in zip(bodies, g)]
 
+    def total_strengths_elastance(self, bodies, gamma, Q):
+        """alpha^(k) = (I - L^(k)) S_L^(k)+ gamma^(k) + alpha_0^(k): the strengths of the representation (Eq. erepK)."""
+        g = self.split(bodies, gamma)
+        return [self.pinv_apply(k, gk, project=True) + self.alpha0(k, Q[k]) for k, gk in zip(bodies, g)]
+
+    def strengths_dirichlet(self, bodies, gamma):
+        """alpha^(k) = S^(kk)+ gamma^(k) (Eq. reconbal): the strengths of a Dirichlet solve."""
+        return [self.pinv_apply_dirichlet(k, gk) for k, gk in zip(bodies, self.split(bodies, gamma))]
+
+    def evaluate(self, bodies, strengths, points: np.ndarray) -> np.ndarray:
+        """u(x) = sum_{k in bodies} sum_j G(x - y_j^(k)) beta_j^(k) at arbitrary points (P_e, 3) (Eq. rep,
+        Eq. repS); returns (P_e,) potentials or (P_e, 3) velocities.  Dense kernel matrices: small cases."""
+        out = np.zeros(points.shape[0] * self.d)
+        for k, bk in zip(bodies, strengths):
+            if self.d == 1:
+                out += laplace_matrix(points, self.Y[k]) @ bk
+            else:
+                out += stokeslet_matrix(points, self.Y[k], self.mu) @ bk
+        return out if self.d == 1 else out.reshape(-1, 3)
+
     def surface_field(self, bodies, strengths, targets=None):
         """The representation evaluated at collocation points: all pairs including self."""
         return self.pair_sum(bodies, strengths, include_self=True, target_bodies=targets)

@@ -6,6 +6,10 @@ Calls only the oracle (oracle/) on the seeded inputs (mfs_inputs/):
 
 sphere100_mobility_oracle.json: U and Omega [100][3] of the 100-sphere mobility problem
 (M = 1200, N = 600, R_p = 0.7, forces and torques N(0,1), seed 2), oracle GMRES tolerance 1e-12.
+
+sphere100_resistance_oracle.json: forces and torques [100][3] of the resistance problem (Sec. 2.2) on
+the same geometry for rigid motions U, Omega ~ N(0,1) drawn with numpy default_rng(14) (U first,
+each of shape (1, 100, 3)), oracle GMRES tolerance 1e-12.
 """
 
 from __future__ import annotations
@@ -39,6 +43,31 @@ def sphere100_mobility():
         "Omega": W.tolist(),
     }
     with open(os.path.join(HERE, "sphere100_mobility_oracle.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print(f"iters {info[0].iters}, {out['seconds']:.0f} s")
+
+
+def sphere100_resistance():
+    import numpy as np
+
+    wl = make_workload("sphere100_mobility")
+    rng = np.random.default_rng(14)
+    U_ref, W_ref = rng.standard_normal((1, 100, 3)), rng.standard_normal((1, 100, 3))
+    t0 = time.time()
+    pr = Problem(wl)
+    F, T, info = pr.solve_resistance(U_ref[0], W_ref[0], tol=1e-12, max_iter=300)
+    out = {
+        "workload": "sphere100_mobility geometry, resistance problem",
+        "description": wl.description,
+        "inputs": "U, Omega = numpy.random.default_rng(14).standard_normal((1, 100, 3)) twice",
+        "oracle_gmres_tol": 1e-12,
+        "oracle_iters": info[0].iters,
+        "oracle_residual": info[0].residual_estimate,
+        "seconds": time.time() - t0,
+        "F": F.tolist(),
+        "T": T.tolist(),
+    }
+    with open(os.path.join(HERE, "sphere100_resistance_oracle.json"), "w") as f:
         json.dump(out, f, indent=1)
     print(f"iters {info[0].iters}, {out['seconds']:.0f} s")
 
