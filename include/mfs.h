@@ -231,6 +231,26 @@ mfs_status mfs_solve_capacitance(mfs_ctx *ctx, const double *phi, double *q, int
 mfs_status mfs_solve_resistance(mfs_ctx *ctx, const double *U, const double *Omega, double *F, double *T,
                                 int32_t nrhs, mfs_solve_info *info, void *stream);
 
+/*
+ * mfs_evaluate -- the solution field of the last solve on this context at arbitrary points: the
+ * representation u(x) = sum_k sum_j G(x - y_j^(k)) beta_j^(k) (Eq. rep, Eq. repS) with the strengths
+ * of that solve, beta = (I - L) S_L^+ gamma + lambda_0 after a mobility solve (Eq. multirep),
+ * (I - L) S_L^+ gamma + alpha_0 after an elastance solve (Eq. erepK), S^+ gamma after a resistance
+ * or capacitance solve (Eq. reconbal).  For the surface residual (Eq. residual) evaluate on a surface
+ * point set finer than the collocation points.
+ *   points [npoints][3] world coordinates, host or device; owner [npoints] (nullable; host or device):
+ *   a body of the suspension the point belongs to -- only that suspension's sources contribute, and
+ *   the point is expressed relative to that body's centre, so the nearest body is the most accurate
+ *   choice.  NULL picks the nearest body (allowed with one suspension only).
+ *   out [nrhs][npoints][d] (potential or velocity), host or device.  nrhs must equal the last solve's.
+ * Points must lie outside the proxy surfaces (in the fluid or conductor exterior, or on the physical
+ * surfaces); at a proxy point itself the kernel is singular and the value is not finite.
+ * Errors: MFS_ERR_INVALID_ARG without a preceding solve, for a mismatched nrhs, an owner outside
+ * [0, P), a non-finite point, or a NULL owner with several suspensions.
+ */
+mfs_status mfs_evaluate(mfs_ctx *ctx, const double *points, const int32_t *owner, int32_t npoints, double *out,
+                        int32_t nrhs, void *stream);
+
 /* The pair-kernel variant the forward pair sums of this context use for `nrhs` right-hand sides
  * (1..max_rhs): the autotuner's pick once a solve or matvec with that nrhs has run (autotune = 1),
  * else the built-in default.  A policy name with its template arguments, e.g.

@@ -48,6 +48,7 @@ EXPORTED = [
     "mfs_dirichlet_matvec",
     "mfs_solve_capacitance",
     "mfs_solve_resistance",
+    "mfs_evaluate",
     "mfs_last_error",
     "mfs_setup_error",
     "mfs_destroy",
@@ -153,6 +154,7 @@ def load_library(path: Optional[str] = None):
     lib.mfs_dirichlet_matvec.argtypes = [vp, vp, vp, i32, vp]
     lib.mfs_solve_capacitance.argtypes = [vp, vp, vp, i32, ctypes.POINTER(_Info), vp]
     lib.mfs_solve_resistance.argtypes = [vp, vp, vp, vp, vp, i32, ctypes.POINTER(_Info), vp]
+    lib.mfs_evaluate.argtypes = [vp, vp, vp, i32, vp, i32, vp]
     lib.mfs_pair_variant.argtypes = [vp, i32]
     lib.mfs_pair_variant.restype = ctypes.c_char_p
     lib.mfs_last_error.argtypes = [vp]
@@ -387,6 +389,20 @@ class MFS:
                                             ctypes.byref(info), _stream_ptr(stream, u.device))
         self._check(rc, allow_not_converged)
         return F, T, _info(info, rc)
+
+    def evaluate(self, points, owner=None, nrhs: int = 1, stream=None):
+        """Field of the last solve at points (npoints, 3): returns (nrhs, npoints, d)."""
+        torch = _torch()
+        p = _Arg(points)
+        npts = int(p.obj.shape[0])
+        o = None
+        if owner is not None:
+            o = owner if isinstance(owner, torch.Tensor) else torch.as_tensor(np.asarray(owner))
+            o = o.to(torch.int32).contiguous()
+        out = self._out((nrhs, npts, self.d), p)
+        self._check(self._lib.mfs_evaluate(self._ctx, p.ptr, None if o is None else o.data_ptr(), npts,
+                                           out.data_ptr(), nrhs, _stream_ptr(stream, p.device)))
+        return out
 
     def mobility_vjp(self, dU, dOmega, want_force_grads: bool = False, stream=None):
         a, b = _Arg(dU), _Arg(dOmega)

@@ -116,8 +116,11 @@ struct mfs_ctx {
     int *done_h = nullptr;
 
     // solution kept for the adjoint
-    double *keep_gamma = nullptr;  // [max_rhs][sum_M][3] solution gamma of the last mobility solve
-    double *keep_lam0 = nullptr;   // [max_rhs][sum_N][3] its completion strengths lambda_0
+    // the last solve, for mfs_mobility_vjp and mfs_evaluate: which problem, its GMRES solution gamma
+    // [max_rhs][sum_M][D] and its inputs (F then T [nrhs][P][3], or Q [nrhs][P])
+    int last_solve = 0;  // 0 none, 1 mobility, 2 elastance, 3 resistance, 4 capacitance
+    double *keep_gamma = nullptr;
+    double *keep_lam0 = nullptr;  // [max_rhs][P][6]
     int last_nrhs = 0;
 
     // adjoint: the transposed direction (proxy targets, collocation sources)
@@ -323,16 +326,16 @@ int default_variant(int D, int nrhs) {
 // Tiles and CTA shares for one pair-kernel variant.  transposed = 0: collocation targets, proxy
 // sources (the matvec and u_0); transposed = 1: proxy targets, collocation sources (the adjoint's
 // S^T sums).
-mfs_status build_plan(mfs_ctx *ctx, int variant, int include_self, int transposed, PairPlan &plan) {
+// Work list of a pair sum over any target set grouped by body: targets of body k are
+// [toff[k], toff[k+1]) and tbody[t] is the body of target t; source blocks per body from boff.
+mfs_status build_plan_for(mfs_ctx *ctx, int variant, int include_self, const std::vector<int> &toff,
+                          const std::vector<int> &tbody, const std::vector<long long> &boff, int ntargets,
+                          PairPlan &plan) {
     int count = 0;
     const PairVariant *vv = pair_variants(&count);
     const PairVariant &v = vv[variant];
     const int TT = v.tile_targets;
     const int C = v.grad ? 3 : v.D * v.nrhs;
-    const std::vector<int> &toff = transposed ? ctx->src_off : ctx->tgt_off;
-    const std::vector<int> &tbody = transposed ? ctx->src_body : ctx->tgt_body;
-    const std::vector<long long> &boff = transposed ? ctx->blkT_off : ctx->blk_off;
-    const int ntargets = transposed ? ctx->sumN : ctx->sumM;
     std::vector<PairTile> tiles;
     long long units = 0;
     for (int s = 0; s < ctx->S; ++s) {
@@ -393,8 +396,21 @@ mfs_status build_plan(mfs_ctx *ctx, int variant, int include_self, int transpose
     plan.partial_bytes = sizeof(double) * (size_t)G * 2 * TT * C;
     plan.direct_bytes = sizeof(double) * (size_t)ntargets * C;
     CK(ctx->alloc(&plan.partial, (size_t)G * 2 * TT * C));
-    CK(ctx->alloc(&plan.direct, (size_t)ntargets * C));
+    CK(ctx->alloc(&plan.direct, (size_t)std::max(ntargets, 1) * C));
     return MFS_OK;
+}
+
+mfs_status build_plan(mfs_ctx *ctx, int variant, int include_self, int transposed, PairPlan &plan) {
+    return build_plan_for(ctx, variant, include_self, transposed ? ctx->src_off : ctx->tgt_off,
+                          transposed ? ctx->src_body : ctx->tgt_body, transposed ? ctx->blkT_off : ctx->blk_off,
+                          transposed ? ctx->sumN : ctx->sumM, plan);
+}
+
+void release_plan(mfs_ctx *ctx, PairPlan &plan) {
+    ctx->release(plan.tiles);
+    ctx->release(plan.partial);
+    ctx->release(plan.direct);
+    plan = PairPlan{};
 }
 
 mfs_status get_plan(mfs_ctx *ctx, int variant, int include_self, PairPlan **out, int transposed = 0) {
@@ -1403,6 +1419,23 @@ mfs_status mfs_pair_sum(mfs_ctx *ctx, const double *strengths, double *u, int32_
     return check_device_error(ctx, st);
 }
 
+// Keep the GMRES solution gamma (ctx->x_d) and the inputs a (and b), n doubles each, of the solve
+// just run (kind: 1 mobility, 2 elastance, 3 resistance, 4 capacitance).
+static mfs_status keep_solution(mfs_ctx *ctx, int kind, int nrhs, const double *a, const double *b, size_t n,
+                                cudaStream_t st) {
+    if (!ctx->keep_gamma) {
+        CK(ctx->alloc(&ctx->keep_gamma, (size_t)ctx->opt.max_rhs * ctx->sumM * ctx->D));
+        CK(ctx->alloc(&ctx->keep_lam0, (size_t)ctx->opt.max_rhs * ctx->P * 6));
+    }
+    CK(cudaMemcpyAsync(ctx->keep_gamma, ctx->x_d, sizeof(double) * nrhs * ctx->sumM * ctx->D,
+                       cudaMemcpyDeviceToDevice, st));
+    if (a) CK(cudaMemcpyAsync(ctx->keep_lam0, a, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    if (b) CK(cudaMemcpyAsync(ctx->keep_lam0 + n, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    ctx->last_solve = kind;
+    ctx->last_nrhs = nrhs;
+    return MFS_OK;
+}
+
 static void begin_call(mfs_ctx *ctx) {
     ctx->launches = 0;
     ctx->pair_launches = 0;
@@ -1479,20 +1512,13 @@ mfs_status mfs_solve_mobility(mfs_ctx *ctx, const double *F, const double *T, do
     CK(extract_stokes(ctx->lam_d, nrhs, ctx->P, ctx->src_local64_d, ctx->src_off_d, ctx->sumN, Uo.d, Oo.d, st));
     ctx->launches += 1;
     CK(cudaEventRecord(ctx->ev1, st));
-    // keep gamma, F and T for mfs_mobility_vjp (outside the timed region)
-    if (!ctx->keep_gamma) {
-        CK(ctx->alloc(&ctx->keep_gamma, (size_t)ctx->opt.max_rhs * ctx->sumM * 3));
-        CK(ctx->alloc(&ctx->keep_lam0, (size_t)ctx->opt.max_rhs * ctx->P * 6));  // F then T
-    }
-    CK(cudaMemcpyAsync(ctx->keep_gamma, ctx->x_d, sizeof(double) * nrhs * ctx->sumM * 3, cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(ctx->keep_lam0, Fi.d, sizeof(double) * nb, cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(ctx->keep_lam0 + nb, Ti.d, sizeof(double) * nb, cudaMemcpyDeviceToDevice, st));
+    // keep gamma, F and T for mfs_mobility_vjp and mfs_evaluate (outside the timed region)
+    CKS(keep_solution(ctx, 1, nrhs, Fi.d, Ti.d, nb, st));
     CK(cudaEventSynchronize(ctx->ev1));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
     CKS(stage_out_finish(ctx, Uo, st));
     CKS(stage_out_finish(ctx, Oo, st));
-    ctx->last_nrhs = nrhs;
     return finish_info(ctx, info, ss, ms, nrhs);
 }
 
@@ -1524,6 +1550,7 @@ mfs_status mfs_solve_elastance(mfs_ctx *ctx, const double *Q, double *V, int32_t
     CK(extract_laplace(ctx->lam_d, nrhs, ctx->P, ctx->src_off_d, ctx->sumN, Vo.d, st));  // Eq. vkal
     ctx->launches += 1;
     CK(cudaEventRecord(ctx->ev1, st));
+    CKS(keep_solution(ctx, 2, nrhs, Qi.d, nullptr, nb, st));
     CK(cudaEventSynchronize(ctx->ev1));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
@@ -1619,6 +1646,7 @@ mfs_status mfs_solve_resistance(mfs_ctx *ctx, const double *U, const double *Ome
     CK(extract_stokes(ctx->lam_d, nrhs, ctx->P, ctx->src_local64_d, ctx->src_off_d, ctx->sumN, Fo.d, To.d, st, 1.0));
     ctx->launches += 2;
     CK(cudaEventRecord(ctx->ev1, st));
+    CKS(keep_solution(ctx, 3, nrhs, nullptr, nullptr, 0, st));
     CK(cudaEventSynchronize(ctx->ev1));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
@@ -1654,6 +1682,7 @@ mfs_status mfs_solve_capacitance(mfs_ctx *ctx, const double *phi, double *q, int
     CK(extract_laplace(ctx->lam_d, nrhs, ctx->P, ctx->src_off_d, ctx->sumN, Qo.d, st, 1));
     ctx->launches += 2;
     CK(cudaEventRecord(ctx->ev1, st));
+    CKS(keep_solution(ctx, 4, nrhs, nullptr, nullptr, 0, st));
     CK(cudaEventSynchronize(ctx->ev1));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
@@ -1724,7 +1753,7 @@ mfs_status mfs_mobility_vjp(mfs_ctx *ctx, const double *dU, const double *dOmega
         if (ctx) ctx->last_error = "mfs_mobility_vjp: invalid argument";
         return MFS_ERR_INVALID_ARG;
     }
-    if (ctx->kind != MFS_STOKES || !ctx->keep_gamma || ctx->last_nrhs != nrhs) {
+    if (ctx->kind != MFS_STOKES || ctx->last_solve != 1 || ctx->last_nrhs != nrhs) {
         ctx->last_error = "mfs_mobility_vjp needs a preceding mfs_solve_mobility with the same nrhs";
         return MFS_ERR_INVALID_ARG;
     }
@@ -1801,6 +1830,185 @@ mfs_status mfs_mobility_vjp(mfs_ctx *ctx, const double *dU, const double *dOmega
     CKS(stage_out_finish(ctx, dco, st));
     CK(cudaStreamSynchronize(st));
     return check_device_error(ctx, st);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Evaluation of the last solve's representation at arbitrary points
+// ---------------------------------------------------------------------------
+static __global__ void add_kernel(double *a, const double *b, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        a[i] += b[i];
+}
+
+// out[h][order[i]][c] = in[h][i][c]: back from owner-sorted to the caller's point order.
+static __global__ void unsort_kernel(const double *in, const int *order, int np, int D, int nrhs, double *out) {
+    const size_t n = (size_t)nrhs * np * D;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t h = e / ((size_t)np * D), r = e % ((size_t)np * D);
+        const int i = (int)(r / D), c = (int)(r % D);
+        out[(h * np + order[i]) * D + c] = in[e];
+    }
+}
+
+namespace {
+// The strengths of the representation of the last solve, [nrhs][sum_N][D] into ctx->lam_d:
+// mobility (I - L) S_L^+ gamma + lambda_0 (Eq. multirep), elastance (I - L) S_L^+ gamma + alpha_0
+// (Eq. erepK), resistance and capacitance S^+ gamma (Eq. reconbal).
+mfs_status last_strengths(mfs_ctx *ctx, int nrhs, double *tmp, cudaStream_t st) {
+    const int P = ctx->P;
+    const size_t ns = (size_t)nrhs * ctx->sumN * ctx->D;
+    if (ctx->last_solve >= 3) {
+        DirichletScope scope(ctx);
+        CKS(precond_apply_dev(ctx, ctx->keep_gamma, ctx->lam_d, 0, nrhs, st));
+        return MFS_OK;
+    }
+    CKS(precond_apply_dev(ctx, ctx->keep_gamma, ctx->lam_d, 1, nrhs, st));
+    if (ctx->last_solve == 1) {
+        const size_t nb = (size_t)nrhs * P * 3;
+        CK(completion_stokes(ctx->keep_lam0, ctx->keep_lam0 + nb, nrhs, P, ctx->rot64_d, ctx->G0inv_d,
+                             ctx->shape_id_d, ctx->src_local64_d, ctx->src_off_d, ctx->sumN, tmp, st));
+    } else {
+        CK(completion_laplace(ctx->keep_lam0, nrhs, P, ctx->src_off_d, ctx->sumN, tmp, st));
+    }
+    add_kernel<<<(unsigned)std::min<size_t>((ns + 255) / 256, 4096), 256, 0, st>>>(ctx->lam_d, tmp, ns);
+    CK(cudaGetLastError());
+    return MFS_OK;
+}
+}  // namespace
+
+extern "C" {
+
+mfs_status mfs_evaluate(mfs_ctx *ctx, const double *points, const int32_t *owner, int32_t npoints, double *out,
+                        int32_t nrhs, void *stream) {
+    if (!ctx || (npoints > 0 && (!points || !out)) || npoints < 0 || nrhs < 1) {
+        if (ctx) ctx->last_error = "mfs_evaluate: invalid argument";
+        return MFS_ERR_INVALID_ARG;
+    }
+    if (ctx->last_solve == 0 || ctx->last_nrhs != nrhs) {
+        ctx->last_error = "mfs_evaluate needs a preceding solve with the same nrhs";
+        return MFS_ERR_INVALID_ARG;
+    }
+    if (!owner && ctx->S > 1) {
+        ctx->last_error = "mfs_evaluate: owner bodies are required with several suspensions";
+        return MFS_ERR_INVALID_ARG;
+    }
+    if (npoints == 0) return MFS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int P = ctx->P, D = ctx->D, np = npoints;
+    // points and owners on the host: the owner grouping is set up there
+    std::vector<double> pts(3 * (size_t)np);
+    std::vector<int> own(np);
+    CK(cudaMemcpy(pts.data(), points, sizeof(double) * pts.size(), cudaMemcpyDefault));
+    if (owner) {
+        CK(cudaMemcpy(own.data(), owner, sizeof(int) * np, cudaMemcpyDefault));
+    } else {  // nearest body centre (single suspension)
+        for (int i = 0; i < np; ++i) {
+            double best = 1e300;
+            int bk = 0;
+            for (int k = 0; k < P; ++k) {
+                double d2 = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    const double d = pts[3 * (size_t)i + a] - ctx->centres[3 * (size_t)k + a];
+                    d2 += d * d;
+                }
+                if (d2 < best) {
+                    best = d2;
+                    bk = k;
+                }
+            }
+            own[i] = bk;
+        }
+    }
+    std::vector<int> toff(P + 1, 0), order(np), tbody(np);
+    for (int i = 0; i < np; ++i) {
+        if (own[i] < 0 || own[i] >= P || !std::isfinite(pts[3 * (size_t)i]) || !std::isfinite(pts[3 * (size_t)i + 1]) ||
+            !std::isfinite(pts[3 * (size_t)i + 2])) {
+            ctx->last_error = "mfs_evaluate: owner out of range or non-finite point";
+            return MFS_ERR_INVALID_ARG;
+        }
+        toff[own[i] + 1]++;
+    }
+    for (int k = 0; k < P; ++k) toff[k + 1] += toff[k];
+    std::vector<float4> t4(np);
+    std::vector<double> t64(3 * (size_t)np);
+    {
+        std::vector<int> fill(toff.begin(), toff.end() - 1);
+        for (int i = 0; i < np; ++i) {
+            const int k = own[i], j = fill[k]++;
+            order[j] = i;
+            tbody[j] = k;
+            double x[3];
+            for (int a = 0; a < 3; ++a) {
+                x[a] = pts[3 * (size_t)i + a] - ctx->centres[3 * (size_t)k + a];
+                t64[3 * (size_t)j + a] = x[a];
+            }
+            float kb;
+            std::memcpy(&kb, &k, sizeof(float));  // body id stored as int bits
+            t4[j] = make_float4((float)x[0], (float)x[1], (float)x[2], kb);
+        }
+    }
+    Staged oo;
+    CKS(stage_out_alloc(ctx, oo, out, (size_t)nrhs * np * D));
+    float4 *t4_d = nullptr;
+    int *order_d = nullptr, *tbody_d = nullptr;
+    double *t64_d = nullptr, *sorted_d = nullptr, *tmp_d = nullptr, *raw_d = nullptr;
+    PairPlan plan;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(st);
+        void *ps[] = {t4_d, order_d, tbody_d, t64_d, sorted_d, tmp_d, raw_d};
+        for (void *p : ps) ctx->release(p);
+        if (plan.tiles) release_plan(ctx, plan);
+    };
+    mfs_status rc = [&]() -> mfs_status {
+        CK(ctx->alloc(&t4_d, np));
+        CK(ctx->alloc(&order_d, np));
+        CK(ctx->alloc(&tbody_d, np));
+        CK(ctx->alloc(&sorted_d, (size_t)nrhs * np * D));
+        CK(ctx->alloc(&tmp_d, (size_t)nrhs * ctx->sumN * D));
+        CK(cudaMemcpyAsync(t4_d, t4.data(), sizeof(float4) * np, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(order_d, order.data(), sizeof(int) * np, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(tbody_d, tbody.data(), sizeof(int) * np, cudaMemcpyHostToDevice, st));
+        CKS(last_strengths(ctx, nrhs, tmp_d, st));
+        const double scale = kernel_scale(ctx);
+        if (ctx->opt.precision == 1) {  // FP64 direct sums
+            CK(ctx->alloc(&t64_d, 3 * (size_t)np));
+            CK(ctx->alloc(&raw_d, (size_t)nrhs * np * D));
+            CK(cudaMemcpyAsync(t64_d, t64.data(), sizeof(double) * t64.size(), cudaMemcpyHostToDevice, st));
+            CK(pair_sum_fp64(D, nrhs, t64_d, tbody_d, np, ctx->src_local4_d, ctx->sumN, ctx->susp_src_begin_d,
+                             ctx->susp_src_end_d, ctx->src_off_d, ctx->centres_d, ctx->lam_d, 1, raw_d, st));
+            const size_t n = (size_t)nrhs * np * D;
+            combine_raw_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(raw_d, nullptr, 0.0, scale, sorted_d, n);
+            CK(cudaGetLastError());
+        } else {  // the FP32 pair kernel on the new targets, all pairs of the owner's suspension
+            const int variant = ctx->best_variant[D == 3][nrhs] >= 0 ? ctx->best_variant[D == 3][nrhs]
+                                                                   : default_variant(D, nrhs);
+            if (variant < 0) {
+                ctx->last_error = "no pair-kernel variant for this nrhs";
+                return MFS_ERR_INVALID_ARG;
+            }
+            CKS(build_plan_for(ctx, variant, 1, toff, tbody, ctx->blk_off, np, plan));
+            int vc = 0;
+            const PairVariant *vv = pair_variants(&vc);
+            CK(pack_sources(D, nrhs, vv[variant].packed, ctx->src_pos_d, ctx->rec_pt_d, ctx->lam_d, ctx->sumN,
+                            ctx->nrec, ctx->rec_d, st));
+            PairGeom g = geom_of(ctx);
+            g.tgt = t4_d;
+            g.ntargets = np;
+            const PairWork w = work_of(plan);
+            if (w.total_units > 0) CK(pair_launch(variant, g, w, ctx->err_d, st));
+            CK(pair_epilogue(D, nrhs, w, nullptr, 0.0, scale, sorted_d, np, st));
+        }
+        const size_t n = (size_t)nrhs * np * D;
+        unsort_kernel<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, st>>>(sorted_d, order_d, np, D,
+                                                                                          nrhs, oo.d);
+        CK(cudaGetLastError());
+        CKS(stage_out_finish(ctx, oo, st));
+        return check_device_error(ctx, st);
+    }();
+    cleanup();
+    return rc;
 }
 
 }  // extern "C"
