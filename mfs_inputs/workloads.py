@@ -21,6 +21,11 @@ Workloads (the sizes are the ones the benchmark and the parity tests use):
   counts uniform in {2..64}, each body a unit sphere or a (1,1,1.5) spheroid
   (probability 1/2, random orientation), M=600, N=300, Delta_sep = 0.3,
   volume fraction 0.1, min bounding-sphere gap 0.1, 4 right-hand sides.
+* ``ellipsoidT5000_mobility``, ``ellipsoidT10000_mobility``  Stokes, Type T
+  ellipsoids (0.4, 0.6, 1) inside unit bounding spheres grown with every sphere
+  exactly 0.2 from at least one other, random orientations, N_v = 34 (M=839,
+  N=660), Delta_sep = 1.05 x 0.125, forces and torques N(0,1) (Sec. 4.2).
+* ``sphere100_elastance``  the sphere100 geometry as a Laplace problem, Q ~ N(0,1).
 """
 
 from __future__ import annotations
@@ -31,6 +36,8 @@ from typing import Callable, Optional
 import numpy as np
 
 from .geometry import (
+    ellipsoid_grid,
+    ellipsoid_proxy,
     fibonacci_sphere,
     grow_cluster,
     random_quaternions,
@@ -43,7 +50,7 @@ from .geometry import (
 @dataclasses.dataclass
 class Shape:
     name: str
-    semi_axes: tuple  # (a, a, c)
+    semi_axes: tuple  # (a, b, c)
     dsep: float
     proxy: np.ndarray  # (N, 3) body frame
     colloc: np.ndarray  # (M, 3) body frame
@@ -134,6 +141,55 @@ def sphere_shape(m: int, n: int, radius: float = 1.0, rp: float = 0.7) -> Shape:
         dsep=radius - rp,
         proxy=fibonacci_sphere(n, rp),
         colloc=fibonacci_sphere(m, radius),
+    )
+
+
+def ellipsoid_shape(n_v: int, a: float, b: float, c: float, dsep: float, colloc_factor: float = 1.15) -> Shape:
+    """Triaxial ellipsoid (Sec. 4.2): proxies on the n_v grid moved dsep inward, collocation points
+    on the grid with round(1.15 n_v) Gauss-Legendre rings (M ~ 1.3 N)."""
+    return Shape(
+        name=f"ellipsoid_{a:g}_{b:g}_{c:g}_Nv{n_v}",
+        semi_axes=(a, b, c),
+        dsep=dsep,
+        proxy=ellipsoid_proxy(n_v, a, b, c, dsep),
+        colloc=ellipsoid_grid(int(round(colloc_factor * n_v)), a, b, c),
+    )
+
+
+def ellipsoid_cluster(
+    count: int = 5000,
+    n_v: int = 34,
+    semi_axes: tuple = (0.4, 0.6, 1.0),
+    dsep: float = 1.05 * 0.125,
+    gap: float = 0.2,
+    seed: int = 6,
+    name: str = "ellipsoidT5000_mobility",
+) -> Workload:
+    """Type T ellipsoids (semi-axes 0.4, 0.6, 1) in a cluster of unit bounding spheres grown with each
+    sphere exactly `gap` from at least one other, random orientations inside the spheres (the footnote
+    of Sec. 4.2's P = 10000 example); forces and torques N(0, 1).  dsep: the resistance offset 0.125 of
+    Sec. 4.2 times 1.05 for the mobility problem."""
+    rng = np.random.default_rng(seed)
+    shape = ellipsoid_shape(n_v, *semi_axes, dsep)
+    centres = grow_cluster(rng, count, 1.0, gap, gap)
+    quats = random_quaternions(rng, count)
+    a, b, c = semi_axes
+    return Workload(
+        name=name,
+        kind="stokes",
+        shapes=[shape],
+        centres=centres,
+        quats=quats,
+        shape_id=np.zeros(count, np.int32),
+        body_offsets=np.array([0, count], np.int32),
+        F=rng.standard_normal((1, count, 3)),
+        T=rng.standard_normal((1, count, 3)),
+        seed=seed,
+        description=(
+            f"Stokes, {count} ellipsoids ({a:g},{b:g},{c:g}) in unit bounding spheres grown at gap {gap:g}, "
+            f"random orientations, N_v={n_v} (M={shape.n_colloc}, N={shape.n_proxy}), Delta_sep={dsep:.5g}, "
+            "F, T ~ N(0,1)"
+        ),
     )
 
 
@@ -305,6 +361,10 @@ WORKLOADS: dict = {
         }
     ),
     "batched256_mobility": batched_suspensions,
+    "ellipsoidT5000_mobility": ellipsoid_cluster,
+    "ellipsoidT10000_mobility": lambda **kw: ellipsoid_cluster(
+        **{"count": 10000, "seed": 7, "name": "ellipsoidT10000_mobility", **kw}
+    ),
     # the 100-sphere geometry as an elastance problem (Laplace kernel), Q ~ N(0, 1)
     "sphere100_elastance": lambda **kw: sphere_suspension(
         **{"kind": "laplace", "name": "sphere100_elastance", **kw}
