@@ -67,8 +67,11 @@ def _args():
                     help="profiling case: 24 spheres with the same M, N and volume fraction (not a bench line)")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "batched256_mobility", "sphere200_adjoint", "spheroid1000_mobility",
-                             "sphere100_elastance", "sphere100_resistance"],
+                             "sphere100_elastance", "sphere100_resistance", "ellipsoidT5000_mobility",
+                             "ellipsoidT10000_mobility"],
                     help="secondary measurements (their own JSON line); the default is the benchmark")
+    ap.add_argument("--compare-nv40", action="store_true",
+                    help="ellipsoid workloads: also solve on the N_v = 40 grid and report the difference")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="secondary workloads: also time the FP64 reference GPU solve (precision = 1)")
     return ap.parse_args()
@@ -287,6 +290,8 @@ def secondary(args):
     wl = make_workload(name)
     t0 = time.perf_counter()
     opts = {"max_iter": 100, "restart": 100} if name == "batched256_mobility" else {}
+    if name.startswith("ellipsoid"):
+        opts = {"max_iter": 60, "restart": 60}  # GMRES basis of 61 vectors of 3 M P doubles
     ctx = MFS.from_workload(wl, profile=1, **opts)
     setup_s = time.perf_counter() - t0
     laplace = wl.kind == "laplace"
@@ -355,6 +360,19 @@ def secondary(args):
     }
     if vjp_ms:
         line["vjp_ms"] = statistics.median(vjp_ms)
+    if args.compare_nv40 and name.startswith("ellipsoid"):
+        # Sec. 4.2's error estimate: the same cluster on the finer grid N_v = 40 (M=1128, N=878),
+        # max-norm difference of the rigid-body motions relative to the finer grid's
+        del ctx
+        torch.cuda.synchronize()
+        wl40 = make_workload(name, n_v=40)
+        ctx40 = MFS.from_workload(wl40, profile=1, **opts)
+        U40, W40, i40 = ctx40.solve_mobility(F, T)
+        a = torch.cat([out[0], out[1]], -1).cpu().numpy()
+        b = torch.cat([U40, W40], -1).cpu().numpy()
+        line["grid_error_nv34_vs_nv40"] = float(np.abs(a - b).max() / np.abs(b).max())
+        line["nv40_solve"] = {"ms": i40.ms_solve, "iters": i40.iters, "pairs_per_s": i40.pairs / (i40.ms_solve / 1e3),
+                              "M": int(wl40.shapes[0].n_colloc), "N": int(wl40.shapes[0].n_proxy)}
     if args.compare_fp64:
         # the all-FP64 GPU path (precision = 1) on the same problem; for many suspensions on the first
         # 16 of them (independent problems: the batched solve's rows for those bodies are comparable)

@@ -1283,11 +1283,43 @@ static mfs_status autotune(mfs_ctx *ctx, int nrhs, cudaStream_t st) {
     int best_i = -1;
     // zero strengths: the timing does not depend on the values
     CK(cudaMemsetAsync(ctx->lam_d, 0, sizeof(double) * (size_t)nrhs * ctx->sumN * ctx->D, st));
+    // Large problems are timed on a sample: the targets of the first bodies of the first suspension
+    // against all of its sources, about 4e10 pairs (tens of milliseconds, every SM busy), so that
+    // trying every variant costs a fraction of one pair sum.
+    const double sample_pairs = 4e10;
+    bool sample = pair_count(ctx, 0) > 2.0 * sample_pairs;
+    std::vector<int> toff_s;
+    int nt_s = 0;
+    if (sample) {
+        const int B0 = ctx->body_off[0], B1 = ctx->body_off[1];
+        const double ns = ctx->src_off[B1] - ctx->src_off[B0];
+        int kb = B0;
+        double acc = 0.0;
+        while (kb < B1 && acc < sample_pairs) {
+            acc += (double)(ctx->tgt_off[kb + 1] - ctx->tgt_off[kb]) * ns;
+            ++kb;
+        }
+        toff_s.assign(ctx->tgt_off.begin(), ctx->tgt_off.end());
+        for (int k = kb; k <= ctx->P; ++k) toff_s[k] = ctx->tgt_off[kb];
+        nt_s = ctx->tgt_off[kb];
+        sample = nt_s > 0;
+    }
     for (int i = 0; i < count; ++i) {
         if (v[i].grad || v[i].D != ctx->D || v[i].nrhs != nrhs) continue;
         if (pair_occupancy(i) <= 0) continue;
-        PairPlan *plan = nullptr;
-        CKS(get_plan(ctx, i, 0, &plan));
+        PairPlan local;
+        PairPlan *plan = &local;
+        if (sample)
+            CKS(build_plan_for(ctx, i, 0, toff_s, ctx->tgt_body, ctx->blk_off, nt_s, local));
+        else
+            CKS(get_plan(ctx, i, 0, &plan));
+        struct Release {
+            mfs_ctx *c;
+            PairPlan *p;
+            ~Release() {
+                if (p->tiles) release_plan(c, *p);
+            }
+        } release{ctx, &local};
         const PairWork w = work_of(*plan);
         if (w.total_units == 0) return MFS_OK;
         CK(pack_sources(ctx->D, nrhs, v[i].packed, ctx->src_pos_d, ctx->rec_pt_d, ctx->lam_d, ctx->sumN, ctx->nrec,
