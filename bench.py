@@ -70,6 +70,8 @@ def _args():
                              "sphere100_elastance", "sphere100_resistance", "ellipsoidT5000_mobility",
                              "ellipsoidT10000_mobility"],
                     help="secondary measurements (their own JSON line); the default is the benchmark")
+    ap.add_argument("--bodies", type=int, default=0,
+                    help="secondary workloads: override the body count (smaller cases for profiling)")
     ap.add_argument("--compare-nv40", action="store_true",
                     help="ellipsoid workloads: also solve on the N_v = 40 grid and report the difference")
     ap.add_argument("--compare-fp64", action="store_true",
@@ -287,7 +289,7 @@ def secondary(args):
 
     dev = torch.device("cuda", 0)
     name = args.workload
-    wl = make_workload(name)
+    wl = make_workload(name, **({"count": args.bodies} if args.bodies else {}))
     t0 = time.perf_counter()
     opts = {"max_iter": 100, "restart": 100} if name == "batched256_mobility" else {}
     if name.startswith("ellipsoid"):
@@ -365,7 +367,7 @@ def secondary(args):
         # max-norm difference of the rigid-body motions relative to the finer grid's
         del ctx
         torch.cuda.synchronize()
-        wl40 = make_workload(name, n_v=40)
+        wl40 = make_workload(name, n_v=40, **({"count": args.bodies} if args.bodies else {}))
         ctx40 = MFS.from_workload(wl40, profile=1, **opts)
         U40, W40, i40 = ctx40.solve_mobility(F, T)
         a = torch.cat([out[0], out[1]], -1).cpu().numpy()
