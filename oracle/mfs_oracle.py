@@ -577,6 +577,23 @@ class Problem:
                 out += stokeslet_matrix(points, self.Y[k], self.mu) @ bk
         return out if self.d == 1 else out.reshape(-1, 3)
 
+    def evaluate_stress(self, bodies, strengths, points: np.ndarray, normals: np.ndarray):
+        """Pressure p and traction T = sigma n of the Stokeslet representation at points with unit normals
+        (Eq. traction): per source, p = (r . lambda) / (4 pi r^3) (the pressure fundamental solution
+        Pi = 2 r / r^3 with the 1/(8 pi) of Sec. 2.2) and sigma_ik = -3 r_i r_k (r . lambda) / (4 pi r^5),
+        r = x - y; both independent of mu.  Returns (p (P_e,), T (P_e, 3))."""
+        p = np.zeros(points.shape[0])
+        T = np.zeros((points.shape[0], 3))
+        for k, bk in zip(bodies, strengths):
+            lam = bk.reshape(-1, 3)
+            r = points[:, None, :] - self.Y[k][None, :, :]  # (P_e, N, 3)
+            rn = np.linalg.norm(r, axis=2)
+            rl = np.einsum("ijk,jk->ij", r, lam)
+            p += np.sum(rl / rn**3, axis=1) / (4.0 * PI)
+            rnrm = np.einsum("ijk,ik->ij", r, normals)
+            T += -3.0 / (4.0 * PI) * np.einsum("ij,ijk->ik", rl * rnrm / rn**5, r)
+        return p, T
+
     def surface_field(self, bodies, strengths, targets=None):
         """The representation evaluated at collocation points: all pairs including self."""
         return self.pair_sum(bodies, strengths, include_self=True, target_bodies=targets)

@@ -66,9 +66,17 @@ __global__ void update_kernel(GmresDev gd, double *w, const double *htmp, int j)
     long long e0, e1;
     lane_chunk(gd, l, b, e0, e1);
     for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        double s = w[e];
-        for (int i = 0; i <= j; ++i) s -= h[i] * gd.V[(size_t)i * gd.n + e];
-        w[e] = s;
+        // four independent FP64 chains (GB300's FP64 latency would serialise a single one)
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int i = 0;
+        for (; i + 3 <= j; i += 4) {
+            s0 += h[i] * gd.V[(size_t)i * gd.n + e];
+            s1 += h[i + 1] * gd.V[(size_t)(i + 1) * gd.n + e];
+            s2 += h[i + 2] * gd.V[(size_t)(i + 2) * gd.n + e];
+            s3 += h[i + 3] * gd.V[(size_t)(i + 3) * gd.n + e];
+        }
+        for (; i <= j; ++i) s0 += h[i] * gd.V[(size_t)i * gd.n + e];
+        w[e] -= (s0 + s1) + (s2 + s3);
     }
 }
 

@@ -615,7 +615,7 @@ mfs_status ensure_gmres(mfs_ctx *ctx, int nrhs) {
     // blocks per lane: enough parallelism for the reductions, at least one
     const long long per_lane = n / std::max(L, 1);
     gd.part_blocks = (int)std::max<long long>(1, std::min<long long>(4 * (long long)ctx->sm_count / std::max(L, 1) + 1,
-                                                                     (per_lane + 4095) / 4096));
+                                                                     (per_lane + 1023) / 1024));
     gd.part_blocks = std::min(gd.part_blocks, 512);
     std::vector<long long> seg(L + 1);
     for (int h = 0; h < nrhs; ++h)
