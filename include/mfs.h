@@ -251,6 +251,23 @@ mfs_status mfs_solve_resistance(mfs_ctx *ctx, const double *U, const double *Ome
 mfs_status mfs_evaluate(mfs_ctx *ctx, const double *points, const int32_t *owner, int32_t npoints, double *out,
                         int32_t nrhs, void *stream);
 
+/*
+ * mfs_evaluate_stress -- pressure and surface traction of the last mobility or resistance solve at
+ * arbitrary points (Stokes contexts): with the strengths beta of mfs_evaluate, the stress tensor
+ * sigma = -p I + mu (grad u + grad u^T) of the representation (Eq. traction),
+ *   p(x) = sum_j (r . beta_j) / (4 pi r^3),   T(x) = sigma n = -3 / (4 pi) sum_j r (r . n)(r . beta_j) / r^5,
+ * r = x - y_j, over the sources of the point's suspension; both are independent of mu.  T is the force
+ * per area the fluid exerts across a surface with unit normal n (pointing into the fluid): over a
+ * body's surface it integrates to minus the force [f; t] = K_N^T lambda of a resistance solve
+ * (Eq. forces).  The traction converges more slowly with N than the velocity (a derivative on the
+ * surface, where the MFS error is largest).
+ *   points [npoints][3], normals [npoints][3] unit (required when traction != NULL), owner as for
+ *   mfs_evaluate; pressure [nrhs][npoints] and traction [nrhs][npoints][3] (either may be NULL, not
+ *   both); all host or device.  Errors as for mfs_evaluate; MFS_ERR_INVALID_ARG for a Laplace context.
+ */
+mfs_status mfs_evaluate_stress(mfs_ctx *ctx, const double *points, const double *normals, const int32_t *owner,
+                               int32_t npoints, double *pressure, double *traction, int32_t nrhs, void *stream);
+
 /* The pair-kernel variant the forward pair sums of this context use for `nrhs` right-hand sides
  * (1..max_rhs): the autotuner's pick once a solve or matvec with that nrhs has run (autotune = 1),
  * else the built-in default.  A policy name with its template arguments, e.g.

@@ -49,6 +49,7 @@ EXPORTED = [
     "mfs_solve_capacitance",
     "mfs_solve_resistance",
     "mfs_evaluate",
+    "mfs_evaluate_stress",
     "mfs_last_error",
     "mfs_setup_error",
     "mfs_destroy",
@@ -155,6 +156,7 @@ def load_library(path: Optional[str] = None):
     lib.mfs_solve_capacitance.argtypes = [vp, vp, vp, i32, ctypes.POINTER(_Info), vp]
     lib.mfs_solve_resistance.argtypes = [vp, vp, vp, vp, vp, i32, ctypes.POINTER(_Info), vp]
     lib.mfs_evaluate.argtypes = [vp, vp, vp, i32, vp, i32, vp]
+    lib.mfs_evaluate_stress.argtypes = [vp, vp, vp, vp, i32, vp, vp, i32, vp]
     lib.mfs_pair_variant.argtypes = [vp, i32]
     lib.mfs_pair_variant.restype = ctypes.c_char_p
     lib.mfs_last_error.argtypes = [vp]
@@ -403,6 +405,26 @@ class MFS:
         self._check(self._lib.mfs_evaluate(self._ctx, p.ptr, None if o is None else o.data_ptr(), npts,
                                            out.data_ptr(), nrhs, _stream_ptr(stream, p.device)))
         return out
+
+    def evaluate_stress(self, points, normals=None, owner=None, nrhs: int = 1, pressure: bool = True,
+                        traction: bool = True, stream=None):
+        """(pressure (nrhs, npoints) or None, traction (nrhs, npoints, 3) or None) of the last Stokes solve."""
+        torch = _torch()
+        p = _Arg(points)
+        npts = int(p.obj.shape[0])
+        n = _Arg(normals) if normals is not None else None
+        o = None
+        if owner is not None:
+            o = owner if isinstance(owner, torch.Tensor) else torch.as_tensor(np.asarray(owner))
+            o = o.to(torch.int32).contiguous()
+        pr = self._out((nrhs, npts), p) if pressure else None
+        tr = self._out((nrhs, npts, 3), p) if traction else None
+        self._check(self._lib.mfs_evaluate_stress(self._ctx, p.ptr, None if n is None else n.ptr,
+                                                  None if o is None else o.data_ptr(), npts,
+                                                  None if pr is None else pr.data_ptr(),
+                                                  None if tr is None else tr.data_ptr(), nrhs,
+                                                  _stream_ptr(stream, p.device)))
+        return pr, tr
 
     def mobility_vjp(self, dU, dOmega, want_force_grads: bool = False, stream=None):
         a, b = _Arg(dU), _Arg(dOmega)

@@ -115,6 +115,17 @@ cudaError_t dirichlet_rhs_stokes(const double *U, const double *Om, int nrhs, in
 cudaError_t dirichlet_rhs_laplace(const double *phi, int nrhs, int P, const int *body_tgt_off, int sum_M, double *b,
                                   cudaStream_t st);
 
+// ---- pressure and traction at evaluation points (stress.cu, Eq. traction) ----
+// FP32: points tgt (owner-relative float4 with owner bits), unit normals nrm [np][3] or null (no
+// traction), scalar-format source records, per-body record offsets, per-body suspension body range
+// [sb0, sb1); outputs p [nrhs][np], traction [nrhs][np][3] (either may be null).
+cudaError_t stress_f32(int nrhs, const float4 *tgt, const float *nrm, int np, const float *rec, int rec_floats,
+                       const int *rec_off, const int *sb0, const int *sb1, const double *centres, double *p_out,
+                       double *t_out, cudaStream_t st);
+cudaError_t stress_f64(int nrhs, const double *tgt_local, const int *tbody, const double *nrm, int np,
+                       const double *src_local, const int *src_off, int sum_N, const double *lam, const int *sb0,
+                       const int *sb1, const double *centres, double *p_out, double *t_out, cudaStream_t st);
+
 // ---- GMRES (gmres.cu): L independent lanes, lane l owns vector entries [seg_off[l], seg_off[l+1]) ----
 struct GmresDev {
     int L, m;                  // lanes, Krylov basis capacity (m <= 1023)

@@ -1884,6 +1884,94 @@ static __global__ void unsort_kernel(const double *in, const int *order, int np,
     }
 }
 
+// Evaluation points grouped by owner body (counting sort): order[j] is the caller's index of the j-th
+// grouped point, toff[k] the first grouped point of body k; t4 / t64 the points relative to their
+// owner's centre (FP32 with the owner id bits / FP64), nrm the grouped unit normals when given.
+struct EvalTargets {
+    std::vector<int> toff, order, tbody;
+    std::vector<float4> t4;
+    std::vector<double> t64;
+    std::vector<float> nrm32;
+    std::vector<double> nrm64;
+};
+
+static mfs_status group_targets(mfs_ctx *ctx, const double *points, const double *normals, const int32_t *owner,
+                                int np, EvalTargets &e) {
+    const int P = ctx->P;
+    if (!owner && ctx->S > 1) {
+        ctx->last_error = "evaluation: owner bodies are required with several suspensions";
+        return MFS_ERR_INVALID_ARG;
+    }
+    std::vector<double> pts(3 * (size_t)np), nv;
+    std::vector<int> own(np);
+    CK(cudaMemcpy(pts.data(), points, sizeof(double) * pts.size(), cudaMemcpyDefault));
+    if (normals) {
+        nv.resize(3 * (size_t)np);
+        CK(cudaMemcpy(nv.data(), normals, sizeof(double) * nv.size(), cudaMemcpyDefault));
+    }
+    if (owner) {
+        CK(cudaMemcpy(own.data(), owner, sizeof(int) * np, cudaMemcpyDefault));
+    } else {  // nearest body centre (single suspension)
+        for (int i = 0; i < np; ++i) {
+            double best = 1e300;
+            int bk = 0;
+            for (int k = 0; k < P; ++k) {
+                double d2 = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    const double d = pts[3 * (size_t)i + a] - ctx->centres[3 * (size_t)k + a];
+                    d2 += d * d;
+                }
+                if (d2 < best) {
+                    best = d2;
+                    bk = k;
+                }
+            }
+            own[i] = bk;
+        }
+    }
+    e.toff.assign(P + 1, 0);
+    e.order.resize(np);
+    e.tbody.resize(np);
+    for (int i = 0; i < np; ++i) {
+        bool finite = std::isfinite(pts[3 * (size_t)i]) && std::isfinite(pts[3 * (size_t)i + 1]) &&
+                      std::isfinite(pts[3 * (size_t)i + 2]);
+        if (normals)
+            finite = finite && std::isfinite(nv[3 * (size_t)i]) && std::isfinite(nv[3 * (size_t)i + 1]) &&
+                     std::isfinite(nv[3 * (size_t)i + 2]);
+        if (own[i] < 0 || own[i] >= P || !finite) {
+            ctx->last_error = "evaluation: owner out of range or non-finite point or normal";
+            return MFS_ERR_INVALID_ARG;
+        }
+        e.toff[own[i] + 1]++;
+    }
+    for (int k = 0; k < P; ++k) e.toff[k + 1] += e.toff[k];
+    e.t4.resize(np);
+    e.t64.resize(3 * (size_t)np);
+    if (normals) {
+        e.nrm32.resize(3 * (size_t)np);
+        e.nrm64.resize(3 * (size_t)np);
+    }
+    std::vector<int> fill(e.toff.begin(), e.toff.end() - 1);
+    for (int i = 0; i < np; ++i) {
+        const int k = own[i], j = fill[k]++;
+        e.order[j] = i;
+        e.tbody[j] = k;
+        double x[3];
+        for (int a = 0; a < 3; ++a) {
+            x[a] = pts[3 * (size_t)i + a] - ctx->centres[3 * (size_t)k + a];
+            e.t64[3 * (size_t)j + a] = x[a];
+            if (normals) {
+                e.nrm64[3 * (size_t)j + a] = nv[3 * (size_t)i + a];
+                e.nrm32[3 * (size_t)j + a] = (float)nv[3 * (size_t)i + a];
+            }
+        }
+        float kb;
+        std::memcpy(&kb, &k, sizeof(float));  // body id stored as int bits
+        e.t4[j] = make_float4((float)x[0], (float)x[1], (float)x[2], kb);
+    }
+    return MFS_OK;
+}
+
 namespace {
 // The strengths of the representation of the last solve, [nrhs][sum_N][D] into ctx->lam_d:
 // mobility (I - L) S_L^+ gamma + lambda_0 (Eq. multirep), elastance (I - L) S_L^+ gamma + alpha_0
@@ -1922,65 +2010,15 @@ mfs_status mfs_evaluate(mfs_ctx *ctx, const double *points, const int32_t *owner
         ctx->last_error = "mfs_evaluate needs a preceding solve with the same nrhs";
         return MFS_ERR_INVALID_ARG;
     }
-    if (!owner && ctx->S > 1) {
-        ctx->last_error = "mfs_evaluate: owner bodies are required with several suspensions";
-        return MFS_ERR_INVALID_ARG;
-    }
     if (npoints == 0) return MFS_OK;
     cudaStream_t st = (cudaStream_t)stream;
     const int P = ctx->P, D = ctx->D, np = npoints;
-    // points and owners on the host: the owner grouping is set up there
-    std::vector<double> pts(3 * (size_t)np);
-    std::vector<int> own(np);
-    CK(cudaMemcpy(pts.data(), points, sizeof(double) * pts.size(), cudaMemcpyDefault));
-    if (owner) {
-        CK(cudaMemcpy(own.data(), owner, sizeof(int) * np, cudaMemcpyDefault));
-    } else {  // nearest body centre (single suspension)
-        for (int i = 0; i < np; ++i) {
-            double best = 1e300;
-            int bk = 0;
-            for (int k = 0; k < P; ++k) {
-                double d2 = 0.0;
-                for (int a = 0; a < 3; ++a) {
-                    const double d = pts[3 * (size_t)i + a] - ctx->centres[3 * (size_t)k + a];
-                    d2 += d * d;
-                }
-                if (d2 < best) {
-                    best = d2;
-                    bk = k;
-                }
-            }
-            own[i] = bk;
-        }
-    }
-    std::vector<int> toff(P + 1, 0), order(np), tbody(np);
-    for (int i = 0; i < np; ++i) {
-        if (own[i] < 0 || own[i] >= P || !std::isfinite(pts[3 * (size_t)i]) || !std::isfinite(pts[3 * (size_t)i + 1]) ||
-            !std::isfinite(pts[3 * (size_t)i + 2])) {
-            ctx->last_error = "mfs_evaluate: owner out of range or non-finite point";
-            return MFS_ERR_INVALID_ARG;
-        }
-        toff[own[i] + 1]++;
-    }
-    for (int k = 0; k < P; ++k) toff[k + 1] += toff[k];
-    std::vector<float4> t4(np);
-    std::vector<double> t64(3 * (size_t)np);
-    {
-        std::vector<int> fill(toff.begin(), toff.end() - 1);
-        for (int i = 0; i < np; ++i) {
-            const int k = own[i], j = fill[k]++;
-            order[j] = i;
-            tbody[j] = k;
-            double x[3];
-            for (int a = 0; a < 3; ++a) {
-                x[a] = pts[3 * (size_t)i + a] - ctx->centres[3 * (size_t)k + a];
-                t64[3 * (size_t)j + a] = x[a];
-            }
-            float kb;
-            std::memcpy(&kb, &k, sizeof(float));  // body id stored as int bits
-            t4[j] = make_float4((float)x[0], (float)x[1], (float)x[2], kb);
-        }
-    }
+    EvalTargets et;
+    CKS(group_targets(ctx, points, nullptr, owner, np, et));
+    std::vector<int> &toff = et.toff, &order = et.order, &tbody = et.tbody;
+    std::vector<float4> &t4 = et.t4;
+    std::vector<double> &t64 = et.t64;
+    (void)P;
     Staged oo;
     CKS(stage_out_alloc(ctx, oo, out, (size_t)nrhs * np * D));
     float4 *t4_d = nullptr;
@@ -2037,6 +2075,106 @@ mfs_status mfs_evaluate(mfs_ctx *ctx, const double *points, const int32_t *owner
                                                                                           nrhs, oo.d);
         CK(cudaGetLastError());
         CKS(stage_out_finish(ctx, oo, st));
+        return check_device_error(ctx, st);
+    }();
+    cleanup();
+    return rc;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+mfs_status mfs_evaluate_stress(mfs_ctx *ctx, const double *points, const double *normals, const int32_t *owner,
+                               int32_t npoints, double *pressure, double *traction, int32_t nrhs, void *stream) {
+    if (!ctx || npoints < 0 || nrhs < 1 || (npoints > 0 && (!points || (!pressure && !traction))) ||
+        (traction && !normals)) {
+        if (ctx) ctx->last_error = "mfs_evaluate_stress: invalid argument";
+        return MFS_ERR_INVALID_ARG;
+    }
+    if (ctx->kind != MFS_STOKES) {
+        ctx->last_error = "mfs_evaluate_stress needs a Stokes context";
+        return MFS_ERR_INVALID_ARG;
+    }
+    if (ctx->last_solve == 0 || ctx->last_nrhs != nrhs) {
+        ctx->last_error = "mfs_evaluate_stress needs a preceding solve with the same nrhs";
+        return MFS_ERR_INVALID_ARG;
+    }
+    if (npoints == 0) return MFS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int P = ctx->P, np = npoints;
+    EvalTargets et;
+    CKS(group_targets(ctx, points, traction ? normals : nullptr, owner, np, et));
+    // per body: the body range of its suspension
+    std::vector<int> sb0(P), sb1(P);
+    for (int s = 0; s < ctx->S; ++s)
+        for (int k = ctx->body_off[s]; k < ctx->body_off[s + 1]; ++k) {
+            sb0[k] = ctx->body_off[s];
+            sb1[k] = ctx->body_off[s + 1];
+        }
+    Staged po, to;
+    if (pressure) CKS(stage_out_alloc(ctx, po, pressure, (size_t)nrhs * np));
+    if (traction) CKS(stage_out_alloc(ctx, to, traction, (size_t)nrhs * np * 3));
+    float4 *t4_d = nullptr;
+    float *n32_d = nullptr;
+    int *order_d = nullptr, *tbody_d = nullptr, *sb0_d = nullptr, *sb1_d = nullptr;
+    double *t64_d = nullptr, *n64_d = nullptr, *ps_d = nullptr, *ts_d = nullptr, *tmp_d = nullptr;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(st);
+        void *ps[] = {t4_d, n32_d, order_d, tbody_d, sb0_d, sb1_d, t64_d, n64_d, ps_d, ts_d, tmp_d};
+        for (void *p : ps) ctx->release(p);
+    };
+    mfs_status rc = [&]() -> mfs_status {
+        CK(ctx->alloc(&order_d, np));
+        CK(ctx->alloc(&sb0_d, P));
+        CK(ctx->alloc(&sb1_d, P));
+        CK(ctx->alloc(&tmp_d, (size_t)nrhs * ctx->sumN * 3));
+        if (pressure) CK(ctx->alloc(&ps_d, (size_t)nrhs * np));
+        if (traction) CK(ctx->alloc(&ts_d, (size_t)nrhs * np * 3));
+        CK(cudaMemcpyAsync(order_d, et.order.data(), sizeof(int) * np, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(sb0_d, sb0.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(sb1_d, sb1.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st));
+        CKS(last_strengths(ctx, nrhs, tmp_d, st));
+        if (ctx->opt.precision == 1) {
+            CK(ctx->alloc(&t64_d, 3 * (size_t)np));
+            CK(ctx->alloc(&tbody_d, np));
+            CK(cudaMemcpyAsync(t64_d, et.t64.data(), sizeof(double) * et.t64.size(), cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(tbody_d, et.tbody.data(), sizeof(int) * np, cudaMemcpyHostToDevice, st));
+            if (traction) {
+                CK(ctx->alloc(&n64_d, 3 * (size_t)np));
+                CK(cudaMemcpyAsync(n64_d, et.nrm64.data(), sizeof(double) * et.nrm64.size(), cudaMemcpyHostToDevice,
+                                   st));
+            }
+            CK(stress_f64(nrhs, t64_d, tbody_d, n64_d, np, ctx->src_local64_d, ctx->src_off_d, ctx->sumN, ctx->lam_d,
+                          sb0_d, sb1_d, ctx->centres_d, ps_d, ts_d, st));
+        } else {
+            CK(ctx->alloc(&t4_d, np));
+            CK(cudaMemcpyAsync(t4_d, et.t4.data(), sizeof(float4) * np, cudaMemcpyHostToDevice, st));
+            if (traction) {
+                CK(ctx->alloc(&n32_d, 3 * (size_t)np));
+                CK(cudaMemcpyAsync(n32_d, et.nrm32.data(), sizeof(float) * et.nrm32.size(), cudaMemcpyHostToDevice,
+                                   st));
+            }
+            // scalar-format records: position then the strengths of every rhs
+            CK(pack_sources(3, nrhs, 0, ctx->src_pos_d, ctx->rec_pt_d, ctx->lam_d, ctx->sumN, ctx->nrec, ctx->rec_d,
+                            st));
+            CK(stress_f32(nrhs, t4_d, n32_d, np, ctx->rec_d, pair_record_floats(3, nrhs, 0), ctx->rec_off_d, sb0_d,
+                          sb1_d, ctx->centres_d, ps_d, ts_d, st));
+        }
+        if (pressure) {
+            const size_t n = (size_t)nrhs * np;
+            unsort_kernel<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, st>>>(ps_d, order_d, np, 1,
+                                                                                              nrhs, po.d);
+            CK(cudaGetLastError());
+            CKS(stage_out_finish(ctx, po, st));
+        }
+        if (traction) {
+            const size_t n = (size_t)nrhs * np * 3;
+            unsort_kernel<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, st>>>(ts_d, order_d, np, 3,
+                                                                                              nrhs, to.d);
+            CK(cudaGetLastError());
+            CKS(stage_out_finish(ctx, to, st));
+        }
         return check_device_error(ctx, st);
     }();
     cleanup();

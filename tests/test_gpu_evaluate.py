@@ -144,3 +144,37 @@ def test_surface_residual_full_size():
     # M = 1200 spheres at gaps >= 0.1: a discretisation-level residual, far below O(1)
     assert eps.max() < 1e-2 and np.sqrt(np.mean(eps**2)) < 1e-3
     ctx.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 2e-6), (1, 1e-10)])
+def test_stress_after_resistance_and_mobility(precision, tol):
+    """Pressure and traction (Eq. traction) at surface and exterior points against the oracle's sums."""
+    wl = _mixed("stokes", nsusp=2)
+    ctx = _ctx(wl, precision=precision, gmres_tol=1e-7 if precision == 0 else 1e-13)
+    pr = Problem(wl)
+    pts, own = _points(wl, pr, np.random.default_rng(6), n_ext=100)
+    nrm = np.random.default_rng(7).standard_normal(pts.shape)
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    rng = np.random.default_rng(8)
+    V, Om = rng.standard_normal((1, wl.num_bodies, 3)), rng.standard_normal((1, wl.num_bodies, 3))
+    ctx.solve_resistance(V, Om)
+    p, T = ctx.evaluate_stress(pts, nrm, own)
+    _, _, info = pr.solve_resistance(V[0], Om[0], tol=1e-13)
+    pref, Tref = np.zeros(len(pts)), np.zeros((len(pts), 3))
+    for s in range(wl.num_suspensions):
+        b = list(pr.suspension_bodies(s))
+        sel = np.isin(own, b)
+        pref[sel], Tref[sel] = pr.evaluate_stress(b, pr.strengths_dirichlet(b, info[s].x), pts[sel], nrm[sel])
+    assert _rel(p.numpy()[0], pref) < tol and _rel(T.numpy()[0], Tref) < tol
+    # after a mobility solve: pressure only
+    ctx.solve_mobility(wl.F[:1], wl.T[:1])
+    p, T = ctx.evaluate_stress(pts, owner=own, traction=False)
+    assert T is None
+    _, _, info = pr.solve_mobility(wl.F[0], wl.T[0], tol=1e-13)
+    for s in range(wl.num_suspensions):
+        b = list(pr.suspension_bodies(s))
+        sel = np.isin(own, b)
+        pref[sel], _ = pr.evaluate_stress(b, pr.total_strengths_mobility(b, info[s].x, wl.F[0], wl.T[0]),
+                                         pts[sel], nrm[sel])
+    assert _rel(p.numpy()[0], pref) < tol
+    ctx.close()
