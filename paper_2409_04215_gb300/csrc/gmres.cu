@@ -4,6 +4,8 @@
 // process, Hessenberg matrix and Givens rotations, so independent problems iterate together
 // and stop separately (converged lanes are masked).  Orthogonalisation is classical
 // Gram-Schmidt applied twice (CGS2); every reduction is deterministic (fixed block partials).
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -43,16 +45,28 @@ __global__ void mdot_kernel(GmresDev gd, const double *w, int j) {
     if (threadIdx.x == 0) gd.part[((size_t)l * gd.part_blocks + b) * (gd.m + 1) + i] = acc;
 }
 
-// hbuf[l][i] (+)= sum_b part[l][b][i]   (grid: L, threads >= j+1)
+// Sum over the block partials of lane l, entry i, by one warp (lanes stride over the blocks, then a
+// fixed shuffle tree: the same order every call).
+__device__ __forceinline__ double warp_part_sum(const GmresDev &gd, int l, int i) {
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int b = lane; b < gd.part_blocks; b += 32) s += gd.part[((size_t)l * gd.part_blocks + b) * (gd.m + 1) + i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// hbuf[l][i] (+)= sum_b part[l][b][i]   (grid: L, one warp per entry i <= j, warps striding)
 __global__ void mdot_reduce_kernel(GmresDev gd, int j, double *htmp, int accumulate) {
     const int l = blockIdx.x;
     if (!gd.active[l]) return;
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < gd.part_blocks; ++b) s += gd.part[((size_t)l * gd.part_blocks + b) * (gd.m + 1) + i];
-        htmp[(size_t)l * (gd.m + 1) + i] = s;
-        if (accumulate) gd.hbuf[(size_t)l * (gd.m + 1) + i] += s;
-        else gd.hbuf[(size_t)l * (gd.m + 1) + i] = s;
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = warp; i <= j; i += nw) {
+        const double s = warp_part_sum(gd, l, i);
+        if ((threadIdx.x & 31) == 0) {
+            htmp[(size_t)l * (gd.m + 1) + i] = s;
+            if (accumulate) gd.hbuf[(size_t)l * (gd.m + 1) + i] += s;
+            else gd.hbuf[(size_t)l * (gd.m + 1) + i] = s;
+        }
     }
 }
 
@@ -97,9 +111,13 @@ __global__ void norm_part_kernel(GmresDev gd, const double *x, int all_lanes) {
 __global__ void normalise_kernel(GmresDev gd, const double *x, double *vdst, double *norm_out, int all_lanes) {
     const int b = blockIdx.x, l = blockIdx.y;
     if (!all_lanes && !gd.active[l]) return;
-    double s = 0.0;
-    for (int q = 0; q < gd.part_blocks; ++q) s += gd.part[((size_t)l * gd.part_blocks + q) * (gd.m + 1)];
-    const double nrm = sqrt(s);
+    __shared__ double nrm_sh;
+    if (threadIdx.x < 32) {  // the first warp sums the block partials of the squared norm
+        const double s = warp_part_sum(gd, l, 0);
+        if (threadIdx.x == 0) nrm_sh = sqrt(s);
+    }
+    __syncthreads();
+    const double nrm = nrm_sh;
     if (b == 0 && threadIdx.x == 0 && norm_out) norm_out[l] = nrm;
     const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
     long long e0, e1;
@@ -203,7 +221,7 @@ cudaError_t gmres_init(GmresDev &gd, const double *b, cudaStream_t st) {
 
 cudaError_t gmres_arnoldi(GmresDev &gd, double *w, int j, cudaStream_t st) {
     dim3 grid(gd.part_blocks, gd.L), gdot(gd.part_blocks, gd.L, j + 1);
-    const int rt = (j + 1) < 1024 ? ((j + 32) / 32) * 32 : 1024;
+    const int rt = 32 * std::min(j + 1, 16);  // one warp per Hessenberg entry, at most 16 warps
     for (int pass = 0; pass < 2; ++pass) {  // CGS2
         mdot_kernel<<<gdot, GM_THREADS, 0, st>>>(gd, w, j);
         mdot_reduce_kernel<<<gd.L, rt, 0, st>>>(gd, j, gd.htmp, pass);
