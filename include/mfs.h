@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define MFS_ABI_VERSION 2
+#define MFS_ABI_VERSION 3
 
 typedef struct mfs_ctx mfs_ctx; /* opaque; owns all internal device memory */
 
@@ -83,10 +83,14 @@ typedef struct {
     int32_t profile;   /* 1: bracket every pair-kernel launch with CUDA events (no host sync) and report
                           their summed device time in mfs_solve_info.ms_pairs; default 0 */
     int32_t tensor_cores; /* precision-0 one-body apply (Eq. pseudo) on the tensor cores (tcgen05 TF32 MMAs,
-                             FP32 accumulation over short K runs, sums in FP64), operands cut from FP64 into
-                             TF32 pieces: 1 = three pieces, six products (FP32-level products);
+                             FP32 accumulation over short K runs, double-float sums), operands cut from FP64
+                             into TF32 pieces: 1 = three pieces, six products (FP32-level products);
                              2 = two pieces, three products (3xTF32, ~2^-21 products);
                              0 = CUDA-core split-K FP32 GEMM (TwoSum-compensated slices).  Default 1 */
+    int32_t pair_variant; /* >= 0: use this entry of the pair-kernel table (mfs_pair_variant_info) for its
+                             (d, nrhs) instead of the autotuner's pick; it must be a forward pair-sum
+                             variant of the context's d, else mfs_setup fails with MFS_ERR_INVALID_ARG.
+                             -1 (default): autotune or the built-in default. */
 } mfs_options;
 
 typedef struct {
@@ -274,6 +278,11 @@ mfs_status mfs_evaluate_stress(mfs_ctx *ctx, const double *points, const double 
  * "PackedStokes<1,3,128>" (rhs, target pairs per thread, threads per CTA).  Never NULL; "" for an
  * invalid ctx or nrhs.  Static storage.  Not in the paper: a profiling aid. */
 const char *mfs_pair_variant(const mfs_ctx *ctx, int32_t nrhs);
+
+/* Entry `index` of the pair-kernel table: its name (as mfs_pair_variant reports it), dimension d (1 or
+ * 3), right-hand sides and whether it is the adjoint's centre-gradient kernel (grad = 1, not a pair
+ * sum).  NULL past the end of the table; the out-pointers may be NULL.  Static storage. */
+const char *mfs_pair_variant_info(int32_t index, int32_t *d, int32_t *nrhs, int32_t *grad);
 
 /* Text of the last error on this context (never NULL; "" when none).  Valid until the next call. */
 const char *mfs_last_error(const mfs_ctx *ctx);

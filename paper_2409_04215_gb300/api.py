@@ -44,6 +44,7 @@ EXPORTED = [
     "mfs_mobility_vjp",
     "mfs_stokeslet_sum_noalloc",
     "mfs_pair_variant",
+    "mfs_pair_variant_info",
     "mfs_dirichlet_apply",
     "mfs_dirichlet_matvec",
     "mfs_solve_capacitance",
@@ -89,6 +90,7 @@ class Options(ctypes.Structure):
         ("max_rhs", ctypes.c_int32),
         ("profile", ctypes.c_int32),
         ("tensor_cores", ctypes.c_int32),
+        ("pair_variant", ctypes.c_int32),
     ]
 
 
@@ -124,7 +126,7 @@ class SolveInfo:
     status: int
 
 
-ABI_VERSION = 2  # MFS_ABI_VERSION of the header these structures mirror
+ABI_VERSION = 3  # MFS_ABI_VERSION of the header these structures mirror
 
 
 def load_library(path: Optional[str] = None):
@@ -157,6 +159,8 @@ def load_library(path: Optional[str] = None):
     lib.mfs_solve_resistance.argtypes = [vp, vp, vp, vp, vp, i32, ctypes.POINTER(_Info), vp]
     lib.mfs_evaluate.argtypes = [vp, vp, vp, i32, vp, i32, vp]
     lib.mfs_evaluate_stress.argtypes = [vp, vp, vp, vp, i32, vp, vp, i32, vp]
+    lib.mfs_pair_variant_info.argtypes = [i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.mfs_pair_variant_info.restype = ctypes.c_char_p
     lib.mfs_pair_variant.argtypes = [vp, i32]
     lib.mfs_pair_variant.restype = ctypes.c_char_p
     lib.mfs_last_error.argtypes = [vp]
@@ -171,6 +175,19 @@ def load_library(path: Optional[str] = None):
         raise RuntimeError(f"libmfs.so ABI {lib.mfs_abi_version()} != {ABI_VERSION}: rebuild the library")
     _lib = lib
     return lib
+
+
+def pair_variants():
+    """The pair-kernel table: [(index, name, d, nrhs, grad)]."""
+    lib = load_library()
+    out, i = [], 0
+    while True:
+        d, r, g = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        name = lib.mfs_pair_variant_info(i, ctypes.byref(d), ctypes.byref(r), ctypes.byref(g))
+        if name is None:
+            return out
+        out.append((i, name.decode(), d.value, r.value, g.value))
+        i += 1
 
 
 def default_options(**kw) -> Options:

@@ -842,9 +842,20 @@ void mfs_default_options(mfs_options *opt) {
     opt->max_rhs = 4;
     opt->profile = 0;
     opt->tensor_cores = 1;
+    opt->pair_variant = -1;
 }
 
 int32_t mfs_abi_version(void) { return MFS_ABI_VERSION; }
+
+const char *mfs_pair_variant_info(int32_t index, int32_t *d, int32_t *nrhs, int32_t *grad) {
+    int count = 0;
+    const PairVariant *vv = pair_variants(&count);
+    if (index < 0 || index >= count) return nullptr;
+    if (d) *d = vv[index].D;
+    if (nrhs) *nrhs = vv[index].nrhs;
+    if (grad) *grad = vv[index].grad;
+    return vv[index].name;
+}
 
 const char *mfs_pair_variant(const mfs_ctx *ctx, int32_t nrhs) {
     if (!ctx || nrhs < 1 || nrhs > 4 || nrhs > ctx->opt.max_rhs) return "";
@@ -1366,6 +1377,17 @@ mfs_status mfs_setup(mfs_ctx **out, mfs_kind kind, const mfs_bodies *bodies, int
         g_setup_error = "mfs_setup: max_iter above restart is not supported (no restarted GMRES)";
         return MFS_ERR_INVALID_ARG;
     }
+    if (ctx->opt.pair_variant >= 0) {  // a forced pair-kernel variant: a forward sum of this kind's d
+        int count = 0;
+        const PairVariant *vv = pair_variants(&count);
+        const int pv = ctx->opt.pair_variant;
+        if (pv >= count || vv[pv].grad || vv[pv].D != (kind == MFS_STOKES ? 3 : 1) ||
+            vv[pv].nrhs > ctx->opt.max_rhs) {
+            g_setup_error = "mfs_setup: pair_variant is not a forward pair-sum variant of this kind";
+            return MFS_ERR_INVALID_ARG;
+        }
+        ctx->best_variant[kind == MFS_STOKES][vv[pv].nrhs] = pv;
+    }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -1375,7 +1397,7 @@ mfs_status mfs_setup(mfs_ctx **out, mfs_kind kind, const mfs_bodies *bodies, int
     }
     cudaStream_t st = (cudaStream_t)stream;
     mfs_status s = setup_impl(ctx.get(), kind, bodies, num_shapes, proxy, colloc, st);
-    if (s == MFS_OK && ctx->opt.autotune && ctx->opt.precision != 1) {
+    if (s == MFS_OK && ctx->opt.autotune && ctx->opt.precision != 1 && ctx->best_variant[kind == MFS_STOKES][1] < 0) {
         // tune the single-rhs variant now; other nrhs on first use
         s = autotune(ctx.get(), 1, st);
     }

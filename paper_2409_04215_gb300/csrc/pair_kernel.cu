@@ -468,6 +468,108 @@ struct PackedStokesReg : PolicyBase {
     }
 };
 
+// Laplace pairs (K2) in packed f32x2 arithmetic: two targets per instruction, as the packed
+// Stokeslet; per pair 3 subtractions, r^2, one MUFU rsqrt and one FMA per rhs.  The MUFU then bounds
+// the kernel (16 rsqrt per clock per SM against 128 FP32 lanes).
+template <int NRHS, int TP, int NT>
+struct PackedLaplaceReg : PolicyBase {
+    static constexpr int D = 1;
+    static constexpr int C = NRHS;
+    static constexpr int REC = rec_floats(1, NRHS, true);
+    static constexpr int TPT = 2 * TP;
+    static constexpr int T = TPT;
+    static constexpr int PSM = 0;
+    float3 tp[T];
+    int tb[T];
+    float hi[T][C], lo[T][C];
+    u64 bsum[TP][C];
+
+    __device__ __forceinline__ void init(float *, int) {}
+    __device__ __forceinline__ void set_target(int j, float4 p) {
+        tp[j] = make_float3(p.x, p.y, p.z);
+        tb[j] = __float_as_int(p.w);
+    }
+    __device__ __forceinline__ void reset() {
+#pragma unroll
+        for (int j = 0; j < T; ++j)
+#pragma unroll
+            for (int c = 0; c < C; ++c) hi[j][c] = lo[j][c] = 0.f;
+#pragma unroll
+        for (int p = 0; p < TP; ++p)
+#pragma unroll
+            for (int c = 0; c < C; ++c) bsum[p][c] = 0ull;
+    }
+    __device__ __forceinline__ void compute(const float *sb, int nrec, const float (*dc)[3], int kb0) {
+        u64 xt[TP][3];
+#pragma unroll
+        for (int p = 0; p < TP; ++p) {
+            const int r0 = tb[2 * p] - kb0, r1 = tb[2 * p + 1] - kb0;
+            xt[p][0] = f2_pack(dc[r0][0] + tp[2 * p].x, dc[r1][0] + tp[2 * p + 1].x);
+            xt[p][1] = f2_pack(dc[r0][1] + tp[2 * p].y, dc[r1][1] + tp[2 * p + 1].y);
+            xt[p][2] = f2_pack(dc[r0][2] + tp[2 * p].z, dc[r1][2] + tp[2 * p + 1].z);
+        }
+        for (int s0 = 0; s0 < nrec; s0 += MFS_BS) {
+            const int s1 = min(s0 + MFS_BS, nrec);
+            u64 blk[TP][C];
+#pragma unroll
+            for (int p = 0; p < TP; ++p)
+#pragma unroll
+                for (int c = 0; c < C; ++c) blk[p][c] = 0ull;
+            for (int s = s0; s < s1; s += 4) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    u64 rec[REC / 2];
+#pragma unroll
+                    for (int v = 0; v < REC / 4; ++v) {
+                        const ulonglong2 f = reinterpret_cast<const ulonglong2 *>(sb + (s + q) * REC)[v];
+                        rec[2 * v] = f.x;
+                        rec[2 * v + 1] = f.y;
+                    }
+#pragma unroll
+                    for (int p = 0; p < TP; ++p) {
+                        const u64 dx = f2_sub(xt[p][0], rec[0]);
+                        const u64 dy = f2_sub(xt[p][1], rec[1]);
+                        const u64 dz = f2_sub(xt[p][2], rec[2]);
+                        const u64 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
+                        float a, b;
+                        f2_unpack(r2, a, b);
+                        const u64 ri = f2_pack(rsqrt_ftz(a), rsqrt_ftz(b));
+#pragma unroll
+                        for (int h = 0; h < NRHS; ++h) blk[p][h] = f2_fma(rec[3 + h], ri, blk[p][h]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < TP; ++p)
+#pragma unroll
+                for (int c = 0; c < C; ++c) bsum[p][c] = f2_add(bsum[p][c], blk[p][c]);
+        }
+    }
+    __device__ __forceinline__ void end_body(int body, bool include_self) {
+#pragma unroll
+        for (int p = 0; p < TP; ++p) {
+            const bool k0 = include_self || (tb[2 * p] != body);
+            const bool k1 = include_self || (tb[2 * p + 1] != body);
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                float v0, v1, s, e;
+                f2_unpack(bsum[p][c], v0, v1);
+                two_sum(hi[2 * p][c], k0 ? v0 : 0.f, s, e);
+                hi[2 * p][c] = s;
+                lo[2 * p][c] += e;
+                two_sum(hi[2 * p + 1][c], k1 ? v1 : 0.f, s, e);
+                hi[2 * p + 1][c] = s;
+                lo[2 * p + 1][c] += e;
+                bsum[p][c] = 0ull;
+            }
+        }
+    }
+    __device__ __forceinline__ float result(int j, int c, float &l) const {
+        l = lo[j][c];
+        return hi[j][c];
+    }
+};
+
 // Centre gradient for the adjoint: per pair, the gradient with respect to r = x_i - y_j of
 // w_i^T G(r) mu_j summed over right-hand sides,
 //   [ w_c (r.mu) + mu_c (w.r) - (w.mu) r_c - 3 (w.r)(r.mu) r_c / r^2 ] / r^3   (x 1/(8 pi mu) later),
@@ -891,6 +993,11 @@ static int occupancy_variant() {
     P(PackedStokes, 1, 3, 128)    \
     P(PackedStokes, 2, 1, 128)    \
     P(PackedStokes, 4, 1, 128)    \
+    P(PackedLaplaceReg, 1, 2, 128) \
+    P(PackedLaplaceReg, 1, 4, 128) \
+    P(PackedLaplaceReg, 1, 2, 256) \
+    P(PackedLaplaceReg, 2, 2, 128) \
+    P(PackedLaplaceReg, 4, 2, 128) \
     G(1, 4, 128)                  \
     G(2, 2, 128)                  \
     G(3, 2, 128)                  \
@@ -898,7 +1005,8 @@ static int occupancy_variant() {
 
 static const PairVariant kVariants[] = {
 #define S(D_, R_, T_, N_) {D_, R_, T_, N_, N_ * T_, 0, 0, "Scalar<" #D_ "," #R_ "," #T_ "," #N_ ">"},
-#define P(POL_, R_, TP_, N_) {3, R_, 2 * TP_, N_, N_ * 2 * TP_, 1, 0, #POL_ "<" #R_ "," #TP_ "," #N_ ">"},
+#define P(POL_, R_, TP_, N_) \
+    {POL_<R_, TP_, N_>::D, R_, 2 * TP_, N_, N_ * 2 * TP_, 1, 0, #POL_ "<" #R_ "," #TP_ "," #N_ ">"},
 #define G(R_, T_, N_) {3, R_, T_, N_, N_ * T_, 0, 1, "GradStokes<" #R_ "," #T_ "," #N_ ">"},
     MFS_VARIANTS(S, P, G)
 #undef S
@@ -970,6 +1078,7 @@ cudaError_t pack_sources(int D, int nrhs, int packed, const float4 *src_pos, con
     PK(3, 1, false) PK(3, 2, false) PK(3, 3, false) PK(3, 4, false)
     PK(1, 1, false) PK(1, 2, false) PK(1, 3, false) PK(1, 4, false)
     PK(3, 1, true) PK(3, 2, true) PK(3, 3, true) PK(3, 4, true)
+    PK(1, 1, true) PK(1, 2, true) PK(1, 3, true) PK(1, 4, true)
 #undef PK
     return cudaErrorInvalidValue;
 }

@@ -46,7 +46,7 @@ def test_library_loads_and_reports(lib_path):
     o = Options()
     lib.mfs_default_options(o)
     assert o.mu == 1.0 and o.gmres_tol == 1e-7 and o.max_rhs == 4 and o.precision == 0
-    assert o.tensor_cores == 1 and o.autotune == 1 and o.profile == 0
+    assert o.tensor_cores == 1 and o.autotune == 1 and o.profile == 0 and o.pair_variant == -1
     assert set(EXPORTED) == set(_declared())
 
 
@@ -89,3 +89,15 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_pair_variant_table(lib_path):
+    from paper_2409_04215_gb300.api import pair_variants
+
+    table = pair_variants()
+    names = [t[1] for t in table]
+    assert len(names) == len(set(names))
+    for d in (1, 3):  # every (d, nrhs) has at least one forward pair-sum variant
+        for r in (1, 2, 3, 4):
+            assert any(t[2] == d and t[3] == r and not t[4] for t in table), (d, r)
+    assert any(n.startswith("PackedLaplaceReg") for n in names) and any(n.startswith("GradStokes") for n in names)
