@@ -91,6 +91,10 @@ typedef struct {
                              (d, nrhs) instead of the autotuner's pick; it must be a forward pair-sum
                              variant of the context's d, else mfs_setup fails with MFS_ERR_INVALID_ARG.
                              -1 (default): autotune or the built-in default. */
+    int32_t graphs;       /* 1 (default): after the first GMRES iteration, the iteration loop runs as one CUDA
+                             graph with a device-side while node (the matvec and Arnoldi kernels read the
+                             iteration index from device memory; no host round trip per iteration).  Not
+                             with profile = 1, whose per-launch events need the host loop.  0: host loop. */
 } mfs_options;
 
 typedef struct {

@@ -91,6 +91,7 @@ class Options(ctypes.Structure):
         ("profile", ctypes.c_int32),
         ("tensor_cores", ctypes.c_int32),
         ("pair_variant", ctypes.c_int32),
+        ("graphs", ctypes.c_int32),
     ]
 
 

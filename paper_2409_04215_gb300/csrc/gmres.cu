@@ -31,18 +31,22 @@ __device__ __forceinline__ void lane_chunk(const GmresDev &gd, int l, int b, lon
     e1 = s0 + len * (b + 1) / gd.part_blocks;
 }
 
-// part[l][b][i] = sum over chunk b of lane l of V[i][e] * w[e], i = 0..j  (grid: PB x L x (j+1))
-__global__ void mdot_kernel(GmresDev gd, const double *w, int j) {
-    const int b = blockIdx.x, l = blockIdx.y, i = blockIdx.z;
-    if (!gd.active[l] || i > j) return;
+// part[l][b][i] = sum over chunk b of lane l of V[i][e] * w[e], i = 0..j  (grid: PB x L; the chunk of w
+// stays in L1 across i)
+__global__ void mdot_kernel(GmresDev gd, const double *w) {
+    const int b = blockIdx.x, l = blockIdx.y;
+    if (!gd.active[l]) return;
+    const int j = *gd.jcur;
     __shared__ double sh[32];
     long long e0, e1;
     lane_chunk(gd, l, b, e0, e1);
-    const double *v = gd.V + (size_t)i * gd.n;
-    double acc = 0.0;
-    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) acc += v[e] * w[e];
-    acc = block_sum(acc, sh);
-    if (threadIdx.x == 0) gd.part[((size_t)l * gd.part_blocks + b) * (gd.m + 1) + i] = acc;
+    for (int i = 0; i <= j; ++i) {
+        const double *v = gd.V + (size_t)i * gd.n;
+        double acc = 0.0;
+        for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) acc += v[e] * w[e];
+        acc = block_sum(acc, sh);
+        if (threadIdx.x == 0) gd.part[((size_t)l * gd.part_blocks + b) * (gd.m + 1) + i] = acc;
+    }
 }
 
 // Sum over the block partials of lane l, entry i, by one warp (lanes stride over the blocks, then a
@@ -56,9 +60,10 @@ __device__ __forceinline__ double warp_part_sum(const GmresDev &gd, int l, int i
 }
 
 // hbuf[l][i] (+)= sum_b part[l][b][i]   (grid: L, one warp per entry i <= j, warps striding)
-__global__ void mdot_reduce_kernel(GmresDev gd, int j, double *htmp, int accumulate) {
+__global__ void mdot_reduce_kernel(GmresDev gd, double *htmp, int accumulate) {
     const int l = blockIdx.x;
     if (!gd.active[l]) return;
+    const int j = *gd.jcur;
     const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int i = warp; i <= j; i += nw) {
         const double s = warp_part_sum(gd, l, i);
@@ -71,9 +76,10 @@ __global__ void mdot_reduce_kernel(GmresDev gd, int j, double *htmp, int accumul
 }
 
 // w -= sum_{i<=j} htmp[l][i] V[i]   (grid: PB x L)
-__global__ void update_kernel(GmresDev gd, double *w, const double *htmp, int j) {
+__global__ void update_kernel(GmresDev gd, double *w, const double *htmp) {
     const int b = blockIdx.x, l = blockIdx.y;
     if (!gd.active[l]) return;
+    const int j = *gd.jcur;
     __shared__ double h[1024];
     for (int i = threadIdx.x; i <= j; i += blockDim.x) h[i] = htmp[(size_t)l * (gd.m + 1) + i];
     __syncthreads();
@@ -107,10 +113,11 @@ __global__ void norm_part_kernel(GmresDev gd, const double *x, int all_lanes) {
     if (threadIdx.x == 0) gd.part[((size_t)l * gd.part_blocks + b) * (gd.m + 1)] = acc;
 }
 
-// v_dst = x / ||x|| per lane, norm taken from the partials (grid: PB x L)
+// v_dst = x / ||x|| per lane, norm taken from the partials (grid: PB x L); vdst = V[j+1] when null
 __global__ void normalise_kernel(GmresDev gd, const double *x, double *vdst, double *norm_out, int all_lanes) {
     const int b = blockIdx.x, l = blockIdx.y;
     if (!all_lanes && !gd.active[l]) return;
+    if (!vdst) vdst = gd.V + (size_t)(*gd.jcur + 1) * gd.n;
     __shared__ double nrm_sh;
     if (threadIdx.x < 32) {  // the first warp sums the block partials of the squared norm
         const double s = warp_part_sum(gd, l, 0);
@@ -136,9 +143,32 @@ __global__ void init_lanes_kernel(GmresDev gd) {
     gd.status[l] = isfinite(b) ? 0 : 2;
 }
 
+// done = no lane active, j = 0 (one thread)
+__global__ void init_done_kernel(GmresDev gd) {
+    int any = 0;
+    for (int l = 0; l < gd.L; ++l) any |= gd.active[l];
+    *gd.done = any ? 0 : 1;
+    *gd.jcur = 0;
+}
+
+__global__ void load_vj_kernel(GmresDev gd, double *vin) {
+    const double *v = gd.V + (size_t)(*gd.jcur) * gd.n;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < gd.n; e += (long long)gridDim.x * blockDim.x)
+        vin[e] = v[e];
+}
+
+// After column j: continue with j + 1 unless every lane stopped or the basis is full.
+__global__ void advance_kernel(GmresDev gd, cudaGraphConditionalHandle cond, int cond_valid) {
+    const int j = *gd.jcur;
+    const int more = (*gd.done == 0) && (j + 1 < gd.m);
+    if (more) *gd.jcur = j + 1;
+    if (cond_valid) cudaGraphSetConditional(cond, more ? 1u : 0u);
+}
+
 // Givens update of column j for every active lane; sets done when no lane is active.
-__global__ void givens_kernel(GmresDev gd, int j, const double *hn) {
+__global__ void givens_kernel(GmresDev gd, const double *hn) {
     const int l = threadIdx.x;
+    const int j = *gd.jcur;
     __shared__ int any_active;
     if (l == 0) any_active = 0;
     __syncthreads();
@@ -216,20 +246,30 @@ cudaError_t gmres_init(GmresDev &gd, const double *b, cudaStream_t st) {
     cudaMemsetAsync(gd.H, 0, sizeof(double) * (size_t)gd.L * (gd.m + 1) * gd.m, st);
     cudaMemsetAsync(gd.g, 0, sizeof(double) * (size_t)gd.L * (gd.m + 1), st);
     init_lanes_kernel<<<(gd.L + 127) / 128, 128, 0, st>>>(gd);
+    init_done_kernel<<<1, 1, 0, st>>>(gd);
     return cudaGetLastError();
 }
 
-cudaError_t gmres_arnoldi(GmresDev &gd, double *w, int j, cudaStream_t st) {
-    dim3 grid(gd.part_blocks, gd.L), gdot(gd.part_blocks, gd.L, j + 1);
-    const int rt = 32 * std::min(j + 1, 16);  // one warp per Hessenberg entry, at most 16 warps
+cudaError_t gmres_arnoldi(GmresDev &gd, double *w, cudaStream_t st) {
+    dim3 grid(gd.part_blocks, gd.L);
     for (int pass = 0; pass < 2; ++pass) {  // CGS2
-        mdot_kernel<<<gdot, GM_THREADS, 0, st>>>(gd, w, j);
-        mdot_reduce_kernel<<<gd.L, rt, 0, st>>>(gd, j, gd.htmp, pass);
-        update_kernel<<<grid, GM_THREADS, 0, st>>>(gd, w, gd.htmp, j);
+        mdot_kernel<<<grid, GM_THREADS, 0, st>>>(gd, w);
+        mdot_reduce_kernel<<<gd.L, 512, 0, st>>>(gd, gd.htmp, pass);  // 16 warps over the entries i <= j
+        update_kernel<<<grid, GM_THREADS, 0, st>>>(gd, w, gd.htmp);
     }
     norm_part_kernel<<<grid, GM_THREADS, 0, st>>>(gd, w, 0);
-    normalise_kernel<<<grid, GM_THREADS, 0, st>>>(gd, w, gd.V + (size_t)(j + 1) * gd.n, gd.hn, 0);
-    givens_kernel<<<1, 256, 0, st>>>(gd, j, gd.hn);
+    normalise_kernel<<<grid, GM_THREADS, 0, st>>>(gd, w, nullptr, gd.hn, 0);
+    givens_kernel<<<1, 256, 0, st>>>(gd, gd.hn);
+    return cudaGetLastError();
+}
+
+cudaError_t gmres_load_vj(GmresDev &gd, double *vin, cudaStream_t st) {
+    load_vj_kernel<<<1024, 256, 0, st>>>(gd, vin);
+    return cudaGetLastError();
+}
+
+cudaError_t gmres_advance(GmresDev &gd, cudaGraphConditionalHandle cond, int cond_valid, cudaStream_t st) {
+    advance_kernel<<<1, 1, 0, st>>>(gd, cond, cond_valid);
     return cudaGetLastError();
 }
 

@@ -143,12 +143,20 @@ struct GmresDev {
     int *status;               // [L] 0 ok, 2 breakdown (non-finite)
     double *resid;             // [L] |g_k| / ||b||
     int *done;                 // [1] 1 when no lane is active
+    int *jcur;                 // [1] the current Arnoldi column j (device-side, so a graph can loop)
     double tol;
     int part_blocks;           // blocks per lane in the reductions
 };
+// Start: v_0 = b / ||b|| per lane, lanes with b = 0 inactive, j = 0, done = (no lane active).
 cudaError_t gmres_init(GmresDev &gd, const double *b, cudaStream_t st);
-// Orthogonalise w = A v_j against v_0..v_j (CGS2), append v_{j+1}, Givens-update every active lane.
-cudaError_t gmres_arnoldi(GmresDev &gd, double *w, int j, cudaStream_t st);
+// Orthogonalise w = A v_j against v_0..v_j (CGS2), append v_{j+1}, Givens-update every active lane;
+// j is read from gd.jcur.
+cudaError_t gmres_arnoldi(GmresDev &gd, double *w, cudaStream_t st);
+// vin = v_j (j from gd.jcur): the input of the next matvec at a fixed address.
+cudaError_t gmres_load_vj(GmresDev &gd, double *vin, cudaStream_t st);
+// j += 1 unless done or the basis is full; with a graph conditional handle (cond_valid), sets it to
+// whether another iteration follows.
+cudaError_t gmres_advance(GmresDev &gd, cudaGraphConditionalHandle cond, int cond_valid, cudaStream_t st);
 // x = V y with H y = g per lane (y_small: [L][m+1] scratch).
 cudaError_t gmres_solution(GmresDev &gd, double *x, double *y_small, cudaStream_t st);
 

@@ -78,6 +78,21 @@ struct ShapeHost {
 struct mfs_ctx {
     int kind = 0, D = 1;
     int fset = 0;  // factor set of the one-body apply: 0 recompleted (Sec. 3.3), 1 bare self block (Sec. 2.3)
+    // GMRES iteration loops captured as CUDA graphs, by nrhs * 4 + fset * 2 + transposed
+    struct SolveGraph {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        int launches = 0, pair_launches = 0;  // per iteration
+    };
+    std::map<int, SolveGraph> graphs;
+    double *vin_d = nullptr;  // matvec input of a graph iteration (v_j copied to a fixed address)
+    void drop_graphs() {
+        for (auto &kv : graphs) {
+            if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+            if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+        }
+        graphs.clear();
+    }
     mfs_options opt{};
     int P = 0, S = 0, nshapes = 0;
     std::vector<double> centres, quats;
@@ -164,6 +179,7 @@ struct mfs_ctx {
         cudaFree(p);
     }
     ~mfs_ctx() {
+        drop_graphs();
         for (void *p : allocs) cudaFree(p);
         if (done_h) cudaFreeHost(done_h);
         if (ev0) cudaEventDestroy(ev0);
@@ -604,8 +620,11 @@ mfs_status ensure_gmres(mfs_ctx *ctx, int nrhs) {
     // free old
     void *olds[] = {ctx->gd.V, ctx->gd.H, ctx->gd.cs, ctx->gd.sn, ctx->gd.g, ctx->gd.beta, ctx->gd.hbuf,
                     ctx->gd.htmp, ctx->gd.hn, ctx->gd.part, ctx->gd.active, ctx->gd.iters, ctx->gd.status,
-                    ctx->gd.resid, ctx->gd.done, ctx->seg_off_d, ctx->w_d, ctx->b_d, ctx->x_d, ctx->ysmall_d};
+                    ctx->gd.resid, ctx->gd.done, ctx->gd.jcur, ctx->seg_off_d, ctx->w_d, ctx->b_d, ctx->x_d,
+                    ctx->ysmall_d, ctx->vin_d};
+    ctx->drop_graphs();  // they hold the old buffers' addresses
     for (void *p : olds) ctx->release(p);
+    ctx->vin_d = nullptr;
     GmresDev &gd = ctx->gd;
     gd = GmresDev{};
     gd.L = L;
@@ -643,6 +662,8 @@ mfs_status ensure_gmres(mfs_ctx *ctx, int nrhs) {
     CK(ctx->alloc(&gd.status, L));
     CK(ctx->alloc(&gd.resid, L));
     CK(ctx->alloc(&gd.done, 1));
+    CK(ctx->alloc(&gd.jcur, 1));
+    CK(ctx->alloc(&ctx->vin_d, n));
     CK(ctx->alloc(&ctx->w_d, n));
     CK(ctx->alloc(&ctx->b_d, n));
     CK(ctx->alloc(&ctx->x_d, n));
@@ -787,23 +808,102 @@ struct SolveStats {
     double resid = 0.0;
 };
 
+// One GMRES iteration's matvec: w = A vin (or A^T vin).
+mfs_status iteration_matvec(mfs_ctx *ctx, const double *vin, int nrhs, bool transposed, cudaStream_t st) {
+    if (transposed) return matvec_T_dev(ctx, vin, ctx->w_d, nrhs, st);
+    return matvec_dev(ctx, vin, ctx->w_d, nrhs, st);
+}
+
+// The loop of iterations j >= 1 as a CUDA graph: a while node whose body loads v_j, applies the
+// matvec, orthogonalises (Arnoldi, Givens) and advances j, clearing the node's condition when every
+// lane stopped or the basis is full (at most m - 1 passes).  Built on first use (the first iteration
+// ran on the host loop, so every plan and tensor map the body needs exists) and kept per key.
+mfs_status solve_graph(mfs_ctx *ctx, int nrhs, bool transposed, cudaStream_t st, mfs_ctx::SolveGraph **out) {
+    const int key = nrhs * 4 + ctx->fset * 2 + (transposed ? 1 : 0);
+    auto it = ctx->graphs.find(key);
+    if (it != ctx->graphs.end()) {
+        *out = &it->second;
+        return MFS_OK;
+    }
+    mfs_ctx::SolveGraph g;
+    GmresDev &gd = ctx->gd;
+    CK(cudaGraphCreate(&g.graph, 0));
+    auto fail = [&](cudaError_t e) {
+        cudaGetLastError();
+        if (g.graph) cudaGraphDestroy(g.graph);
+        ctx->last_error = std::string("CUDA graph of the GMRES loop: ") + cudaGetErrorString(e);
+        return MFS_ERR_CUDA;
+    };
+    cudaGraphConditionalHandle cond;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, g.graph, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return fail(e);
+    // the parameter union has no default constructor: zeroed storage, then the conditional member
+    alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+    std::memset(cp_raw, 0, sizeof(cp_raw));
+    cudaGraphNodeParams &cp = *reinterpret_cast<cudaGraphNodeParams *>(cp_raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, g.graph, nullptr, nullptr, 0, &cp);
+    if (e != cudaSuccess) return fail(e);
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    const int l0 = ctx->launches, p0 = ctx->pair_launches;
+    e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return fail(e);
+    mfs_status ms = MFS_OK;
+    cudaError_t ce = gmres_load_vj(gd, ctx->vin_d, st);
+    if (ce == cudaSuccess) ms = iteration_matvec(ctx, ctx->vin_d, nrhs, transposed, st);
+    if (ce == cudaSuccess && ms == MFS_OK) ce = gmres_arnoldi(gd, ctx->w_d, st);
+    if (ce == cudaSuccess && ms == MFS_OK) ce = gmres_advance(gd, cond, 1, st);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(st, &captured);
+    g.launches = ctx->launches - l0 + 11;
+    g.pair_launches = ctx->pair_launches - p0;
+    ctx->launches = l0;
+    ctx->pair_launches = p0;
+    if (ms != MFS_OK) {
+        cudaGraphDestroy(g.graph);
+        return ms;
+    }
+    if (ce != cudaSuccess) return fail(ce);
+    if (e != cudaSuccess) return fail(e);
+    e = cudaGraphInstantiate(&g.exec, g.graph, 0);
+    if (e != cudaSuccess) return fail(e);
+    it = ctx->graphs.emplace(key, g).first;
+    *out = &it->second;
+    return MFS_OK;
+}
+
 // Solve A x = b (or A^T x = b) with b = ctx->b_d for all lanes; x in ctx->x_d.
 mfs_status gmres_solve(mfs_ctx *ctx, int nrhs, cudaStream_t st, SolveStats &stats, bool transposed = false) {
     GmresDev &gd = ctx->gd;
     CK(gmres_init(gd, ctx->b_d, st));
-    ctx->launches += 5;
-    int j = 0;
-    for (; j < gd.m; ++j) {
-        if (transposed)
-            CKS(matvec_T_dev(ctx, gd.V + (size_t)j * gd.n, ctx->w_d, nrhs, st));
-        else
-            CKS(matvec_dev(ctx, gd.V + (size_t)j * gd.n, ctx->w_d, nrhs, st));
-        stats.matvecs++;
-        CK(gmres_arnoldi(gd, ctx->w_d, j, st));
-        ctx->launches += 9;
+    ctx->launches += 6;
+    const bool use_graph = ctx->opt.graphs && !ctx->opt.profile;
+    for (int j = 0; j < gd.m; ++j) {
+        CKS(iteration_matvec(ctx, gd.V + (size_t)j * gd.n, nrhs, transposed, st));
+        CK(gmres_arnoldi(gd, ctx->w_d, st));
+        CK(gmres_advance(gd, cudaGraphConditionalHandle(), 0, st));
+        ctx->launches += 10;
         CK(cudaMemcpyAsync(ctx->done_h, gd.done, sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        if (*ctx->done_h) break;
+        stats.matvecs = j + 1;
+        if (*ctx->done_h || j + 1 >= gd.m) break;
+        if (use_graph) {  // the remaining iterations as one graph launch
+            mfs_ctx::SolveGraph *g = nullptr;
+            CKS(solve_graph(ctx, nrhs, transposed, st, &g));
+            CK(cudaGraphLaunch(g->exec, st));
+            int jend = 0;
+            CK(cudaMemcpyAsync(&jend, gd.jcur, sizeof(int), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            const int extra = jend - j;  // iterations the graph ran (j advanced from j + 1 to jend)
+            ctx->launches += extra * g->launches;
+            ctx->pair_launches += extra * g->pair_launches;
+            stats.matvecs = jend + 1;
+            break;
+        }
     }
     CK(gmres_solution(gd, ctx->x_d, ctx->ysmall_d, st));
     ctx->launches += 2;
@@ -843,6 +943,7 @@ void mfs_default_options(mfs_options *opt) {
     opt->profile = 0;
     opt->tensor_cores = 1;
     opt->pair_variant = -1;
+    opt->graphs = 1;
 }
 
 int32_t mfs_abi_version(void) { return MFS_ABI_VERSION; }
