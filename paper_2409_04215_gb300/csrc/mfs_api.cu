@@ -86,6 +86,7 @@ struct mfs_ctx {
     };
     std::map<int, SolveGraph> graphs;
     double *vin_d = nullptr;  // matvec input of a graph iteration (v_j copied to a fixed address)
+    cudaStream_t cap_stream = nullptr;  // capture only (the legacy stream cannot capture); launches use the caller's
     void drop_graphs() {
         for (auto &kv : graphs) {
             if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
@@ -180,6 +181,7 @@ struct mfs_ctx {
     }
     ~mfs_ctx() {
         drop_graphs();
+        if (cap_stream) cudaStreamDestroy(cap_stream);
         for (void *p : allocs) cudaFree(p);
         if (done_h) cudaFreeHost(done_h);
         if (ev0) cudaEventDestroy(ev0);
@@ -818,13 +820,15 @@ mfs_status iteration_matvec(mfs_ctx *ctx, const double *vin, int nrhs, bool tran
 // matvec, orthogonalises (Arnoldi, Givens) and advances j, clearing the node's condition when every
 // lane stopped or the basis is full (at most m - 1 passes).  Built on first use (the first iteration
 // ran on the host loop, so every plan and tensor map the body needs exists) and kept per key.
-mfs_status solve_graph(mfs_ctx *ctx, int nrhs, bool transposed, cudaStream_t st, mfs_ctx::SolveGraph **out) {
+mfs_status solve_graph(mfs_ctx *ctx, int nrhs, bool transposed, mfs_ctx::SolveGraph **out) {
     const int key = nrhs * 4 + ctx->fset * 2 + (transposed ? 1 : 0);
     auto it = ctx->graphs.find(key);
     if (it != ctx->graphs.end()) {
         *out = &it->second;
         return MFS_OK;
     }
+    if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t st = ctx->cap_stream;  // records the body; nothing executes on it
     mfs_ctx::SolveGraph g;
     GmresDev &gd = ctx->gd;
     CK(cudaGraphCreate(&g.graph, 0));
@@ -893,7 +897,7 @@ mfs_status gmres_solve(mfs_ctx *ctx, int nrhs, cudaStream_t st, SolveStats &stat
         if (*ctx->done_h || j + 1 >= gd.m) break;
         if (use_graph) {  // the remaining iterations as one graph launch
             mfs_ctx::SolveGraph *g = nullptr;
-            CKS(solve_graph(ctx, nrhs, transposed, st, &g));
+            CKS(solve_graph(ctx, nrhs, transposed, &g));
             CK(cudaGraphLaunch(g->exec, st));
             int jend = 0;
             CK(cudaMemcpyAsync(&jend, gd.jcur, sizeof(int), cudaMemcpyDeviceToHost, st));
