@@ -445,18 +445,24 @@ int tc_gemm_bn(int m, int pieces) {  // MMA N: columns per CTA, a multiple of 16
     return b > cap ? cap : (b < 16 ? 16 : b);
 }
 
+size_t tc_gemm_smem(int BN, int pieces) {
+    return (size_t)tc::STAGES * pieces * (tc::B_TILE + (size_t)BN * tc::BK * 4) + 1024;
+}
+
 int tc_gemm_chunks(int m, int n, int k, int sm_count, int pieces) {
     const int bn = tc_gemm_bn(m, pieces);
     const int tiles = ((n + tc::BM - 1) / tc::BM) * ((m + bn - 1) / bn);
-    int s = (2 * sm_count + tiles - 1) / tiles;  // about two CTAs per SM in total
-    const int smax = (k + 255) / 256;            // chunks of at least 256 K
+    // whole waves: as many K chunks as fill the SMs once at the shared-memory occupancy (228 KB per
+    // SM, 1 KB reserved per CTA), so no second, partly empty wave trails the first
+    const size_t per_cta = tc_gemm_smem(bn, pieces) + 1024;
+    int resident = (int)(233472 / per_cta);
+    if (resident < 1) resident = 1;
+    int s = (resident * sm_count) / tiles;
+    const int smax = (k + 255) / 256;  // chunks of at least 256 K
     if (s > smax) s = smax;
     return s < 1 ? 1 : s;
 }
 
-size_t tc_gemm_smem(int BN, int pieces) {
-    return (size_t)tc::STAGES * pieces * (tc::B_TILE + (size_t)BN * tc::BK * 4) + 1024;
-}
 
 int tc_gemm_sz(int k, int S) {
     const int kchunk = ((k + S - 1) / S + tc::BK - 1) / tc::BK * tc::BK;
