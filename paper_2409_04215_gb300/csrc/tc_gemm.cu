@@ -458,7 +458,7 @@ int tc_gemm_chunks(int m, int n, int k, int sm_count, int pieces) {
     int resident = (int)(233472 / per_cta);
     if (resident < 1) resident = 1;
     int s = (resident * sm_count) / tiles;
-    const int smax = (k + 255) / 256;  // chunks of at least 256 K
+    const int smax = (k + 127) / 128;  // chunks of at least 128 K
     if (s > smax) s = smax;
     return s < 1 ? 1 : s;
 }
