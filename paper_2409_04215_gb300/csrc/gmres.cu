@@ -31,21 +31,42 @@ __device__ __forceinline__ void lane_chunk(const GmresDev &gd, int l, int b, lon
     e1 = s0 + len * (b + 1) / gd.part_blocks;
 }
 
-// part[l][b][i] = sum over chunk b of lane l of V[i][e] * w[e], i = 0..j  (grid: PB x L; the chunk of w
-// stays in L1 across i)
+// part[l][b][i] = sum over chunk b of lane l of V[i][e] * w[e], i = 0..j  (grid: PB x L).  Eight
+// columns at a time: w[e] is read once per group, eight accumulators per thread, one grouped block
+// reduction (warp shuffles, then the warps' sums added in a fixed order) per group.
 __global__ void mdot_kernel(GmresDev gd, const double *w) {
+    constexpr int G = 8;
     const int b = blockIdx.x, l = blockIdx.y;
     if (!gd.active[l]) return;
     const int j = *gd.jcur;
-    __shared__ double sh[32];
+    __shared__ double sh[GM_THREADS / 32][G];
     long long e0, e1;
     lane_chunk(gd, l, b, e0, e1);
-    for (int i = 0; i <= j; ++i) {
-        const double *v = gd.V + (size_t)i * gd.n;
-        double acc = 0.0;
-        for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) acc += v[e] * w[e];
-        acc = block_sum(acc, sh);
-        if (threadIdx.x == 0) gd.part[((size_t)l * gd.part_blocks + b) * (gd.m + 1) + i] = acc;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i0 = 0; i0 <= j; i0 += G) {
+        const int ng = min(G, j + 1 - i0);
+        double acc[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) acc[g] = 0.0;
+        for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+            const double we = w[e];
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+                if (g < ng) acc[g] += gd.V[(size_t)(i0 + g) * gd.n + e] * we;
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            double v = acc[g];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) sh[wid][g] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < ng) {
+            double s = 0.0;
+            for (int q = 0; q < nw; ++q) s += sh[q][threadIdx.x];
+            gd.part[((size_t)l * gd.part_blocks + b) * (gd.m + 1) + i0 + threadIdx.x] = s;
+        }
+        __syncthreads();
     }
 }
 

@@ -994,6 +994,7 @@ static int occupancy_variant() {
     P(PackedStokes, 1, 3, 64)     \
     P(PackedStokes, 1, 3, 256)    \
     P(PackedStokes, 1, 4, 128)    \
+    P(PackedStokes, 1, 4, 64)     \
     P(PackedStokes, 2, 1, 128)    \
     P(PackedStokes, 4, 1, 128)    \
     P(PackedLaplaceReg, 1, 2, 128) \
