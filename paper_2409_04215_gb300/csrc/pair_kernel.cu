@@ -997,6 +997,9 @@ static int occupancy_variant() {
     P(PackedStokes, 1, 4, 64)     \
     P(PackedStokes, 2, 1, 128)    \
     P(PackedStokes, 4, 1, 128)    \
+    P(PackedStokes, 4, 2, 64)     \
+    P(PackedStokes, 4, 1, 64)     \
+    P(PackedStokes, 2, 2, 64)     \
     P(PackedLaplaceReg, 1, 2, 128) \
     P(PackedLaplaceReg, 1, 4, 128) \
     P(PackedLaplaceReg, 1, 2, 256) \
