@@ -506,6 +506,15 @@ def main():
            "h2d_bytes_per_step": int(Fh.numel() * 8 + Th.numel() * 8),
            "d2h_bytes_per_step": int(2 * Fh.numel() * 8), "ms_per_step": 1e3 * e2e_sec}
 
+    # the FP32 peak checked on this GPU now: f32x2 and scalar FMA on independent chains (outside the
+    # timed region; about 30 ms of device time)
+    from paper_2409_04215_gb300.api import fp32_fma_rate
+
+    probe = {"ffma2_tflops": fp32_fma_rate(True), "ffma_tflops": fp32_fma_rate(False),
+             "how": "mfs_fp32_fma_rate: 8 independent fma chains per thread, 32 warps per SM, one ~15 ms launch"}
+    roofline["peak_probe"] = probe
+    roofline["frac_of_probe"] = achieved / probe["ffma2_tflops"]
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()

@@ -288,6 +288,17 @@ const char *mfs_pair_variant(const mfs_ctx *ctx, int32_t nrhs);
  * sum).  NULL past the end of the table; the out-pointers may be NULL.  Static storage. */
 const char *mfs_pair_variant_info(int32_t index, int32_t *d, int32_t *nrhs, int32_t *grad);
 
+/*
+ * mfs_fp32_fma_rate -- measured FP32 FMA throughput of the current device (TFLOP/s, an FMA counted as
+ * two flops), the denominator check for the pair kernel's share of peak.  The paper has no
+ * counterpart.  packed = 0 times scalar fma.rn.f32, packed = 1 the f32x2 form the Stokeslet kernel
+ * issues; each on 8 independent chains per thread, 32 resident warps per SM, one launch of about
+ * 10-20 ms after a short warm-up launch, timed with CUDA events on `stream` (the call synchronises
+ * that stream).  Allocates and frees a few KB (stream-ordered).  *tflops is set to 0 on failure;
+ * packed outside {0, 1} or a NULL tflops returns MFS_ERR_INVALID_ARG.
+ */
+mfs_status mfs_fp32_fma_rate(int32_t packed, double *tflops, void *stream);
+
 /* Text of the last error on this context (never NULL; "" when none).  Valid until the next call. */
 const char *mfs_last_error(const mfs_ctx *ctx);
 

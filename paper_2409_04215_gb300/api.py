@@ -45,6 +45,7 @@ EXPORTED = [
     "mfs_stokeslet_sum_noalloc",
     "mfs_pair_variant",
     "mfs_pair_variant_info",
+    "mfs_fp32_fma_rate",
     "mfs_dirichlet_apply",
     "mfs_dirichlet_matvec",
     "mfs_solve_capacitance",
@@ -163,6 +164,7 @@ def load_library(path: Optional[str] = None):
     lib.mfs_pair_variant_info.argtypes = [i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.mfs_pair_variant_info.restype = ctypes.c_char_p
     lib.mfs_pair_variant.argtypes = [vp, i32]
+    lib.mfs_fp32_fma_rate.argtypes = [i32, ctypes.POINTER(ctypes.c_double), vp]
     lib.mfs_pair_variant.restype = ctypes.c_char_p
     lib.mfs_last_error.argtypes = [vp]
     lib.mfs_last_error.restype = ctypes.c_char_p
@@ -189,6 +191,19 @@ def pair_variants():
             return out
         out.append((i, name.decode(), d.value, r.value, g.value))
         i += 1
+
+
+def fp32_fma_rate(packed: bool = True, stream=None) -> float:
+    """Measured FP32 FMA throughput of the current CUDA device in TFLOP/s (mfs_fp32_fma_rate):
+    f32x2 fma when packed, else scalar fma.  Synchronises the stream."""
+    lib = load_library()
+    out = ctypes.c_double()
+    torch = _torch()
+    st = _stream_ptr(stream, torch.device("cuda", torch.cuda.current_device()))
+    rc = lib.mfs_fp32_fma_rate(1 if packed else 0, ctypes.byref(out), st)
+    if rc != MFS_OK:
+        raise MFSError(rc, "mfs_fp32_fma_rate failed")
+    return out.value
 
 
 def default_options(**kw) -> Options:

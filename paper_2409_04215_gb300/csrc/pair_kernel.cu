@@ -69,6 +69,12 @@ __device__ __forceinline__ float rsqrt_ftz(float x) {
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+// 1/x by the hardware approximation (same flush argument): moves 1/r^2 from the FMA pipe to MUFU.
+__device__ __forceinline__ float rcp_ftz(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 // ---------------------------------------------------------------------------
 // Record layouts
@@ -137,7 +143,8 @@ __device__ __forceinline__ Stage make_stage(const PairTile *tiles, int ntiles, c
 // ---------------------------------------------------------------------------
 // Hooks every policy has; the gradient policy overrides them (target strengths, source-side sums).
 struct PolicyBase {
-    static constexpr int MINB = 1;  // minimum resident CTAs per SM requested from the compiler
+    static constexpr int MINB = 1;         // minimum resident CTAs per SM requested from the compiler
+    static constexpr int STAGE_BYTES = 0;  // bytes of one source stage; 0: the staging loop's default
     __device__ __forceinline__ void load_extra(int, int, const PairGeom &) {}
     __device__ __forceinline__ void source_side(int, bool, double *) {}
 };
@@ -240,8 +247,15 @@ struct Scalar : PolicyBase {
     }
 };
 
-template <int NRHS, int TP, int NT>
+// QU sources are unrolled per step of the inner loop (bodies hold a multiple of 4 records);
+// RCP takes 1/r^2 from MUFU (rcp) instead of ri * ri on the FMA pipe (16 instead of 17 packed
+// FMA-pipe instructions per two pairs); SB overrides the stage size and MB asks the compiler for
+// MB resident CTAs per SM (smaller stages and fewer registers: more warps to hide latency).
+template <int NRHS, int TP, int NT, int QU = 4, bool RCP = false, int SB = 0, int MB = 1>
 struct PackedStokes : PolicyBase {
+    static_assert(QU == 1 || QU == 2 || QU == 4, "bodies are padded to multiples of 4 records");
+    static constexpr int STAGE_BYTES = SB;
+    static constexpr int MINB = MB;
     static constexpr int D = 3;
     static constexpr int C = 3 * NRHS;
     static constexpr int REC = rec_floats(3, NRHS, true);
@@ -295,9 +309,9 @@ struct PackedStokes : PolicyBase {
             for (int p = 0; p < TP; ++p)
 #pragma unroll
                 for (int c = 0; c < C; ++c) blk[p][c] = 0ull;
-            for (int s = s0; s < s1; s += 4) {
+            for (int s = s0; s < s1; s += QU) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
+                for (int q = 0; q < QU; ++q) {
                     u64 rec[REC / 2];
 #pragma unroll
                     for (int v = 0; v < REC / 4; ++v) {
@@ -314,7 +328,7 @@ struct PackedStokes : PolicyBase {
                         float a, b;
                         f2_unpack(r2, a, b);
                         const u64 ri = f2_pack(rsqrt_ftz(a), rsqrt_ftz(b));
-                        const u64 ri2 = f2_mul(ri, ri);
+                        const u64 ri2 = RCP ? f2_pack(rcp_ftz(a), rcp_ftz(b)) : f2_mul(ri, ri);
 #pragma unroll
                         for (int h = 0; h < NRHS; ++h) {
                             const u64 lx = rec[3 + 3 * h], ly = rec[4 + 3 * h], lz = rec[5 + 3 * h];
@@ -705,7 +719,7 @@ template <class Pol, int NT>
 struct StageCfg {
     static constexpr int REC = Pol::REC;
     // 16 KB stages; 12 KB when the policy keeps per-target state in shared memory (occupancy)
-    static constexpr int STAGE_BYTES = Pol::PSM ? 12288 : 16384;
+    static constexpr int STAGE_BYTES = Pol::STAGE_BYTES ? Pol::STAGE_BYTES : (Pol::PSM ? 12288 : 16384);
     static constexpr int STAGE_REC = (STAGE_BYTES / (REC * 4)) / MFS_BS * MFS_BS;
     static constexpr int STAGE_BLOCKS = STAGE_REC / MFS_BS;
     static constexpr int SMEM = 2 * STAGE_REC * REC * 4 + Pol::PSM * NT * 4;
@@ -730,6 +744,15 @@ template <int NRHS, int TP, int NT>
 struct PackedStokesB5 : PackedStokes<NRHS, TP, NT> {
     static constexpr int MINB = 5;
 };
+// S6B6: 6 KB stages (128 records) and at least 6 resident CTAs per SM (12 warps of 64-thread CTAs
+// instead of 10); Rcp: 1/r^2 from MUFU.  On 100 spheres (M = 1200, N = 600) both measured a little
+// slower than PackedStokes<1,4,64> (58.8 % and 60.8 % of FP32 peak against 62.6 %), as did 7 and
+// 8 CTAs per SM with 3 and 2 target pairs per thread (51 %, 58 %): more warps do not close the
+// gap to the FMA pipe's peak here.  They stay in the table for the autotuner's other geometries.
+template <int NRHS, int TP, int NT>
+struct PackedStokesS6B6 : PackedStokes<NRHS, TP, NT, 4, false, 6144, 6> {};
+template <int NRHS, int TP, int NT>
+struct PackedStokesRcp : PackedStokes<NRHS, TP, NT, 4, true> {};
 
 template <class Pol, int NT, int MINB = Pol::MINB>
 __global__ void __launch_bounds__(NT, MINB) pair_sum_kernel(PairGeom geo, PairWork work, int *err) {
@@ -1000,6 +1023,8 @@ static int occupancy_variant() {
     P(PackedStokes, 4, 2, 64)     \
     P(PackedStokes, 4, 1, 64)     \
     P(PackedStokes, 2, 2, 64)     \
+    P(PackedStokesS6B6, 1, 4, 64) \
+    P(PackedStokesRcp, 1, 4, 64)  \
     P(PackedLaplaceReg, 1, 2, 128) \
     P(PackedLaplaceReg, 1, 4, 128) \
     P(PackedLaplaceReg, 1, 2, 256) \
@@ -1258,4 +1283,95 @@ extern "C" mfs_status mfs_stokeslet_sum_noalloc(const double *targets, int32_t n
     pair_epilogue_kernel<3, 1><<<ntiles, 256, 0, st>>>(work, nullptr, 0.0, 1.0 / (8.0 * MFS_PI * mu), u,
                                                        num_targets);
     return cudaGetLastError() == cudaSuccess ? MFS_OK : MFS_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 FMA-rate probe: the throughput the pair kernel's roofline divides by
+// ---------------------------------------------------------------------------
+namespace mfs {
+namespace fmaprobe {
+
+constexpr int kChains = 8;     // independent dependency chains per thread
+constexpr int kThreads = 256;  // threads per CTA
+constexpr int kCtasPerSm = 4;  // 32 resident warps per SM
+constexpr int kIters = 1 << 18;
+
+// a <- a * b + c on kChains independent chains; b < 1 and c > 0 keep every value near c / (1 - b)
+// (normal FP32 numbers), and the final test against a value the chains never reach keeps the
+// compiler from removing them.
+template <bool PACKED>
+__global__ void __launch_bounds__(kThreads) fma_rate_kernel(float b, float c, int iters, float *sink) {
+    const float seed = 0.5f + 1e-3f * (float)(threadIdx.x & 31);
+    if (PACKED) {
+        u64 a[kChains];
+        const u64 bb = f2_pack(b, b), cc = f2_pack(c, c);
+#pragma unroll
+        for (int i = 0; i < kChains; ++i) a[i] = f2_pack(seed + (float)i, seed - (float)i);
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int i = 0; i < kChains; ++i) a[i] = f2_fma(a[i], bb, cc);
+        }
+        float s = 0.f;
+#pragma unroll
+        for (int i = 0; i < kChains; ++i) {
+            float lo, hi;
+            f2_unpack(a[i], lo, hi);
+            s += lo + hi;
+        }
+        if (s == -1.0f) sink[blockIdx.x] = s;
+    } else {
+        float a[kChains];
+#pragma unroll
+        for (int i = 0; i < kChains; ++i) a[i] = seed + (float)i;
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int i = 0; i < kChains; ++i) a[i] = fmaf(a[i], b, c);
+        }
+        float s = 0.f;
+#pragma unroll
+        for (int i = 0; i < kChains; ++i) s += a[i];
+        if (s == -1.0f) sink[blockIdx.x] = s;
+    }
+}
+
+}  // namespace fmaprobe
+}  // namespace mfs
+
+extern "C" mfs_status mfs_fp32_fma_rate(int32_t packed, double *tflops, void *stream) {
+    using namespace mfs::fmaprobe;
+    if (!tflops || (packed != 0 && packed != 1)) return MFS_ERR_INVALID_ARG;
+    *tflops = 0.0;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+        return MFS_ERR_CUDA;
+    const int grid = sms * kCtasPerSm;
+    float *sink = nullptr;
+    if (cudaMallocAsync(&sink, sizeof(float) * grid, st) != cudaSuccess) return MFS_ERR_OOM;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    mfs_status rc = MFS_ERR_CUDA;
+    if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+        auto launch = [&](int iters) {
+            if (packed)
+                fma_rate_kernel<true><<<grid, kThreads, 0, st>>>(0.9999999f, 1e-7f, iters, sink);
+            else
+                fma_rate_kernel<false><<<grid, kThreads, 0, st>>>(0.9999999f, 1e-7f, iters, sink);
+        };
+        launch(kIters / 16);  // warm-up (clocks up, code loaded)
+        cudaEventRecord(e0, st);
+        launch(kIters);
+        cudaEventRecord(e1, st);
+        float ms = 0.f;
+        if (cudaGetLastError() == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms > 0.f) {
+            const double fmas = (double)grid * kThreads * kChains * (packed ? 2.0 : 1.0) * kIters;
+            *tflops = 2.0 * fmas / (ms * 1e-3) / 1e12;
+            rc = MFS_OK;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFreeAsync(sink, st);
+    return rc;
 }

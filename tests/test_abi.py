@@ -62,6 +62,9 @@ def test_setup_rejects_bad_input_without_gpu(lib_path):
     rc = lib.mfs_setup(ctypes.byref(out), 1, None, 1, None, None, None, None)
     assert rc == 1  # MFS_ERR_INVALID_ARG
     assert b"invalid" in lib.mfs_setup_error()
+    val = ctypes.c_double(-1.0)
+    assert lib.mfs_fp32_fma_rate(2, ctypes.byref(val), None) == 1  # packed must be 0 or 1
+    assert lib.mfs_fp32_fma_rate(1, None, None) == 1
 
 
 def test_struct_layouts_match_the_header(tmp_path):
