@@ -753,6 +753,9 @@ template <int NRHS, int TP, int NT>
 struct PackedStokesS6B6 : PackedStokes<NRHS, TP, NT, 4, false, 6144, 6> {};
 template <int NRHS, int TP, int NT>
 struct PackedStokesRcp : PackedStokes<NRHS, TP, NT, 4, true> {};
+// 6 KB stages only: 7 target pairs per thread keep 4 CTAs (8 warps) per SM within shared memory.
+template <int NRHS, int TP, int NT>
+struct PackedStokesS6 : PackedStokes<NRHS, TP, NT, 4, false, 6144> {};
 
 template <class Pol, int NT, int MINB = Pol::MINB>
 __global__ void __launch_bounds__(NT, MINB) pair_sum_kernel(PairGeom geo, PairWork work, int *err) {
@@ -823,9 +826,9 @@ __global__ void __launch_bounds__(NT, MINB) pair_sum_kernel(PairGeom geo, PairWo
             }
         }
         // centre offsets of the tile's target bodies relative to this stage's source body
-        if (tid < tl.nb * 3) {
-            const int kb = tl.kb0 + tid / 3, c = tid % 3;
-            dcs[buf][tid / 3][c] = (float)(geo.centres[kb * 3 + c] - geo.centres[cur.body * 3 + c]);
+        for (int q = tid; q < tl.nb * 3; q += NT) {  // up to MFS_MAX_TILE_BODIES * 3 entries, NT may be fewer
+            const int kb = tl.kb0 + q / 3, c = q % 3;
+            dcs[buf][q / 3][c] = (float)(geo.centres[kb * 3 + c] - geo.centres[cur.body * 3 + c]);
         }
         const bool ok = mbar_wait_bounded(&bars[buf], (uint32_t)((si >> 1) & 1), err, wait_limit);
         if (__syncthreads_or(!ok)) {
@@ -1025,6 +1028,11 @@ static int occupancy_variant() {
     P(PackedStokes, 2, 2, 64)     \
     P(PackedStokesS6B6, 1, 4, 64) \
     P(PackedStokesRcp, 1, 4, 64)  \
+    P(PackedStokes, 1, 5, 64)     \
+    P(PackedStokes, 1, 5, 128)    \
+    P(PackedStokes, 1, 6, 64)     \
+    P(PackedStokesS6, 1, 7, 64)   \
+    P(PackedStokes, 1, 6, 128)    \
     P(PackedLaplaceReg, 1, 2, 128) \
     P(PackedLaplaceReg, 1, 4, 128) \
     P(PackedLaplaceReg, 1, 2, 256) \

@@ -52,3 +52,24 @@ def test_every_variant_matches_oracle(include_self):
             ref = _oracle_pair(pr, wl, s[h].reshape(-1), include_self)
             assert _rel(u[h].reshape(-1), ref) < 1e-6, (name, h)
         ctx.close()
+
+
+def test_every_variant_tiny_bodies():
+    """Bodies of 12 collocation and 6 proxy points: every target tile spans the maximum of 32 bodies,
+    so the per-tile table of centre offsets (96 entries) is larger than a 64-thread CTA."""
+    table = _table()
+    assert table
+    problems = {}
+    for kind in ("stokes", "laplace"):
+        wl = _mixed(kind, P=80, m=12, n=6, nsusp=2, seed=52)
+        problems[kind] = (wl, Problem(wl))
+    for idx, name, d, nrhs, _ in table:
+        kind = "stokes" if d == 3 else "laplace"
+        wl, pr = problems[kind]
+        ctx = _ctx(wl, pair_variant=idx)
+        s = np.random.default_rng(idx + 100).standard_normal((nrhs, ctx.sum_N, d))
+        u = ctx.pair_sum(torch.tensor(s, device="cuda"), include_self=False).cpu().numpy()
+        for h in range(nrhs):
+            ref = _oracle_pair(pr, wl, s[h].reshape(-1), False)
+            assert _rel(u[h].reshape(-1), ref) < 1e-6, (name, h)
+        ctx.close()
