@@ -69,12 +69,6 @@ __device__ __forceinline__ float rsqrt_ftz(float x) {
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-// 1/x by the hardware approximation (same flush argument): moves 1/r^2 from the FMA pipe to MUFU.
-__device__ __forceinline__ float rcp_ftz(float x) {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
 
 // ---------------------------------------------------------------------------
 // Record layouts
@@ -143,8 +137,7 @@ __device__ __forceinline__ Stage make_stage(const PairTile *tiles, int ntiles, c
 // ---------------------------------------------------------------------------
 // Hooks every policy has; the gradient policy overrides them (target strengths, source-side sums).
 struct PolicyBase {
-    static constexpr int MINB = 1;         // minimum resident CTAs per SM requested from the compiler
-    static constexpr int STAGE_BYTES = 0;  // bytes of one source stage; 0: the staging loop's default
+    static constexpr int MINB = 1;  // minimum resident CTAs per SM requested from the compiler
     __device__ __forceinline__ void load_extra(int, int, const PairGeom &) {}
     __device__ __forceinline__ void source_side(int, bool, double *) {}
 };
@@ -247,15 +240,8 @@ struct Scalar : PolicyBase {
     }
 };
 
-// QU sources are unrolled per step of the inner loop (bodies hold a multiple of 4 records);
-// RCP takes 1/r^2 from MUFU (rcp) instead of ri * ri on the FMA pipe (16 instead of 17 packed
-// FMA-pipe instructions per two pairs); SB overrides the stage size and MB asks the compiler for
-// MB resident CTAs per SM (smaller stages and fewer registers: more warps to hide latency).
-template <int NRHS, int TP, int NT, int QU = 4, bool RCP = false, int SB = 0, int MB = 1>
+template <int NRHS, int TP, int NT>
 struct PackedStokes : PolicyBase {
-    static_assert(QU == 1 || QU == 2 || QU == 4, "bodies are padded to multiples of 4 records");
-    static constexpr int STAGE_BYTES = SB;
-    static constexpr int MINB = MB;
     static constexpr int D = 3;
     static constexpr int C = 3 * NRHS;
     static constexpr int REC = rec_floats(3, NRHS, true);
@@ -309,9 +295,9 @@ struct PackedStokes : PolicyBase {
             for (int p = 0; p < TP; ++p)
 #pragma unroll
                 for (int c = 0; c < C; ++c) blk[p][c] = 0ull;
-            for (int s = s0; s < s1; s += QU) {
+            for (int s = s0; s < s1; s += 4) {
 #pragma unroll
-                for (int q = 0; q < QU; ++q) {
+                for (int q = 0; q < 4; ++q) {
                     u64 rec[REC / 2];
 #pragma unroll
                     for (int v = 0; v < REC / 4; ++v) {
@@ -328,7 +314,7 @@ struct PackedStokes : PolicyBase {
                         float a, b;
                         f2_unpack(r2, a, b);
                         const u64 ri = f2_pack(rsqrt_ftz(a), rsqrt_ftz(b));
-                        const u64 ri2 = RCP ? f2_pack(rcp_ftz(a), rcp_ftz(b)) : f2_mul(ri, ri);
+                        const u64 ri2 = f2_mul(ri, ri);
 #pragma unroll
                         for (int h = 0; h < NRHS; ++h) {
                             const u64 lx = rec[3 + 3 * h], ly = rec[4 + 3 * h], lz = rec[5 + 3 * h];
@@ -719,7 +705,7 @@ template <class Pol, int NT>
 struct StageCfg {
     static constexpr int REC = Pol::REC;
     // 16 KB stages; 12 KB when the policy keeps per-target state in shared memory (occupancy)
-    static constexpr int STAGE_BYTES = Pol::STAGE_BYTES ? Pol::STAGE_BYTES : (Pol::PSM ? 12288 : 16384);
+    static constexpr int STAGE_BYTES = Pol::PSM ? 12288 : 16384;
     static constexpr int STAGE_REC = (STAGE_BYTES / (REC * 4)) / MFS_BS * MFS_BS;
     static constexpr int STAGE_BLOCKS = STAGE_REC / MFS_BS;
     static constexpr int SMEM = 2 * STAGE_REC * REC * 4 + Pol::PSM * NT * 4;
@@ -744,18 +730,6 @@ template <int NRHS, int TP, int NT>
 struct PackedStokesB5 : PackedStokes<NRHS, TP, NT> {
     static constexpr int MINB = 5;
 };
-// S6B6: 6 KB stages (128 records) and at least 6 resident CTAs per SM (12 warps of 64-thread CTAs
-// instead of 10); Rcp: 1/r^2 from MUFU.  On 100 spheres (M = 1200, N = 600) both measured a little
-// slower than PackedStokes<1,4,64> (58.8 % and 60.8 % of FP32 peak against 62.6 %), as did 7 and
-// 8 CTAs per SM with 3 and 2 target pairs per thread (51 %, 58 %): more warps do not close the
-// gap to the FMA pipe's peak here.  They stay in the table for the autotuner's other geometries.
-template <int NRHS, int TP, int NT>
-struct PackedStokesS6B6 : PackedStokes<NRHS, TP, NT, 4, false, 6144, 6> {};
-template <int NRHS, int TP, int NT>
-struct PackedStokesRcp : PackedStokes<NRHS, TP, NT, 4, true> {};
-// 6 KB stages only: 7 target pairs per thread keep 4 CTAs (8 warps) per SM within shared memory.
-template <int NRHS, int TP, int NT>
-struct PackedStokesS6 : PackedStokes<NRHS, TP, NT, 4, false, 6144> {};
 
 template <class Pol, int NT, int MINB = Pol::MINB>
 __global__ void __launch_bounds__(NT, MINB) pair_sum_kernel(PairGeom geo, PairWork work, int *err) {
@@ -1026,13 +1000,9 @@ static int occupancy_variant() {
     P(PackedStokes, 4, 2, 64)     \
     P(PackedStokes, 4, 1, 64)     \
     P(PackedStokes, 2, 2, 64)     \
-    P(PackedStokesS6B6, 1, 4, 64) \
-    P(PackedStokesRcp, 1, 4, 64)  \
     P(PackedStokes, 1, 5, 64)     \
     P(PackedStokes, 1, 5, 128)    \
     P(PackedStokes, 1, 6, 64)     \
-    P(PackedStokesS6, 1, 7, 64)   \
-    P(PackedStokes, 1, 6, 128)    \
     P(PackedLaplaceReg, 1, 2, 128) \
     P(PackedLaplaceReg, 1, 4, 128) \
     P(PackedLaplaceReg, 1, 2, 256) \
