@@ -71,6 +71,9 @@ def _args():
                              "sphere100_elastance", "sphere100_resistance", "ellipsoidT5000_mobility",
                              "ellipsoidT10000_mobility"],
                     help="secondary measurements (their own JSON line); the default is the benchmark")
+    ap.add_argument("--pair-variant", default="",
+                    help="force this entry of the pair-kernel table (its name, e.g. 'PackedStokes<1,4,64>') "
+                         "instead of the autotuner's pick (default headline only)")
     ap.add_argument("--bodies", type=int, default=0,
                     help="secondary workloads: override the body count (smaller cases for profiling)")
     ap.add_argument("--compare-nv40", action="store_true",
@@ -435,7 +438,15 @@ def main():
     from paper_2409_04215_gb300 import MFS
 
     wl = make_workload(WORKLOAD, count=24) if args.small else make_workload(WORKLOAD)
-    ctx = MFS.from_workload(wl, profile=1)
+    forced = {}
+    if args.pair_variant:
+        from paper_2409_04215_gb300.api import pair_variants
+
+        idx = [i for i, name, d, nrhs, grad in pair_variants() if name == args.pair_variant and not grad]
+        if not idx:
+            raise SystemExit(f"no pair-kernel variant named {args.pair_variant!r}")
+        forced = {"pair_variant": idx[0]}
+    ctx = MFS.from_workload(wl, profile=1, **forced)
     F = torch.tensor(wl.F, device=dev)
     T = torch.tensor(wl.T, device=dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2, written between steps
@@ -542,7 +553,8 @@ def main():
         "config": {"workload": f"{WORKLOAD}: 100 unit spheres, volume fraction 0.1, min gap 0.1, M=1200, N=600, "
                                "R_p=0.7", "nrhs": wl.nrhs, "gmres_tol": 1e-7,
                    "l2": "512 MB buffer written between timed steps (flush)",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "pair_variant": args.pair_variant + " (forced)" if args.pair_variant else "autotuned"},
         "profile_case": "24 spheres (not a bench line)" if args.small else None,
         "solve_ms": ms_max / args.steps,
         "gmres_iters": infos[-1].iters,
