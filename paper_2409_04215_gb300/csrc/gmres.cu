@@ -31,51 +31,88 @@ __device__ __forceinline__ void lane_chunk(const GmresDev &gd, int l, int b, lon
     e1 = s0 + len * (b + 1) / gd.part_blocks;
 }
 
-// part[l][b][i] = sum over chunk b of lane l of V[i][e] * w[e], i = 0..j  (grid: PB x L).  Eight
-// columns at a time: w[e] is read once per group, eight accumulators per thread, one grouped block
-// reduction (warp shuffles, then the warps' sums added in a fixed order) per group.
-__global__ void mdot_kernel(GmresDev gd, const double *w) {
-    constexpr int G = 8;
+#define MDOT_THREADS 512
+
+// Columns i0 .. i0+G-1 of one block's chunk: part[l][b][i] = sum over the chunk of V[i][e] * w[e].
+// The loop is bound by memory latency, not by the FP64 pipe: 16 warps per block, four elements per
+// step (4 (G + 1) independent loads in flight per thread).  The block's G x MDOT_THREADS partials go
+// to shared memory and warp g adds column g's values in a fixed order (16 per lane, then a shuffle
+// tree): GB300 executes FP64 at about 2 DFMA per clock per SM, so the reduction costs 21 FP64
+// instructions per column per block rather than a shuffle tree per thread and column.
+template <int G>
+__device__ __forceinline__ void mdot_group(const GmresDev &gd, const double *w, long long e0, long long e1, int i0,
+                                           double *sh, double *dst) {
+    double acc[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) acc[g] = 0.0;
+    const double *V = gd.V + (size_t)i0 * gd.n;
+    const long long step = blockDim.x;
+    long long e = e0 + threadIdx.x;
+    for (; e + 3 * step < e1; e += 4 * step) {
+        double we[4], v[G][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) we[u] = w[e + u * step];
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[g][u] = V[(size_t)g * gd.n + e + u * step];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int g = 0; g < G; ++g) acc[g] = fma(v[g][u], we[u], acc[g]);
+    }
+    for (; e < e1; e += step) {
+        const double we = w[e];
+#pragma unroll
+        for (int g = 0; g < G; ++g) acc[g] = fma(V[(size_t)g * gd.n + e], we, acc[g]);
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) sh[g * MDOT_THREADS + threadIdx.x] = acc[g];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int g = warp; g < G; g += nw) {
+        double r = 0.0;
+        for (int k = lane; k < (int)blockDim.x; k += 32) r += sh[g * MDOT_THREADS + k];
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+        if (lane == 0) dst[i0 + g] = r;
+    }
+    __syncthreads();
+}
+
+// part[l][b][i] = sum over chunk b of lane l of V[i][e] * w[e], i = 0..j  (grid: PB x L, MDOT_THREADS
+// threads): groups of 8 columns, then one group of 4, 2 and 1 for the rest (no predicated-off FP64
+// work).
+__global__ void __launch_bounds__(MDOT_THREADS) mdot_kernel(GmresDev gd, const double *w) {
     const int b = blockIdx.x, l = blockIdx.y;
     if (!gd.active[l]) return;
     const int j = *gd.jcur;
-    __shared__ double sh[GM_THREADS / 32][G];
+    __shared__ double sh[8 * MDOT_THREADS];
     long long e0, e1;
     lane_chunk(gd, l, b, e0, e1);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i0 = 0; i0 <= j; i0 += G) {
-        const int ng = min(G, j + 1 - i0);
-        double acc[G];
-#pragma unroll
-        for (int g = 0; g < G; ++g) acc[g] = 0.0;
-        for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-            const double we = w[e];
-#pragma unroll
-            for (int g = 0; g < G; ++g)
-                if (g < ng) acc[g] += gd.V[(size_t)(i0 + g) * gd.n + e] * we;
-        }
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            double v = acc[g];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) sh[wid][g] = v;
-        }
-        __syncthreads();
-        if (threadIdx.x < ng) {
-            double s = 0.0;
-            for (int q = 0; q < nw; ++q) s += sh[q][threadIdx.x];
-            gd.part[((size_t)l * gd.part_blocks + b) * (gd.m + 1) + i0 + threadIdx.x] = s;
-        }
-        __syncthreads();
-    }
+    double *dst = gd.part + ((size_t)l * gd.part_blocks + b) * (gd.m + 1);
+    int i0 = 0;
+    for (; i0 + 8 <= j + 1; i0 += 8) mdot_group<8>(gd, w, e0, e1, i0, sh, dst);
+    if (j + 1 - i0 >= 4) { mdot_group<4>(gd, w, e0, e1, i0, sh, dst); i0 += 4; }
+    if (j + 1 - i0 >= 2) { mdot_group<2>(gd, w, e0, e1, i0, sh, dst); i0 += 2; }
+    if (j + 1 - i0 >= 1) mdot_group<1>(gd, w, e0, e1, i0, sh, dst);
 }
 
-// Sum over the block partials of lane l, entry i, by one warp (lanes stride over the blocks, then a
-// fixed shuffle tree: the same order every call).
+// Sum over the block partials of lane l, entry i, by one warp: each lane adds its blocks (four
+// independent loads per step), then a fixed shuffle tree -- the same order every call.
 __device__ __forceinline__ double warp_part_sum(const GmresDev &gd, int l, int i) {
     const int lane = threadIdx.x & 31;
-    double s = 0.0;
-    for (int b = lane; b < gd.part_blocks; b += 32) s += gd.part[((size_t)l * gd.part_blocks + b) * (gd.m + 1) + i];
+    const double *p = gd.part + (size_t)l * gd.part_blocks * (gd.m + 1) + i;
+    const size_t stride = (size_t)(gd.m + 1);
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int b = lane;
+    for (; b + 96 < gd.part_blocks; b += 128) {
+        s0 += p[(size_t)b * stride];
+        s1 += p[(size_t)(b + 32) * stride];
+        s2 += p[(size_t)(b + 64) * stride];
+        s3 += p[(size_t)(b + 96) * stride];
+    }
+    for (; b < gd.part_blocks; b += 32) s0 += p[(size_t)b * stride];
+    double s = (s0 + s1) + (s2 + s3);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     return s;
 }
@@ -96,8 +133,10 @@ __global__ void mdot_reduce_kernel(GmresDev gd, double *htmp, int accumulate) {
     }
 }
 
-// w -= sum_{i<=j} htmp[l][i] V[i]   (grid: PB x L)
-__global__ void update_kernel(GmresDev gd, double *w, const double *htmp) {
+// w -= sum_{i<=j} htmp[l][i] V[i]   (grid: PB x L).  Four elements per step and eight columns per
+// inner step, so that 32 independent loads are in flight per thread (the kernel is bound by memory
+// latency); each element's sum runs over the columns in order (one FP64 chain per element).
+__global__ void __launch_bounds__(2 * GM_THREADS) update_kernel(GmresDev gd, double *w, const double *htmp) {
     const int b = blockIdx.x, l = blockIdx.y;
     if (!gd.active[l]) return;
     const int j = *gd.jcur;
@@ -106,18 +145,35 @@ __global__ void update_kernel(GmresDev gd, double *w, const double *htmp) {
     __syncthreads();
     long long e0, e1;
     lane_chunk(gd, l, b, e0, e1);
-    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        // four independent FP64 chains (GB300's FP64 latency would serialise a single one)
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    const long long step = blockDim.x;
+    long long e = e0 + threadIdx.x;
+    for (; e + 3 * step < e1; e += 4 * step) {
+        double a[4] = {0.0, 0.0, 0.0, 0.0};
         int i = 0;
-        for (; i + 3 <= j; i += 4) {
-            s0 += h[i] * gd.V[(size_t)i * gd.n + e];
-            s1 += h[i + 1] * gd.V[(size_t)(i + 1) * gd.n + e];
-            s2 += h[i + 2] * gd.V[(size_t)(i + 2) * gd.n + e];
-            s3 += h[i + 3] * gd.V[(size_t)(i + 3) * gd.n + e];
+        for (; i + 8 <= j + 1; i += 8) {
+            const double *V = gd.V + (size_t)i * gd.n + e;
+            double v[8][4];
+#pragma unroll
+            for (int g = 0; g < 8; ++g)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[g][u] = V[(size_t)g * gd.n + u * step];
+#pragma unroll
+            for (int g = 0; g < 8; ++g)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) a[u] = fma(h[i + g], v[g][u], a[u]);
         }
-        for (; i <= j; ++i) s0 += h[i] * gd.V[(size_t)i * gd.n + e];
-        w[e] -= (s0 + s1) + (s2 + s3);
+        for (; i <= j; ++i) {
+            const double *V = gd.V + (size_t)i * gd.n + e;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] = fma(h[i], V[u * step], a[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) w[e + u * step] -= a[u];
+    }
+    for (; e < e1; e += step) {
+        double a = 0.0;
+        for (int i = 0; i <= j; ++i) a = fma(h[i], gd.V[(size_t)i * gd.n + e], a);
+        w[e] -= a;
     }
 }
 
@@ -128,8 +184,19 @@ __global__ void norm_part_kernel(GmresDev gd, const double *x, int all_lanes) {
     __shared__ double sh[32];
     long long e0, e1;
     lane_chunk(gd, l, b, e0, e1);
-    double acc = 0.0;
-    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) acc += x[e] * x[e];
+    // four elements per step: independent loads in flight (the loop is bound by memory latency)
+    const long long step = blockDim.x;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    long long e = e0 + threadIdx.x;
+    for (; e + 3 * step < e1; e += 4 * step) {
+        const double x0 = x[e], x1 = x[e + step], x2 = x[e + 2 * step], x3 = x[e + 3 * step];
+        a0 = fma(x0, x0, a0);
+        a1 = fma(x1, x1, a1);
+        a2 = fma(x2, x2, a2);
+        a3 = fma(x3, x3, a3);
+    }
+    for (; e < e1; e += step) a0 = fma(x[e], x[e], a0);
+    double acc = (a0 + a1) + (a2 + a3);
     acc = block_sum(acc, sh);
     if (threadIdx.x == 0) gd.part[((size_t)l * gd.part_blocks + b) * (gd.m + 1)] = acc;
 }
@@ -150,7 +217,16 @@ __global__ void normalise_kernel(GmresDev gd, const double *x, double *vdst, dou
     const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
     long long e0, e1;
     lane_chunk(gd, l, b, e0, e1);
-    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) vdst[e] = x[e] * inv;
+    const long long step = blockDim.x;
+    long long e = e0 + threadIdx.x;
+    for (; e + 3 * step < e1; e += 4 * step) {
+        const double x0 = x[e], x1 = x[e + step], x2 = x[e + 2 * step], x3 = x[e + 3 * step];
+        vdst[e] = x0 * inv;
+        vdst[e + step] = x1 * inv;
+        vdst[e + 2 * step] = x2 * inv;
+        vdst[e + 3 * step] = x3 * inv;
+    }
+    for (; e < e1; e += step) vdst[e] = x[e] * inv;
 }
 
 __global__ void init_lanes_kernel(GmresDev gd) {
@@ -198,15 +274,17 @@ __global__ void givens_kernel(GmresDev gd, const double *hn) {
         const int m = gd.m;
         double *H = gd.H + (size_t)ll * (m + 1) * m;  // H[i][jj] at i*m + jj
         double *cs = gd.cs + (size_t)ll * m, *sn = gd.sn + (size_t)ll * m, *g = gd.g + (size_t)ll * (m + 1);
-        for (int i = 0; i <= j; ++i) H[i * m + j] = gd.hbuf[(size_t)ll * (m + 1) + i];
+        // column j from hbuf, rotated by the previous Givens rotations with one value carried in a
+        // register (the loads of hbuf, cs and sn do not wait on the chain; H is written once)
+        const double *hcol = gd.hbuf + (size_t)ll * (m + 1);
         const double h_next = hn[ll];
-        H[(j + 1) * m + j] = h_next;
+        double carry = hcol[0];
         for (int i = 0; i < j; ++i) {
-            const double a = H[i * m + j], c = H[(i + 1) * m + j];
-            H[i * m + j] = cs[i] * a + sn[i] * c;
-            H[(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+            const double c = hcol[i + 1];
+            H[i * m + j] = cs[i] * carry + sn[i] * c;
+            carry = -sn[i] * carry + cs[i] * c;
         }
-        const double a = H[j * m + j], c = H[(j + 1) * m + j];
+        const double a = carry, c = h_next;
         const double den = hypot(a, c);
         cs[j] = den > 0.0 ? a / den : 1.0;
         sn[j] = den > 0.0 ? c / den : 0.0;
@@ -274,9 +352,9 @@ cudaError_t gmres_init(GmresDev &gd, const double *b, cudaStream_t st) {
 cudaError_t gmres_arnoldi(GmresDev &gd, double *w, cudaStream_t st) {
     dim3 grid(gd.part_blocks, gd.L);
     for (int pass = 0; pass < 2; ++pass) {  // CGS2
-        mdot_kernel<<<grid, GM_THREADS, 0, st>>>(gd, w);
+        mdot_kernel<<<grid, MDOT_THREADS, 0, st>>>(gd, w);
         mdot_reduce_kernel<<<gd.L, 512, 0, st>>>(gd, gd.htmp, pass);  // 16 warps over the entries i <= j
-        update_kernel<<<grid, GM_THREADS, 0, st>>>(gd, w, gd.htmp);
+        update_kernel<<<grid, 2 * GM_THREADS, 0, st>>>(gd, w, gd.htmp);  // latency-bound: more loads in flight
     }
     norm_part_kernel<<<grid, GM_THREADS, 0, st>>>(gd, w, 0);
     normalise_kernel<<<grid, GM_THREADS, 0, st>>>(gd, w, nullptr, gd.hn, 0);

@@ -633,10 +633,12 @@ mfs_status ensure_gmres(mfs_ctx *ctx, int nrhs) {
     gd.m = m;
     gd.n = n;
     gd.tol = ctx->opt.gmres_tol;
-    // blocks per lane: enough parallelism for the reductions, at least one
+    // blocks per lane: one wave over all lanes (SMs / L, so that no SM runs two blocks while others
+    // run one), but at least ~2048 elements per block (8 per thread), so that the FP64 work of the dot
+    // products outweighs their block reductions
     const long long per_lane = n / std::max(L, 1);
-    gd.part_blocks = (int)std::max<long long>(1, std::min<long long>(4 * (long long)ctx->sm_count / std::max(L, 1) + 1,
-                                                                     (per_lane + 1023) / 1024));
+    gd.part_blocks = (int)std::max<long long>(1, std::min<long long>((long long)ctx->sm_count / std::max(L, 1),
+                                                                     (per_lane + 2047) / 2048));
     gd.part_blocks = std::min(gd.part_blocks, 512);
     std::vector<long long> seg(L + 1);
     for (int h = 0; h < nrhs; ++h)
