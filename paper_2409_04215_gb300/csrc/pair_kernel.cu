@@ -1008,6 +1008,7 @@ static int occupancy_variant() {
     P(PackedLaplaceReg, 1, 2, 256) \
     P(PackedLaplaceReg, 2, 2, 128) \
     P(PackedLaplaceReg, 4, 2, 128) \
+    P(PackedLaplaceReg, 1, 8, 64)  \
     G(1, 4, 128)                  \
     G(2, 2, 128)                  \
     G(3, 2, 128)                  \
