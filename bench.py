@@ -406,6 +406,23 @@ def secondary(args):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(ms: float, dist=None, device=None) -> float:
+    """The slowest rank's timed milliseconds (all-reduce MAX; identity on one process).  The tensor
+    lives on `device` (the rank's GPU under NCCL, the CPU under gloo)."""
+    if dist is None:
+        return float(ms)
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_step_per_rank: float, steps: int, world: int, ms_max: float) -> float:
+    """Units of all ranks per second of the slowest rank (replicas: every rank does the same work)."""
+    return units_per_step_per_rank * steps * world / (ms_max / 1e3)
+
+
 def main():
     args = _args()
     if args.impl == "gpu" and args.workload == "sphere100_resistance":
@@ -476,12 +493,9 @@ def main():
         dist.barrier()
     ck = clocks.stop()
     ms = sum(a.elapsed_time(b) for a, b in ev)
-    t_max = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if dist:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms_max = float(t_max.item())
+    ms_max = max_over_ranks(ms, dist, dev)
     pairs_step = infos[-1].pairs * wl.nrhs
-    value = pairs_step * args.steps * world / (ms_max / 1e3)
+    value = whole_job_rate(pairs_step, args.steps, world, ms_max)
 
     # pair kernel roofline (device time of the kernel launches alone, CUDA events on the library's stream)
     pair_ms = sum(i.ms_pairs for i in infos)
