@@ -1,7 +1,7 @@
 """GPU parity: libmfs (through the C ABI) against the FP64 oracle on the same seeded inputs.
 
 Tolerances (relative 2-norm unless said otherwise): matvec <= 1e-6 and solved velocities /
-potentials <= 1e-5 (the stated targets of this build); bare pair sums <= 1e-6; the FP64
+potentials <= 1e-5 (the accuracy targets of the FP32 path); bare pair sums <= 1e-6; the FP64
 reference path (precision = 1) <= 1e-11.  Sizes are ragged on purpose: N not a multiple of
 4, M not a multiple of 32, tiles that straddle bodies, several suspensions, up to 4 rhs.
 """
