@@ -80,6 +80,10 @@ cudaError_t tc_gemm(int pieces, const TcMap *b, const TcMap *a, int m, int n, in
 // FP64 [rows][cols] -> pieces dst[p][cols][ld_dst] (transposed, zero K padding), p at offset p * pstride.
 cudaError_t split_pieces_transpose(const double *src, int rows, int cols, float *dst, int ld_dst, size_t pstride,
                                    int pieces, cudaStream_t st);
+// pieces src[p][rows][ld_src] (first cols valid) -> dst[p][cols][ld_dst] (transposed, zero padding to
+// ld_dst >= rows), p at offsets p * sstride and p * dstride.
+cudaError_t transpose_pieces(const float *src, int rows, int cols, int ld_src, size_t sstride, float *dst, int ld_dst,
+                             size_t dstride, int pieces, cudaStream_t st);
 // sum_z P[z] ([rows][cols], (hi, lo) pairs, double-float sums) -> pieces dst[p][rows][ld_dst].
 cudaError_t reduce_pieces(int S, int rows, int cols, const float2 *P, float *dst, int ld_dst, size_t pstride,
                           int pieces, cudaStream_t st);

@@ -48,6 +48,11 @@ struct FactorSet {
     float *Utp = nullptr, *Wptp = nullptr, *Wrtp = nullptr;  // [piece][r or dN][ld]
     size_t ut_stride = 0, wt_stride = 0;
     TcMap mU[3], mWp[3], mWr[3];
+    // the transposed apply (adjoint), built on first use: pieces of U [dM][ld2] and of W^T [r][ld2]
+    bool tcT_ready = false;
+    float *Un = nullptr, *WpT = nullptr, *WrT = nullptr;
+    size_t un_stride = 0;
+    TcMap mUn[3], mWpT[3], mWrT[3];
 };
 
 struct ShapeHost {
@@ -60,6 +65,7 @@ struct ShapeHost {
     double *Pk = nullptr;                              // split-K chunk results
     size_t Pk_count = 0;
     double *O64 = nullptr, *PkT = nullptr;             // adjoint: transposed-apply output and chunks
+    float2 *PtcT = nullptr;                            // adjoint: tensor-core chunk results
     // tensor-core apply scratch: K-major TF32 pieces of the columns, chunk results
     int pieces = 0;        // TF32 pieces per operand (3: 6xTF32 products, 2: 3xTF32)
     int ld1 = 0, ld2 = 0;  // K extents padded to 32: roundup(dM, 32), roundup(r, 32)
@@ -743,6 +749,36 @@ mfs_status ensure_transposed(mfs_ctx *ctx) {
         }
         CK(ctx->alloc(&sh.PkT, need));
         CK(ctx->alloc(&sh.O64, (size_t)R * nb * m));
+        FactorSet &fx = sh.fs[0];
+        if (fx.tc_ready) {  // tensor cores: the factor pieces transposed (exact), their maps, chunk results
+            const int np = sh.pieces;
+            fx.un_stride = (size_t)m * sh.ld2;
+            CK(ctx->alloc(&fx.Un, np * fx.un_stride));
+            CK(ctx->alloc(&fx.WpT, np * fx.wt_stride));
+            CK(ctx->alloc(&fx.WrT, np * fx.wt_stride));
+            // U^T pieces [r][ld1] -> U pieces [dM][ld2]; W pieces [dN][ld2] -> W^T pieces [r][ld2]
+            CK(transpose_pieces(fx.Utp, n, m, sh.ld1, fx.ut_stride, fx.Un, sh.ld2, fx.un_stride, np, 0));
+            CK(transpose_pieces(fx.Wptp, n, n, sh.ld2, fx.wt_stride, fx.WpT, sh.ld2, fx.wt_stride, np, 0));
+            CK(transpose_pieces(fx.Wrtp, n, n, sh.ld2, fx.wt_stride, fx.WrT, sh.ld2, fx.wt_stride, np, 0));
+            CK(cudaDeviceSynchronize());
+            bool enc = true;
+            for (int p = 0; p < np; ++p)
+                enc = enc && make_tc_map(fx.mUn[p], fx.Un + p * fx.un_stride, m, sh.ld2, 128) &&
+                      make_tc_map(fx.mWpT[p], fx.WpT + p * fx.wt_stride, n, sh.ld2, 128) &&
+                      make_tc_map(fx.mWrT[p], fx.WrT + p * fx.wt_stride, n, sh.ld2, 128);
+            if (!enc) {
+                ctx->last_error = "tensor-map encoding for the transposed tensor-core apply failed";
+                return MFS_ERR_CUDA;
+            }
+            size_t needT = 0;
+            for (int h = 1; h <= R; ++h) {
+                const int cols = h * nb;
+                needT = std::max(needT, (size_t)tc_gemm_sz(n, tc_gemm_chunks(cols, n, n, ctx->sm_count, np)) * cols * n);
+                needT = std::max(needT, (size_t)tc_gemm_sz(n, tc_gemm_chunks(cols, m, n, ctx->sm_count, np)) * cols * m);
+            }
+            CK(ctx->alloc(&sh.PtcT, needT));
+            fx.tcT_ready = true;
+        }
     }
     ctx->trans_ready = true;
     return MFS_OK;
@@ -782,7 +818,40 @@ mfs_status precondT_dev(mfs_ctx *ctx, const double *z, double *out, int project,
         const int nb = (int)sh.bodies.size();
         if (nb == 0) continue;
         const int ncols = nb * nrhs;
-        const ShapeDev &sd = sh.fs[0].dev;
+        const FactorSet &fx = sh.fs[0];
+        const ShapeDev &sd = fx.dev;
+        if (fx.tcT_ready && ctx->opt.precision == 0) {
+            // tensor cores, as the forward apply: x = W^T (R_N^T z) with the K = dN column pieces in Tp,
+            // x cut back into pieces (same layout, Tp reused), out = R_M U x kept in FP64
+            const int np = sh.pieces;
+            auto it = sh.amaps.find(ncols);
+            if (it == sh.amaps.end()) {
+                std::array<TcMap, 6> mp;
+                const int bn = tc_gemm_bn(ncols, np);
+                bool enc = true;
+                for (int p = 0; p < np; ++p)
+                    enc = enc && make_tc_map(mp[p], sh.Ap + p * sh.ap_stride, ncols, sh.ld1, bn) &&
+                          make_tc_map(mp[3 + p], sh.Tp + p * sh.tp_stride, ncols, sh.ld2, bn);
+                if (!enc) {
+                    ctx->last_error = "tensor-map encoding for the tensor-core apply failed";
+                    return MFS_ERR_CUDA;
+                }
+                it = sh.amaps.emplace(ncols, mp).first;
+            }
+            const TcMap *colmaps = it->second.data() + 3;
+            CK(gather_rotate_pieces(3, z, ctx->sumN * 3, sh.col_body, sh.col_rhs, ctx->src_off_d, ctx->rot64_d, ncols,
+                                    sd.dN, sh.Tp, sh.ld2, sh.tp_stride, np, st));
+            const int S1 = tc_gemm_chunks(ncols, sd.r, sd.dN, ctx->sm_count, np);
+            CK(tc_gemm(np, project ? fx.mWpT : fx.mWrT, colmaps, ncols, sd.r, sd.dN, S1, sh.PtcT, ctx->err_d, st));
+            CK(reduce_pieces(tc_gemm_sz(sd.dN, S1), ncols, sd.r, sh.PtcT, sh.Tp, sh.ld2, sh.tp_stride, np, st));
+            const int S2 = tc_gemm_chunks(ncols, sd.dM, sd.r, ctx->sm_count, np);
+            CK(tc_gemm(np, fx.mUn, colmaps, ncols, sd.dM, sd.r, S2, sh.PtcT, ctx->err_d, st));
+            CK(reduce_f64(tc_gemm_sz(sd.r, S2), (size_t)ncols * sd.dM, sh.PtcT, sh.O64, st));
+            CK(scatter_rotate(3, nullptr, sh.O64, sh.col_body, sh.col_rhs, ctx->tgt_off_d, ctx->rot_d, ctx->rot64_d,
+                              ncols, sd.dM, ctx->sumM, out, st));
+            ctx->launches += 6;
+            continue;
+        }
         CK(gather_rotate(3, z, ctx->sumN * 3, sh.col_body, sh.col_rhs, ctx->src_off_d, ctx->rot64_d, ncols, sd.dN,
                          sh.A, nullptr, st));
         const int S1 = gemm_splitk_chunks(ncols, sd.r, sd.dN, ctx->sm_count);

@@ -358,6 +358,36 @@ __global__ void gather_rotate_pieces_kernel(int D, const double *gamma, int sum_
     }
 }
 
+// dst[p][c][r] = src[p][r][c] for r < rows, c < cols, zero for r in [rows, ld_dst): the pieces of a
+// factor laid out for the transposed product (a transposition of TF32 values, exact).  Tiles of
+// 32 x 32 through shared memory (both sides coalesced).
+__global__ void transpose_pieces_kernel(const float *src, int rows, int cols, int ld_src, size_t sstride, float *dst,
+                                        int ld_dst, size_t dstride) {
+    __shared__ float t[32][33];
+    const int p = blockIdx.z;
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    const float *sp = src + p * sstride;
+    float *dp = dst + p * dstride;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        t[i][threadIdx.x] = (r < rows && c < cols) ? sp[(size_t)r * ld_src + c] : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (c < cols && r < ld_dst) dp[(size_t)c * ld_dst + r] = t[threadIdx.x][i];
+    }
+}
+
+cudaError_t transpose_pieces(const float *src, int rows, int cols, int ld_src, size_t sstride, float *dst, int ld_dst,
+                             size_t dstride, int pieces, cudaStream_t st) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    if (pieces < 2 || pieces > 3 || ld_dst < rows || ld_src < cols) return cudaErrorInvalidValue;
+    dim3 grid((cols + 31) / 32, (ld_dst + 31) / 32, pieces), block(32, 8);
+    transpose_pieces_kernel<<<grid, block, 0, st>>>(src, rows, cols, ld_src, sstride, dst, ld_dst, dstride);
+    return cudaGetLastError();
+}
+
 cudaError_t split_pieces_transpose(const double *src, int rows, int cols, float *dst, int ld_dst, size_t pstride,
                                    int pieces, cudaStream_t st) {
     if (cols == 0) return cudaSuccess;

@@ -28,13 +28,14 @@ def _loss_grads(U, W):
     return 2.0 * U, 0.6 * W
 
 
+@pytest.mark.parametrize("tensor_cores", [1, 0])  # the transposed one-body apply on tcgen05 or CUDA cores
 @pytest.mark.parametrize("nrhs", [1, 2])
-def test_vjp_matches_oracle_adjoint(nrhs):
+def test_vjp_matches_oracle_adjoint(nrhs, tensor_cores):
     from oracle import Problem
     from paper_2409_04215_gb300 import MFS
 
     wl = _mixed("stokes", P=6, m=160, n=80, seed=31, nsusp=2)
-    ctx = MFS.from_workload(wl, gmres_tol=1e-10)
+    ctx = MFS.from_workload(wl, gmres_tol=1e-10, tensor_cores=tensor_cores)
     F = torch.tensor(wl.F[:nrhs], device="cuda")
     T = torch.tensor(wl.T[:nrhs], device="cuda")
     U, W, _ = ctx.solve_mobility(F, T)
