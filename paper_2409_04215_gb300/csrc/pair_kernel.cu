@@ -855,39 +855,60 @@ __global__ void __launch_bounds__(NT, MINB) pair_sum_kernel(PairGeom geo, PairWo
 }
 
 // Epilogue: out[r][t][d] = beta * base[r][t][d] + scale * (sum of the CTA shares of target t).
+// One block per tile; the CTAs that share the tile and the slot each wrote (0: the tile is where the
+// CTA's range starts, 1: where it ends) are found once per block, and the threads then run over the
+// tile's (target, component) entries, which are contiguous in every array for one right-hand side.
 template <int D, int NRHS>
-__global__ void pair_epilogue_kernel(PairWork work, const double *base, double beta, double scale, double *out,
+__global__ void __launch_bounds__(1024) pair_epilogue_kernel(PairWork work, const double *base, double beta, double scale, double *out,
                                      int ntargets) {
     constexpr int C = D * NRHS;
+    constexpr int MAXS = 256;
+    __shared__ signed char slot_of[MAXS];  // per CTA gA + i: slot 0 / 1, -1 for an empty range
     const PairTile tl = work.tiles[blockIdx.x];
     const long long W = work.total_units;
-    for (int t = tl.t0 + threadIdx.x; t < tl.t1; t += blockDim.x) {
-        double v[C];
-#pragma unroll
-        for (int c = 0; c < C; ++c) v[c] = 0.0;
+    const int ns = (tl.gA >= 0 && tl.gA != tl.gB) ? tl.gB - tl.gA + 1 : 0;
+    for (int i = threadIdx.x; i < ns && i < MAXS; i += blockDim.x) {
+        const int gg = tl.gA + i;
+        const long long b0 = (long long)gg * W / work.G, b1 = (long long)(gg + 1) * W / work.G;
+        slot_of[i] = b0 >= b1 ? -1 : (b0 >= tl.u0 ? 0 : 1);
+    }
+    __syncthreads();
+    const int nt = tl.t1 - tl.t0;
+    for (int q = threadIdx.x; q < nt * C; q += blockDim.x) {
+        const int t = tl.t0 + q / C, c = q % C;
+        double v = 0.0;
         if (tl.gA >= 0) {
             if (tl.gA == tl.gB) {
-#pragma unroll
-                for (int c = 0; c < C; ++c) v[c] = work.direct[(size_t)t * C + c];
+                v = work.direct[(size_t)t * C + c];
             } else {
-                for (int gg = tl.gA; gg <= tl.gB; ++gg) {
-                    const long long b0 = (long long)gg * W / work.G, b1 = (long long)(gg + 1) * W / work.G;
-                    if (b0 >= b1) continue;
-                    const int slot = (b0 >= tl.u0) ? 0 : 1;
-                    const double *src = work.partial + ((size_t)(gg * 2 + slot) * work.tile_targets + (t - tl.t0)) * C;
-#pragma unroll
-                    for (int c = 0; c < C; ++c) v[c] += src[c];
+                // shares of CTAs gA, gA + 1, ... added in that order; four loads issued before the adds
+                const size_t within = (size_t)(t - tl.t0) * C + c, per_slot = (size_t)work.tile_targets * C;
+                auto share = [&](int i) -> double {
+                    int slot;
+                    if (i < MAXS) {
+                        slot = slot_of[i];
+                    } else {
+                        const int gg = tl.gA + i;
+                        const long long b0 = (long long)gg * W / work.G, b1 = (long long)(gg + 1) * W / work.G;
+                        slot = b0 >= b1 ? -1 : (b0 >= tl.u0 ? 0 : 1);
+                    }
+                    return slot < 0 ? 0.0 : work.partial[(size_t)((tl.gA + i) * 2 + slot) * per_slot + within];
+                };
+                int i = 0;
+                for (; i + 4 <= ns; i += 4) {
+                    const double p0 = share(i), p1 = share(i + 1), p2 = share(i + 2), p3 = share(i + 3);
+                    v += p0;
+                    v += p1;
+                    v += p2;
+                    v += p3;
                 }
+                for (; i < ns; ++i) v += share(i);
             }
         }
-#pragma unroll
-        for (int h = 0; h < NRHS; ++h)
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-                const size_t o = ((size_t)h * ntargets + t) * D + d;
-                const double b = base ? beta * base[o] : 0.0;
-                out[o] = b + scale * v[h * D + d];
-            }
+        const int h = c / D, d = c % D;
+        const size_t o = ((size_t)h * ntargets + t) * D + d;
+        const double b = base ? beta * base[o] : 0.0;
+        out[o] = b + scale * v;
     }
 }
 
@@ -1064,7 +1085,7 @@ cudaError_t pair_launch(int vi, const PairGeom &geo, const PairWork &work, int *
 
 cudaError_t pair_epilogue(int D, int nrhs, const PairWork &work, const double *base, double beta, double scale,
                           double *out, int ntargets, cudaStream_t st) {
-    const int threads = 256;
+    const int threads = 1024;  // one block per tile: a few hundred blocks at most, so wide blocks
     if (work.ntiles == 0) return cudaSuccess;
 #define E(D_, R_)                                                                                      \
     if (D == D_ && nrhs == R_) {                                                                       \
@@ -1259,7 +1280,7 @@ extern "C" mfs_status mfs_stokeslet_sum_noalloc(const double *targets, int32_t n
     work.tile_targets = TT;
     work.include_self = 1;
     if (launch_variant<Pol, NT>(geo, work, &meta->err, st) != cudaSuccess) return MFS_ERR_CUDA;
-    pair_epilogue_kernel<3, 1><<<ntiles, 256, 0, st>>>(work, nullptr, 0.0, 1.0 / (8.0 * MFS_PI * mu), u,
+    pair_epilogue_kernel<3, 1><<<ntiles, 1024, 0, st>>>(work, nullptr, 0.0, 1.0 / (8.0 * MFS_PI * mu), u,
                                                        num_targets);
     return cudaGetLastError() == cudaSuccess ? MFS_OK : MFS_ERR_CUDA;
 }
