@@ -142,6 +142,19 @@ mfs_status mfs_update_centers(mfs_ctx *ctx, const double *centers, void *stream)
 mfs_status mfs_matvec(mfs_ctx *ctx, const double *gamma, double *y, int32_t nrhs, void *stream);
 
 /*
+ * mfs_matvec_transposed -- y = A^T w for the matrix A of Eq. 2esysprec (the operator the adjoint of
+ * mfs_mobility_vjp solves with; the paper solves forward problems only):
+ *   y^(k') = w^(k') + ((I - L^(k')) S_L^(k')+)^T sum_{k != k', same suspension} S^(kk')^T w^(k),
+ * where S^(kk')^T is the Stokeslet pair sum with the collocation points of body k as sources and the
+ * proxy points of body k' as targets (the Stokeslet is symmetric and even in r), and the transposed
+ * one-body apply is R_M U W^T R_N^T (Eq. pseudo transposed).  Stokes contexts only (else
+ * MFS_ERR_INVALID_ARG).  w, y: [nrhs][sum_M][3], host or device, 1 <= nrhs <= max_rhs.  FP32 pair
+ * sums and an FP32-level one-body apply (tensor cores when tensor_cores != 0) in every precision
+ * mode.  The first call builds the transposed-apply data (a one-off setup cost, synchronising).
+ */
+mfs_status mfs_matvec_transposed(mfs_ctx *ctx, const double *w, double *y, int32_t nrhs, void *stream);
+
+/*
  * mfs_precond_apply -- lambda^(k) = S_L^(k)+ gamma^(k) (Eq. pseudo with Remark congruent), followed
  * by the projection (I - L^(k)) when project != 0 (Sec. 3.3, item 2).  gamma [nrhs][sum_M][d],
  * lambda [nrhs][sum_N][d], host or device.

@@ -46,6 +46,7 @@ EXPORTED = [
     "mfs_pair_variant",
     "mfs_pair_variant_info",
     "mfs_fp32_fma_rate",
+    "mfs_matvec_transposed",
     "mfs_dirichlet_apply",
     "mfs_dirichlet_matvec",
     "mfs_solve_capacitance",
@@ -150,6 +151,7 @@ def load_library(path: Optional[str] = None):
                               ctypes.POINTER(_PointSet), ctypes.POINTER(Options), vp]
     lib.mfs_update_centers.argtypes = [vp, vp, vp]
     lib.mfs_matvec.argtypes = [vp, vp, vp, i32, vp]
+    lib.mfs_matvec_transposed.argtypes = [vp, vp, vp, i32, vp]
     lib.mfs_precond_apply.argtypes = [vp, vp, vp, i32, i32, vp]
     lib.mfs_pair_sum.argtypes = [vp, vp, vp, i32, i32, vp]
     lib.mfs_solve_elastance.argtypes = [vp, vp, vp, i32, ctypes.POINTER(_Info), vp]
@@ -345,6 +347,15 @@ class MFS:
         nrhs = a.obj.shape[0] if a.obj.ndim == 3 else 1
         y = self._out(tuple(a.obj.shape), a)
         self._check(self._lib.mfs_matvec(self._ctx, a.ptr, y.data_ptr(), nrhs, _stream_ptr(stream, a.device)))
+        return y
+
+    def matvec_transposed(self, w, stream=None):
+        """y = A^T w (mfs_matvec_transposed), Stokes contexts; same shapes as matvec."""
+        a = _Arg(w)
+        nrhs = a.obj.shape[0] if a.obj.ndim == 3 else 1
+        y = self._out(tuple(a.obj.shape), a)
+        self._check(self._lib.mfs_matvec_transposed(self._ctx, a.ptr, y.data_ptr(), nrhs,
+                                                    _stream_ptr(stream, a.device)))
         return y
 
     def precond_apply(self, gamma, project: bool = True, stream=None):

@@ -1619,6 +1619,26 @@ mfs_status mfs_matvec(mfs_ctx *ctx, const double *gamma, double *y, int32_t nrhs
     return check_device_error(ctx, st);
 }
 
+mfs_status mfs_matvec_transposed(mfs_ctx *ctx, const double *w, double *y, int32_t nrhs, void *stream) {
+    if (!ctx || !w || !y || nrhs < 1 || nrhs > ctx->opt.max_rhs) {
+        if (ctx) ctx->last_error = "mfs_matvec_transposed: invalid argument";
+        return MFS_ERR_INVALID_ARG;
+    }
+    if (ctx->kind != MFS_STOKES) {
+        ctx->last_error = "mfs_matvec_transposed: Stokes contexts only";
+        return MFS_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    CKS(ensure_transposed(ctx));
+    const size_t n = (size_t)nrhs * ctx->sumM * 3;
+    Staged wi, yo;
+    CKS(stage_in(ctx, wi, w, n, st));
+    CKS(stage_out_alloc(ctx, yo, y, n));
+    CKS(matvec_T_dev(ctx, wi.d, yo.d, nrhs, st));
+    CKS(stage_out_finish(ctx, yo, st));
+    return check_device_error(ctx, st);
+}
+
 mfs_status mfs_precond_apply(mfs_ctx *ctx, const double *gamma, double *lambda, int32_t project, int32_t nrhs,
                              void *stream) {
     if (!ctx || !gamma || !lambda || nrhs < 1 || nrhs > ctx->opt.max_rhs) {

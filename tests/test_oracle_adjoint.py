@@ -58,3 +58,15 @@ def test_translation_invariance_of_gradient():
     U, W, _ = pr.solve_mobility(F, T, tol=1e-14)
     g, _, _ = pr.mobility_vjp(F, T, 2 * U, 0 * W)
     np.testing.assert_allclose(g.sum(axis=0), 0.0, atol=1e-10 * np.abs(g).max())
+
+
+def test_transposed_matvec_is_the_transpose_of_the_assembled_matrix():
+    """A^T w by the oracle's transposed pair sums and transposed one-body apply equals the transpose of
+    Eq. 2esysprec assembled from explicit kernel matrices and rotation blocks (rotated mixed shapes)."""
+    wl = _cluster("stokes", P=3, m=50, n=25)
+    pr = Problem(wl)
+    bodies = list(range(3))
+    A = pr.assemble_dense(bodies)
+    w = np.random.default_rng(4).standard_normal(A.shape[0])
+    ref = A.T @ w
+    np.testing.assert_allclose(pr.matvec_T(bodies, w), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
