@@ -73,7 +73,7 @@ def _args():
                     help="secondary measurements (their own JSON line); the default is the benchmark")
     ap.add_argument("--pair-variant", default="",
                     help="force this entry of the pair-kernel table (its name, e.g. 'PackedStokes<1,4,64>') "
-                         "instead of the autotuner's pick (default headline only)")
+                         "instead of the autotuner's pick (headline and secondary workloads)")
     ap.add_argument("--bodies", type=int, default=0,
                     help="secondary workloads: override the body count (smaller cases for profiling)")
     ap.add_argument("--compare-nv40", action="store_true",
@@ -298,6 +298,13 @@ def secondary(args):
     opts = {"max_iter": 100, "restart": 100} if name == "batched256_mobility" else {}
     if name.startswith("ellipsoid"):
         opts = {"max_iter": 60, "restart": 60}  # GMRES basis of 61 vectors of 3 M P doubles
+    if args.pair_variant:
+        from paper_2409_04215_gb300.api import pair_variants
+
+        idx = [i for i, vname, d, nrhs, grad in pair_variants() if vname == args.pair_variant and not grad]
+        if not idx:
+            raise SystemExit(f"no pair-kernel variant named {args.pair_variant!r}")
+        opts["pair_variant"] = idx[0]
     ctx = MFS.from_workload(wl, profile=1, **opts)
     setup_s = time.perf_counter() - t0
     laplace = wl.kind == "laplace"
