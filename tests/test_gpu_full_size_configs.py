@@ -1,0 +1,109 @@
+"""Parity at the full sizes of the other benchmark configurations, with the autotuned kernels the
+benchmark times: sampled outputs the oracle can compute one by one, else properties that hold at
+any size.
+
+* 1000 (1,1,2) spheroids, M = 2000, N = 1000 (6e6 unknowns): the matvec of Eq. 2esysprec on a
+  rigid-motion field, three target bodies against the oracle's sums over all 999 source bodies.
+* 200 spheres, M = 800, N = 400, the adjoint: the centre gradient sums to zero (translation
+  invariance); <A x, y> = <x, A^T y> on the full operator; and, since the discrete mobility matrix is
+  symmetric to the discretisation level (Sec. 3 / the oracle's R M = I pins), the force and torque
+  gradient of L = sum |U_k|^2 equals 2 x the velocities and rotations of a forward solve driven by
+  (F, T) = (U, 0).
+* 256 suspensions x 4 right-hand sides: two sampled suspensions (the smallest and one of about 20
+  bodies) against oracle solves of each right-hand side.
+"""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from mfs_inputs import make_workload  # noqa: E402
+from oracle import Problem  # noqa: E402
+from oracle.mfs_oracle import split_workload  # noqa: E402
+
+from test_gpu_parity import _rel  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+
+
+def test_spheroid1000_matvec_sampled():
+    from paper_2409_04215_gb300 import MFS
+
+    wl = make_workload("spheroid1000_mobility")
+    ctx = MFS.from_workload(wl)
+    pr = Problem(wl)
+    bodies = list(range(pr.P))
+    rng = np.random.default_rng(8)
+    V = rng.standard_normal((pr.P, 6))
+    # a rigid motion of every body at its collocation points: v + omega x (x - c) (Eq. Kdef)
+    gam = np.concatenate([(V[k, :3] + np.cross(V[k, 3:], pr.X[k] - wl.centres[k])).reshape(-1) for k in bodies])
+    y = ctx.matvec(torch.tensor(gam.reshape(1, -1, 3), device="cuda")).cpu().numpy().reshape(-1)
+    g = pr.split(bodies, gam)
+    lam_hat = [pr.pinv_apply(k, gk, project=True) for k, gk in zip(bodies, g)]
+    sample = [0, 500, 999]
+    ref = pr.pair_sum(bodies, lam_hat, include_self=False, target_bodies=sample)
+    got = pr.split(bodies, y)
+    num = sum(np.sum((got[k] - g[k] - r) ** 2) for k, r in zip(sample, ref))
+    den = sum(np.sum((g[k] + r) ** 2) for k, r in zip(sample, ref))
+    assert np.sqrt(num / den) < 1e-6
+    ctx.close()
+
+
+def test_sphere200_adjoint_properties():
+    from paper_2409_04215_gb300 import MFS
+
+    wl = make_workload("sphere200_adjoint")
+    ctx = MFS.from_workload(wl)
+    F = torch.tensor(wl.F[:1], device="cuda")
+    T = torch.tensor(wl.T[:1], device="cuda")
+    U, W, info = ctx.solve_mobility(F, T)
+    assert info.converged
+    dc, dF, dT = ctx.mobility_vjp(2.0 * U, torch.zeros_like(W), want_force_grads=True)
+    dc = dc.cpu().numpy()
+    # translation invariance: moving every body by the same vector changes nothing
+    assert np.abs(dc.sum(axis=0)).max() <= 1e-5 * np.abs(dc).sum(axis=0).max()
+    # the adjoint identity on the full operator
+    rng = np.random.default_rng(3)
+    x = torch.tensor(rng.standard_normal((1, ctx.sum_M, 3)), device="cuda")
+    yv = torch.tensor(rng.standard_normal((1, ctx.sum_M, 3)), device="cuda")
+    Ax = ctx.matvec(x)
+    lhs = float((Ax * yv).sum())
+    rhs = float((x * ctx.matvec_transposed(yv)).sum())
+    assert abs(lhs - rhs) <= 1e-6 * float(torch.linalg.norm(Ax) * torch.linalg.norm(yv))
+    # dL/d[F; T] = 2 M^T U = 2 M U (M symmetric to the discretisation level): a forward solve
+    U2, W2, _ = ctx.solve_mobility(U, torch.zeros_like(W))
+    got = np.concatenate([dF.cpu().numpy()[0], dT.cpu().numpy()[0]], axis=1)
+    want = 2.0 * np.concatenate([U2.cpu().numpy()[0], W2.cpu().numpy()[0]], axis=1)
+    assert _rel(got, want) < 1e-4
+    ctx.close()
+
+
+def test_batched256_sampled_suspensions():
+    from paper_2409_04215_gb300 import MFS
+
+    wl = make_workload("batched256_mobility")
+    ctx = MFS.from_workload(wl, max_iter=100, restart=100)
+    U, W, info = ctx.solve_mobility(torch.tensor(wl.F, device="cuda"), torch.tensor(wl.T, device="cuda"))
+    assert info.converged and info.lanes == 4 * wl.num_suspensions
+    U, W = U.cpu().numpy(), W.cpu().numpy()
+    sizes = np.diff(wl.body_offsets)
+    # the smallest suspension and one of about 20 bodies (oracle cost grows as the bodies squared)
+    for s in (int(np.argmin(sizes)), int(np.argmin(np.abs(sizes - 20)))):
+        sub = split_workload(wl, s)
+        pr = Problem(sub)
+        b0, b1 = wl.body_offsets[s], wl.body_offsets[s + 1]
+        for h in range(4):
+            Ur, Wr, _ = pr.solve_mobility(sub.F[h], sub.T[h], tol=1e-12)
+            got = np.concatenate([U[h, b0:b1], W[h, b0:b1]], 1)
+            assert _rel(got, np.concatenate([Ur, Wr], 1)) < 1e-5, (s, h)
+    ctx.close()
