@@ -149,8 +149,9 @@ mfs_status mfs_matvec(mfs_ctx *ctx, const double *gamma, double *y, int32_t nrhs
  * proxy points of body k' as targets (the Stokeslet is symmetric and even in r), and the transposed
  * one-body apply is R_M U W^T R_N^T (Eq. pseudo transposed).  Stokes contexts only (else
  * MFS_ERR_INVALID_ARG).  w, y: [nrhs][sum_M][3], host or device, 1 <= nrhs <= max_rhs.  FP32 pair
- * sums and an FP32-level one-body apply (tensor cores when tensor_cores != 0) in every precision
- * mode.  The first call builds the transposed-apply data (a one-off setup cost, synchronising).
+ * sums and an FP32-level one-body apply in every precision mode (on the tensor cores when
+ * tensor_cores != 0 and precision = 0, else the CUDA-core split-K GEMM).  The first call builds the
+ * transposed-apply data (a one-off setup cost, synchronising).
  */
 mfs_status mfs_matvec_transposed(mfs_ctx *ctx, const double *w, double *y, int32_t nrhs, void *stream);
 
