@@ -313,6 +313,16 @@ const char *mfs_pair_variant_info(int32_t index, int32_t *d, int32_t *nrhs, int3
  */
 mfs_status mfs_fp32_fma_rate(int32_t packed, double *tflops, void *stream);
 
+/*
+ * mfs_selftest_bounded_wait -- exercises the error path of the kernels' bounded device waits (the
+ * paper has no counterpart).  A one-warp kernel waits on a shared-memory mbarrier phase with the same
+ * bounded wait the pair and tensor-core kernels use; with arrive = 1 the phase is completed first and
+ * the call returns MFS_OK, with arrive = 0 nothing completes it, the waiters give up after `limit`
+ * polls (1 <= limit <= 2^24), set the device error flag and the call returns MFS_ERR_DEVICE_TIMEOUT
+ * with the CUDA context intact.  Synchronises `stream`; allocates 4 bytes (stream-ordered).
+ */
+mfs_status mfs_selftest_bounded_wait(int32_t arrive, int64_t limit, void *stream);
+
 /* Text of the last error on this context (never NULL; "" when none).  Valid until the next call. */
 const char *mfs_last_error(const mfs_ctx *ctx);
 

@@ -47,6 +47,7 @@ EXPORTED = [
     "mfs_pair_variant_info",
     "mfs_fp32_fma_rate",
     "mfs_matvec_transposed",
+    "mfs_selftest_bounded_wait",
     "mfs_dirichlet_apply",
     "mfs_dirichlet_matvec",
     "mfs_solve_capacitance",
@@ -167,6 +168,7 @@ def load_library(path: Optional[str] = None):
     lib.mfs_pair_variant_info.restype = ctypes.c_char_p
     lib.mfs_pair_variant.argtypes = [vp, i32]
     lib.mfs_fp32_fma_rate.argtypes = [i32, ctypes.POINTER(ctypes.c_double), vp]
+    lib.mfs_selftest_bounded_wait.argtypes = [i32, ctypes.c_int64, vp]
     lib.mfs_pair_variant.restype = ctypes.c_char_p
     lib.mfs_last_error.argtypes = [vp]
     lib.mfs_last_error.restype = ctypes.c_char_p
@@ -206,6 +208,15 @@ def fp32_fma_rate(packed: bool = True, stream=None) -> float:
     if rc != MFS_OK:
         raise MFSError(rc, "mfs_fp32_fma_rate failed")
     return out.value
+
+
+def selftest_bounded_wait(arrive: bool, limit: int = 1000, stream=None) -> int:
+    """Status of mfs_selftest_bounded_wait: MFS_OK (0) when the barrier phase is completed, else the
+    bounded wait gives up and the call returns MFS_ERR_DEVICE_TIMEOUT (7)."""
+    lib = load_library()
+    torch = _torch()
+    st = _stream_ptr(stream, torch.device("cuda", torch.cuda.current_device()))
+    return int(lib.mfs_selftest_bounded_wait(1 if arrive else 0, int(limit), st))
 
 
 def default_options(**kw) -> Options:

@@ -1375,3 +1375,47 @@ extern "C" mfs_status mfs_fp32_fma_rate(int32_t packed, double *tflops, void *st
     cudaFreeAsync(sink, st);
     return rc;
 }
+
+// ---------------------------------------------------------------------------
+// Self-test of the bounded device waits: a barrier phase that nothing completes
+// ---------------------------------------------------------------------------
+namespace mfs {
+namespace selftest {
+
+// One warp waits on phase 0 of a shared-memory mbarrier with the kernels' own bounded wait.  With
+// `arrive`, thread 0 completes the phase first (an arrival with no expected bytes) and the wait
+// succeeds; without, no thread ever arrives and every waiter gives up after `limit` polls and records
+// the timeout flag, exactly as a lost bulk copy would make a pair or tensor-core kernel do.
+__global__ void bounded_wait_kernel(int arrive, long long limit, int *err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (arrive && threadIdx.x == 0) mbar_arrive_expect_tx(&bar, 0);
+    __syncthreads();
+    mbar_wait_bounded(&bar, 0, err, limit);
+}
+
+}  // namespace selftest
+}  // namespace mfs
+
+extern "C" mfs_status mfs_selftest_bounded_wait(int32_t arrive, int64_t limit, void *stream) {
+    if ((arrive != 0 && arrive != 1) || limit < 1 || limit > (1ll << 24)) return MFS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int *err = nullptr;
+    if (cudaMallocAsync(&err, sizeof(int), st) != cudaSuccess) return MFS_ERR_OOM;
+    mfs_status rc = MFS_ERR_CUDA;
+    int h = -1;
+    if (cudaMemsetAsync(err, 0, sizeof(int), st) == cudaSuccess) {
+        mfs::selftest::bounded_wait_kernel<<<1, 32, 0, st>>>(arrive, (long long)limit, err);
+        if (cudaGetLastError() == cudaSuccess &&
+            cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+            cudaStreamSynchronize(st) == cudaSuccess)
+            rc = (h & MFS_DEVERR_TIMEOUT) ? MFS_ERR_DEVICE_TIMEOUT : (h == 0 ? MFS_OK : MFS_ERR_CUDA);
+    }
+    cudaFreeAsync(err, st);
+    cudaStreamSynchronize(st);
+    return rc;
+}
