@@ -80,6 +80,9 @@ def _args():
                     help="ellipsoid workloads: also solve on the N_v = 40 grid and report the difference")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="secondary workloads: also time the FP64 reference GPU solve (precision = 1)")
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 2, 3],
+                    help="mfs_options.precision of a secondary measurement (3: compensated double-FP32 pair "
+                         "sums); any value but 0 runs the named workload as a secondary line, not the benchmark")
     return ap.parse_args()
 
 
@@ -305,6 +308,8 @@ def secondary(args):
         if not idx:
             raise SystemExit(f"no pair-kernel variant named {args.pair_variant!r}")
         opts["pair_variant"] = idx[0]
+    if args.precision:
+        opts["precision"] = args.precision
     ctx = MFS.from_workload(wl, profile=1, **opts)
     setup_s = time.perf_counter() - t0
     laplace = wl.kind == "laplace"
@@ -361,7 +366,8 @@ def secondary(args):
         "warmup": args.warmup,
         "ms_per_step": solve_ms,
         "higher_is_better": True,
-        "dtype": "f32 pair sums, f64 GMRES",
+        "dtype": {0: "f32 pair sums, f64 GMRES", 2: "f32 pair sums, f64 one-body apply and GMRES",
+                  3: "compensated double-f32 pair sums, f64 one-body apply and GMRES"}[args.precision],
         "data": "synthetic",
         "config": {"workload": wl.description, "bodies": wl.num_bodies, "suspensions": wl.num_suspensions,
                    "nrhs": wl.nrhs, "gmres_tol": 1e-7, **opts},
@@ -437,7 +443,7 @@ def main():
     if args.impl == "gpu" and args.workload == "sphere100_resistance":
         resistance_two_way(args)
         return
-    if args.impl == "gpu" and args.workload != WORKLOAD:
+    if args.impl == "gpu" and (args.workload != WORKLOAD or args.precision != 0):
         secondary(args)
         return
     rank = int(os.environ.get("RANK", "0"))

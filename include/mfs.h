@@ -77,7 +77,13 @@ typedef struct {
     double eps_trunc;  /* singular values <= sigma_1 * eps_trunc are dropped (Eq. pseudo); default 0 */
     int32_t precision; /* 0: FP32 pair sums with compensated accumulation and FP32 one-body apply (default);
                           1: FP64 pair sums and FP64 one-body apply (reference GPU path);
-                          2: FP32 pair sums, FP64 one-body apply */
+                          2: FP32 pair sums, FP64 one-body apply;
+                          3: compensated double-FP32 pair sums (every pair term carried as hi + lo
+                             to about 2^-28 of its size, TwoSum accumulation) and FP64 one-body
+                             apply: matvec and pair sums near FP64 accuracy on any input, including
+                             rough gamma whose pseudo-inverse strengths are large and cancel, where
+                             FP32 pair sums lose about eps_32 * |lambda| / |y|.  The transposed sums and
+                             the evaluation at arbitrary points (mfs_evaluate*) stay FP32. */
     int32_t autotune;  /* 1: time pair-kernel variants on this geometry at setup (default 1) */
     int32_t max_rhs;   /* largest nrhs any later call will use (1..4); default 4 */
     int32_t profile;   /* 1: bracket every pair-kernel launch with CUDA events (no host sync) and report
@@ -209,15 +215,19 @@ mfs_status mfs_mobility_vjp(mfs_ctx *ctx, const double *dU, const double *dOmega
  *   u_i = sum_j (I + r r^T / r^2) lambda_j / (8 pi mu r),  r = x_i - y_j,  over ALL pairs.
  *
  * targets [num_targets][3], sources [num_sources][3], strengths [num_sources][3] and the output
- * u [num_targets][3] are FP64 DEVICE pointers owned by the caller.  Coordinates are used as FP32
- * in the pair loop (one body, no centre shift), so keep them O(1)-O(100) in magnitude; a target
- * on top of a source gives a non-finite result.
+ * u [num_targets][3] are FP64 DEVICE pointers owned by the caller.  Coordinates are taken relative
+ * to the first target in FP64 and then used as FP32 in the pair loop, so separations carry an
+ * absolute rounding of about 6e-8 times the extent of the point set, wherever the set sits; a
+ * target on top of a source gives a non-finite result.  If a bounded device wait inside the pair
+ * kernel gives up (the kernels' timeout path, which a healthy GPU never takes), every entry of u is
+ * set to NaN by the same call: the result is never assembled from another call's scratch.
  * Allocates nothing: its scratch (about 21 MB) is a fixed __device__ array inside libmfs that every
  * GPU which loads the library holds until the process exits.  Limits: num_targets and num_sources
  * at most MFS_NOALLOC_MAX_TARGETS / MFS_NOALLOC_MAX_SOURCES; larger sizes, NULL pointers or mu <= 0
  * return MFS_ERR_INVALID_ARG without launching anything.  All launches go on `stream`; the call
- * does not synchronise.  The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream capture.  Every call reuses
+ * does not synchronise.  The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) and the kernel's occupancy under a lock, so make that first call before any
+ * stream capture; several devices in one process each get their own copy of the array.  Every call reuses
  * the same array, which keeps the previous call's contents: calls whose GPU work overlaps (other
  * streams or other host threads) race and must be serialised by the caller.
  */

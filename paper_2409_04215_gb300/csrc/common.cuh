@@ -35,6 +35,11 @@ struct PairTile {
     int gA, gB;          // first and last CTA whose share meets this tile
 };
 
+// Compensated pair sums split body-local coordinates and centre differences at multiples of
+// 1/MFS_XGRID: the "high" parts of a target and a source then differ by an exactly representable
+// FP32 number, and its square is exact while it is shorter than 32 (11 significant bits).
+#define MFS_XGRID 64.0
+
 struct PairGeom {
     const float4 *tgt;         // [ntargets] body-local rotated target (x,y,z), w = body id (int bits)
     const float *src;          // [sum_Npad][REC] packed source records
@@ -43,6 +48,8 @@ struct PairGeom {
     const double *centres;     // [P][3]
     int ntargets;
     const float *tgt_w = nullptr;  // gradient kernel only: target strengths w, FP32 [nrhs][ntargets][3]
+    // compensated kernels only: body-local targets split as x = hi + lo, hi a multiple of 1/MFS_XGRID
+    const float4 *tgt_hi = nullptr, *tgt_lo = nullptr;  // [ntargets] (x, y, z, unused)
 };
 
 struct PairWork {

@@ -11,6 +11,7 @@ struct PairVariant {
     int D, nrhs, T, NT, tile_targets;
     int packed;  // 1: f32x2 Stokes policy with duplicated source records
     int grad;    // 1: centre-gradient kernel of the adjoint (not a pair sum)
+    int comp;    // 1: compensated double-FP32 arithmetic (precision = 3), records from pack_sources_comp
     const char *name;  // policy and template arguments, e.g. "PackedStokes<1,3,128>"
 };
 const PairVariant *pair_variants(int *count);
@@ -21,6 +22,9 @@ cudaError_t pair_epilogue(int D, int nrhs, const PairWork &work, const double *b
                           double *out, int ntargets, cudaStream_t st);
 cudaError_t pack_sources(int D, int nrhs, int packed, const float4 *src_pos, const int *src_pt_of_rec,
                          const double *strength, int nsrc, int nrec, float *records, cudaStream_t st);
+// Records of the compensated kernels from FP64 body-local positions [nsrc][3] and strengths.
+cudaError_t pack_sources_comp(int D, int nrhs, const double *src_local64, const int *src_pt_of_rec,
+                              const double *strength, int nsrc, int nrec, float *records, cudaStream_t st);
 
 // FP64 reference pair sum (precision = 1): one thread per target, direct loops; raw sums (no 1/(4pi) factor).
 cudaError_t pair_sum_fp64(int D, int nrhs, const double *tgt_local, const int *tgt_body, int ntargets,

@@ -116,6 +116,7 @@ struct mfs_ctx {
     float *rot_d = nullptr;
     int *shape_id_d = nullptr;
     float4 *tgt_pos_d = nullptr, *src_pos_d = nullptr;
+    float4 *tgt_hi_d = nullptr, *tgt_lo_d = nullptr;  // precision 3: grid-split body-local targets
     double *tgt_local64_d = nullptr, *src_local64_d = nullptr, *src_local4_d = nullptr;
     int *tgt_body_d = nullptr, *rec_pt_d = nullptr, *rec_off_d = nullptr, *tgt_off_d = nullptr,
         *src_off_d = nullptr, *susp_src_begin_d = nullptr, *susp_src_end_d = nullptr;
@@ -332,19 +333,34 @@ void gram6(const std::vector<double> &Y0, double *G) {
     }
 }
 
-int default_variant(int D, int nrhs) {
+int default_variant(int D, int nrhs, int comp = 0) {
     int count = 0;
     const PairVariant *v = pair_variants(&count);
     // preferred variant per kind and nrhs when not autotuned: packed f32x2 for Stokes, scalar for Laplace
     const int wantT = (D == 3) ? (nrhs == 1 ? 4 : 2) : 4;
     const int wantNT = 128, wantPacked = (D == 3 && nrhs != 3) ? 1 : 0;
+    if (!comp)
+        for (int i = 0; i < count; ++i)
+            if (!v[i].grad && !v[i].comp && v[i].D == D && v[i].nrhs == nrhs && v[i].T == wantT &&
+                v[i].NT == wantNT && v[i].packed == wantPacked)
+                return i;
     for (int i = 0; i < count; ++i)
-        if (!v[i].grad && v[i].D == D && v[i].nrhs == nrhs && v[i].T == wantT && v[i].NT == wantNT &&
-            v[i].packed == wantPacked)
-            return i;
-    for (int i = 0; i < count; ++i)
-        if (!v[i].grad && v[i].D == D && v[i].nrhs == nrhs) return i;
+        if (!v[i].grad && v[i].comp == comp && v[i].D == D && v[i].nrhs == nrhs) return i;
     return -1;
+}
+
+// The forward pair-sum variant of this context for nrhs: compensated kernels with precision = 3.
+int forward_variant(const mfs_ctx *ctx, int nrhs) {
+    const int tuned = ctx->best_variant[ctx->D == 3][nrhs];
+    return tuned >= 0 ? tuned : default_variant(ctx->D, nrhs, ctx->opt.precision == 3);
+}
+
+// An FP32 (not compensated) variant for the sums that have no compensated form (transposed sums,
+// evaluation at arbitrary points).
+int fp32_variant(const mfs_ctx *ctx, int D, int nrhs) {
+    if (ctx->opt.precision == 3) return default_variant(D, nrhs, 0);
+    const int tuned = ctx->best_variant[D == 3][nrhs];
+    return tuned >= 0 ? tuned : default_variant(D, nrhs, 0);
 }
 
 // Tiles and CTA shares for one pair-kernel variant.  transposed = 0: collocation targets, proxy
@@ -470,7 +486,20 @@ PairGeom geom_of(mfs_ctx *ctx) {
     g.blk_off = ctx->blk_off_d;
     g.centres = ctx->centres_d;
     g.ntargets = ctx->sumM;
+    g.tgt_hi = ctx->tgt_hi_d;
+    g.tgt_lo = ctx->tgt_lo_d;
     return g;
+}
+
+// Source records for `variant` from FP64 strengths [nrhs][sum_N][D].
+cudaError_t pack_for(mfs_ctx *ctx, int variant, const double *strength, int nrhs, cudaStream_t st) {
+    int vc = 0;
+    const PairVariant *vv = pair_variants(&vc);
+    if (vv[variant].comp)
+        return pack_sources_comp(ctx->D, nrhs, ctx->src_local64_d, ctx->rec_pt_d, strength, ctx->sumN, ctx->nrec,
+                                 ctx->rec_d, st);
+    return pack_sources(ctx->D, nrhs, vv[variant].packed, ctx->src_pos_d, ctx->rec_pt_d, strength, ctx->sumN,
+                        ctx->nrec, ctx->rec_d, st);
 }
 
 double kernel_scale(mfs_ctx *ctx) {
@@ -498,20 +527,14 @@ mfs_status pair_apply(mfs_ctx *ctx, const double *strength, double *out, const d
         ctx->pair_launches += 1;
         return MFS_OK;
     }
-    const int variant = ctx->best_variant[ctx->D == 3][nrhs] >= 0 ? ctx->best_variant[ctx->D == 3][nrhs]
-                                                                  : default_variant(ctx->D, nrhs);
+    const int variant = forward_variant(ctx, nrhs);
     if (variant < 0) {
         ctx->last_error = "no pair-kernel variant for this nrhs";
         return MFS_ERR_INVALID_ARG;
     }
     PairPlan *plan = nullptr;
     CKS(get_plan(ctx, variant, include_self, &plan));
-    {
-        int vc = 0;
-        const PairVariant *vv = pair_variants(&vc);
-        CK(pack_sources(ctx->D, nrhs, vv[variant].packed, ctx->src_pos_d, ctx->rec_pt_d, strength, ctx->sumN,
-                        ctx->nrec, ctx->rec_d, st));
-    }
+    CK(pack_for(ctx, variant, strength, nrhs, st));
     const PairWork w = work_of(*plan);
     ctx->launches += 2;
     if (w.total_units > 0) {
@@ -787,7 +810,7 @@ mfs_status ensure_transposed(mfs_ctx *ctx) {
 // z^(k') = sum_k S^(kk')^T w^(k) at the proxy points (the Stokeslet is symmetric and even in r),
 // self pairs included or not.  w: [nrhs][sum_M][3], z: [nrhs][sum_N][3], both FP64 on the device.
 mfs_status pair_apply_T(mfs_ctx *ctx, const double *w, double *z, int nrhs, int include_self, cudaStream_t st) {
-    const int variant = ctx->best_variant[1][nrhs] >= 0 ? ctx->best_variant[1][nrhs] : default_variant(3, nrhs);
+    const int variant = fp32_variant(ctx, 3, nrhs);
     int vc = 0;
     const PairVariant *vv = pair_variants(&vc);
     PairPlan *plan = nullptr;
@@ -1035,8 +1058,7 @@ const char *mfs_pair_variant_info(int32_t index, int32_t *d, int32_t *nrhs, int3
 
 const char *mfs_pair_variant(const mfs_ctx *ctx, int32_t nrhs) {
     if (!ctx || nrhs < 1 || nrhs > 4 || nrhs > ctx->opt.max_rhs) return "";
-    const int tuned = ctx->best_variant[ctx->D == 3][nrhs];
-    const int v = tuned >= 0 ? tuned : default_variant(ctx->D, nrhs);
+    const int v = forward_variant(ctx, nrhs);
     int count = 0;
     const PairVariant *vv = pair_variants(&count);
     return (v >= 0 && v < count) ? vv[v].name : "";
@@ -1412,6 +1434,23 @@ static mfs_status setup_impl(mfs_ctx *ctx, mfs_kind kind, const mfs_bodies *bodi
     CK(cudaMemcpy(ctx->rot_d, rot32.data(), sizeof(float) * 9 * P, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->shape_id_d, ctx->shape_id.data(), sizeof(int) * P, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->tgt_pos_d, tgt_pos.data(), sizeof(float4) * ctx->sumM, cudaMemcpyHostToDevice));
+    if (ctx->opt.precision == 3) {  // compensated pair sums: x = hi + lo, hi on the 1/MFS_XGRID grid
+        std::vector<float4> hi(ctx->sumM), lo(ctx->sumM);
+        for (int t = 0; t < ctx->sumM; ++t) {
+            float h[3], l[3];
+            for (int a = 0; a < 3; ++a) {
+                const double x = tgt64[3 * (size_t)t + a], xh = std::rint(x * MFS_XGRID) / MFS_XGRID;
+                h[a] = (float)xh;
+                l[a] = (float)(x - xh);
+            }
+            hi[t] = make_float4(h[0], h[1], h[2], 0.f);
+            lo[t] = make_float4(l[0], l[1], l[2], 0.f);
+        }
+        CK(ctx->alloc(&ctx->tgt_hi_d, ctx->sumM));
+        CK(ctx->alloc(&ctx->tgt_lo_d, ctx->sumM));
+        CK(cudaMemcpy(ctx->tgt_hi_d, hi.data(), sizeof(float4) * ctx->sumM, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->tgt_lo_d, lo.data(), sizeof(float4) * ctx->sumM, cudaMemcpyHostToDevice));
+    }
     CK(cudaMemcpy(ctx->src_pos_d, src_pos.data(), sizeof(float4) * ctx->sumN, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->tgt_local64_d, tgt64.data(), sizeof(double) * tgt64.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->src_local64_d, src64.data(), sizeof(double) * src64.size(), cudaMemcpyHostToDevice));
@@ -1447,7 +1486,8 @@ static mfs_status setup_impl(mfs_ctx *ctx, mfs_kind kind, const mfs_bodies *bodi
     if (status != MFS_OK) return status;
 
     // work buffers
-    const int recf = std::max(pair_record_floats(D, R, 0), D == 3 ? pair_record_floats(D, R, 1) : 0);
+    const int recf = std::max({pair_record_floats(D, R, 0), D == 3 ? pair_record_floats(D, R, 1) : 0,
+                               ctx->opt.precision == 3 ? pair_record_floats(D, R, 2) : 0});
     CK(ctx->alloc(&ctx->rec_d, (size_t)ctx->nrec * recf));
     CK(cudaMemset(ctx->rec_d, 0, sizeof(float) * (size_t)ctx->nrec * recf));
     CK(ctx->alloc(&ctx->lam_d, (size_t)R * ctx->sumN * D));
@@ -1492,7 +1532,7 @@ static mfs_status autotune(mfs_ctx *ctx, int nrhs, cudaStream_t st) {
         sample = nt_s > 0;
     }
     for (int i = 0; i < count; ++i) {
-        if (v[i].grad || v[i].D != ctx->D || v[i].nrhs != nrhs) continue;
+        if (v[i].grad || v[i].D != ctx->D || v[i].nrhs != nrhs || v[i].comp != (ctx->opt.precision == 3)) continue;
         if (pair_occupancy(i) <= 0) continue;
         PairPlan local;
         PairPlan *plan = &local;
@@ -1509,8 +1549,7 @@ static mfs_status autotune(mfs_ctx *ctx, int nrhs, cudaStream_t st) {
         } release{ctx, &local};
         const PairWork w = work_of(*plan);
         if (w.total_units == 0) return MFS_OK;
-        CK(pack_sources(ctx->D, nrhs, v[i].packed, ctx->src_pos_d, ctx->rec_pt_d, ctx->lam_d, ctx->sumN, ctx->nrec,
-                        ctx->rec_d, st));
+        CK(pack_for(ctx, i, ctx->lam_d, nrhs, st));
         float ms_best = 1e30f;
         for (int rep = 0; rep < 3; ++rep) {
             CK(cudaEventRecord(ctx->ev0, st));
@@ -1545,7 +1584,7 @@ mfs_status mfs_setup(mfs_ctx **out, mfs_kind kind, const mfs_bodies *bodies, int
     if (opt) ctx->opt = *opt; else mfs_default_options(&ctx->opt);
     if (ctx->opt.max_rhs < 1 || ctx->opt.max_rhs > 4 || ctx->opt.max_iter < 1 || ctx->opt.restart < 1 ||
         ctx->opt.restart > 1023 || !(ctx->opt.mu > 0.0) || !(ctx->opt.gmres_tol >= 0.0) ||
-        ctx->opt.precision < 0 || ctx->opt.precision > 2 || !(ctx->opt.eps_trunc >= 0.0)) {
+        ctx->opt.precision < 0 || ctx->opt.precision > 3 || !(ctx->opt.eps_trunc >= 0.0)) {
         g_setup_error = "mfs_setup: invalid options";
         return MFS_ERR_INVALID_ARG;
     }
@@ -1558,7 +1597,7 @@ mfs_status mfs_setup(mfs_ctx **out, mfs_kind kind, const mfs_bodies *bodies, int
         const PairVariant *vv = pair_variants(&count);
         const int pv = ctx->opt.pair_variant;
         if (pv >= count || vv[pv].grad || vv[pv].D != (kind == MFS_STOKES ? 3 : 1) ||
-            vv[pv].nrhs > ctx->opt.max_rhs) {
+            vv[pv].nrhs > ctx->opt.max_rhs || vv[pv].comp != (ctx->opt.precision == 3)) {
             g_setup_error = "mfs_setup: pair_variant is not a forward pair-sum variant of this kind";
             return MFS_ERR_INVALID_ARG;
         }
@@ -2270,8 +2309,7 @@ mfs_status mfs_evaluate(mfs_ctx *ctx, const double *points, const int32_t *owner
             combine_raw_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(raw_d, nullptr, 0.0, scale, sorted_d, n);
             CK(cudaGetLastError());
         } else {  // the FP32 pair kernel on the new targets, all pairs of the owner's suspension
-            const int variant = ctx->best_variant[D == 3][nrhs] >= 0 ? ctx->best_variant[D == 3][nrhs]
-                                                                   : default_variant(D, nrhs);
+            const int variant = fp32_variant(ctx, D, nrhs);
             if (variant < 0) {
                 ctx->last_error = "no pair-kernel variant for this nrhs";
                 return MFS_ERR_INVALID_ARG;

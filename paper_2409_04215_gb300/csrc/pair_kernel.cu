@@ -21,6 +21,8 @@
 //    pipe needs.  Source records then hold every value twice, so one 128-bit
 //    shared-memory load yields two ready operand pairs.
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 
 #include "../../include/mfs.h"
 #include "common.cuh"
@@ -138,7 +140,9 @@ __device__ __forceinline__ Stage make_stage(const PairTile *tiles, int ntiles, c
 // Hooks every policy has; the gradient policy overrides them (target strengths, source-side sums).
 struct PolicyBase {
     static constexpr int MINB = 1;  // minimum resident CTAs per SM requested from the compiler
-    __device__ __forceinline__ void load_extra(int, int, const PairGeom &) {}
+    static constexpr bool GRID_DC = false;  // true: centre differences split into grid hi + lo (compensated)
+    // idx: the target (a clamped duplicate when !valid: computed, never written)
+    __device__ __forceinline__ void load_extra(int, int, bool, const PairGeom &) {}
     __device__ __forceinline__ void source_side(int, bool, double *) {}
 };
 
@@ -163,7 +167,8 @@ struct Scalar : PolicyBase {
 #pragma unroll
             for (int c = 0; c < C; ++c) hi[j][c] = lo[j][c] = bsum[j][c] = 0.f;
     }
-    __device__ __forceinline__ void compute(const float *sb, int nrec, const float (*dc)[3], int kb0) {
+    __device__ __forceinline__ void compute(const float *sb, int nrec, const float (*dc)[3], const float (*)[3],
+                                            int kb0) {
         float3 xt[T];
 #pragma unroll
         for (int j = 0; j < T; ++j) {
@@ -278,7 +283,8 @@ struct PackedStokes : PolicyBase {
 #pragma unroll
             for (int c = 0; c < C; ++c) bsum[p][c] = 0ull;
     }
-    __device__ __forceinline__ void compute(const float *sb, int nrec, const float (*dc)[3], int kb0) {
+    __device__ __forceinline__ void compute(const float *sb, int nrec, const float (*dc)[3], const float (*)[3],
+                                            int kb0) {
         u64 xt[TP][3];
 #pragma unroll
         for (int p = 0; p < TP; ++p) {
@@ -389,7 +395,8 @@ struct PackedStokesReg : PolicyBase {
 #pragma unroll
             for (int c = 0; c < C; ++c) bsum[p][c] = 0ull;
     }
-    __device__ __forceinline__ void compute(const float *sb, int nrec, const float (*dc)[3], int kb0) {
+    __device__ __forceinline__ void compute(const float *sb, int nrec, const float (*dc)[3], const float (*)[3],
+                                            int kb0) {
         u64 xt[TP][3];
 #pragma unroll
         for (int p = 0; p < TP; ++p) {
@@ -499,7 +506,8 @@ struct PackedLaplaceReg : PolicyBase {
 #pragma unroll
             for (int c = 0; c < C; ++c) bsum[p][c] = 0ull;
     }
-    __device__ __forceinline__ void compute(const float *sb, int nrec, const float (*dc)[3], int kb0) {
+    __device__ __forceinline__ void compute(const float *sb, int nrec, const float (*dc)[3], const float (*)[3],
+                                            int kb0) {
         u64 xt[TP][3];
 #pragma unroll
         for (int p = 0; p < TP; ++p) {
@@ -592,12 +600,12 @@ struct GradStokes : PolicyBase {
         tp[j] = make_float3(p.x, p.y, p.z);
         tb[j] = __float_as_int(p.w);
     }
-    __device__ __forceinline__ void load_extra(int j, int idx, const PairGeom &geo) {
+    __device__ __forceinline__ void load_extra(int j, int idx, bool valid, const PairGeom &geo) {
 #pragma unroll
         for (int h = 0; h < NRHS; ++h)
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-                w[j][3 * h + c] = idx >= 0 ? geo.tgt_w[((size_t)h * geo.ntargets + idx) * 3 + c] : 0.f;
+                w[j][3 * h + c] = valid ? geo.tgt_w[((size_t)h * geo.ntargets + idx) * 3 + c] : 0.f;
     }
     __device__ __forceinline__ void reset() {
 #pragma unroll
@@ -605,7 +613,8 @@ struct GradStokes : PolicyBase {
 #pragma unroll
             for (int c = 0; c < 3; ++c) hi[j][c] = lo[j][c] = bsum[j][c] = 0.f;
     }
-    __device__ __forceinline__ void compute(const float *sb, int nrec, const float (*dc)[3], int kb0) {
+    __device__ __forceinline__ void compute(const float *sb, int nrec, const float (*dc)[3], const float (*)[3],
+                                            int kb0) {
         float3 xt[T];
 #pragma unroll
         for (int j = 0; j < T; ++j) {
@@ -699,6 +708,185 @@ struct GradStokes : PolicyBase {
 };
 
 // ---------------------------------------------------------------------------
+// Compensated (double-FP32) pair sums: every pair term is carried as an unevaluated FP32 sum
+// hi + lo, accurate to about 2^-28 of its size instead of FP32's 2^-24, and summed per target with
+// TwoSum.  The FP32 policies above lose about eps_32 |G| |lambda| per pair; when the strengths are
+// large and their fields cancel (the pseudo-inverse applied to a rough gamma, Eq. pseudo), that
+// rounding noise is larger than 1e-6 of the result.  Exactness is arranged, not emulated:
+//  * r = a + e: the body-local coordinates and the centre difference are split at multiples of
+//    1/MFS_XGRID, so a = (dc_hi + x_hi) - y_hi is exact and |a|^2 is exact for |a| < 32;
+//  * lambda = L + l with L an 11-bit block-floating value (one exponent per source), so a . L is
+//    exact (three products of 11-bit integers on one scale) for |a| < 32;
+//  * 1/r from the MUFU estimate y0 and the exactly computed residual h = 1 - r^2 y0^2 (one Newton
+//    step carried in the low part);
+//  * products and sums that feed the high part are split exactly (FMA product error, TwoSum).
+// The intrinsics __fmul_rn / __fadd_rn keep the compiler from contracting the error-free
+// transformations into FMAs.  Beyond |a| = 32 the squares and dot products round once (FP32
+// accuracy for far pairs, whose terms are smaller by 1/r).
+// Record: [y_hi(3) y_lo(3)] then per right-hand side Stokes [L(3) l(3) lambda_f32(3)], Laplace
+// [lambda_hi lambda_lo].
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void df_two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (hi, lo) += (th, tl)
+__device__ __forceinline__ void df_acc(float &hi, float &lo, float th, float tl) {
+    float s, e;
+    df_two_sum(hi, th, s, e);
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(e, tl));
+}
+
+template <int D, int NRHS>
+__host__ __device__ constexpr int comp_rec_floats() {
+    return (6 + (D == 3 ? 9 : 2) * NRHS + 3) / 4 * 4;
+}
+
+template <int D, int NRHS, int T, int NT>
+struct Comp : PolicyBase {
+    static constexpr int DIM = D;
+    static constexpr int C = D * NRHS;
+    static constexpr int REC = comp_rec_floats<D, NRHS>();
+    static constexpr int TPT = T;
+    static constexpr int PSM = 0;
+    static constexpr bool GRID_DC = true;
+    float xh[T][3], xl[T][3];
+    int tb[T];
+    float Sh[T][C], Sl[T][C];  // finished source bodies (self left out)
+    float Bh[T][C], Bl[T][C];  // the current source body
+
+    __device__ __forceinline__ void init(float *, int) {}
+    __device__ __forceinline__ void set_target(int j, float4 p) { tb[j] = __float_as_int(p.w); }
+    __device__ __forceinline__ void load_extra(int j, int idx, bool, const PairGeom &geo) {
+        const float4 h = geo.tgt_hi[idx], l = geo.tgt_lo[idx];
+        xh[j][0] = h.x;
+        xh[j][1] = h.y;
+        xh[j][2] = h.z;
+        xl[j][0] = l.x;
+        xl[j][1] = l.y;
+        xl[j][2] = l.z;
+    }
+    __device__ __forceinline__ void reset() {
+#pragma unroll
+        for (int j = 0; j < T; ++j)
+#pragma unroll
+            for (int c = 0; c < C; ++c) Sh[j][c] = Sl[j][c] = Bh[j][c] = Bl[j][c] = 0.f;
+    }
+    __device__ __forceinline__ void compute(const float *sb, int nrec, const float (*dch)[3], const float (*dcl)[3],
+                                            int kb0) {
+        float th_[T][3], tl_[T][3];  // target relative to the source body's centre, hi (exact) + lo
+#pragma unroll
+        for (int j = 0; j < T; ++j) {
+            const int r = tb[j] - kb0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                th_[j][c] = __fadd_rn(dch[r][c], xh[j][c]);
+                tl_[j][c] = __fadd_rn(dcl[r][c], xl[j][c]);
+            }
+        }
+#pragma unroll 1
+        for (int s = 0; s < nrec; ++s) {
+            float rec[REC];
+#pragma unroll
+            for (int v = 0; v < REC / 4; ++v) {
+                const float4 f = reinterpret_cast<const float4 *>(sb + s * REC)[v];
+                rec[4 * v + 0] = f.x;
+                rec[4 * v + 1] = f.y;
+                rec[4 * v + 2] = f.z;
+                rec[4 * v + 3] = f.w;
+            }
+#pragma unroll
+            for (int j = 0; j < T; ++j) {
+                float a[3], e[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    a[c] = __fsub_rn(th_[j][c], rec[c]);      // exact (grid)
+                    e[c] = __fsub_rn(tl_[j][c], rec[3 + c]);  // small
+                }
+                // r^2 = A + B: A = |a|^2 exact, B = e . (2a + e)
+                const float A = __fmaf_rn(a[0], a[0], __fmaf_rn(a[1], a[1], __fmul_rn(a[2], a[2])));
+                const float w0 = __fmaf_rn(2.f, a[0], e[0]), w1 = __fmaf_rn(2.f, a[1], e[1]),
+                            w2 = __fmaf_rn(2.f, a[2], e[2]);
+                const float B = __fmaf_rn(e[0], w0, __fmaf_rn(e[1], w1, __fmul_rn(e[2], w2)));
+                const float r2h = __fadd_rn(A, B);
+                const float r2l = __fadd_rn(__fsub_rn(A, r2h), B);
+                // 1/r = y0 (1 + h/2), 1/r^2 = (q + qe)(1 + h), h = 1 - r^2 y0^2 computed exactly to first order
+                const float y0 = rsqrt_ftz(r2h);
+                const float q = __fmul_rn(y0, y0);
+                const float qe = __fmaf_rn(y0, y0, -q);
+                const float Pp = __fmul_rn(r2h, q);
+                const float Pe = __fmaf_rn(r2h, q, -Pp);
+                float h = __fsub_rn(__fsub_rn(1.f, Pp), Pe);
+                h = __fmaf_rn(-r2h, qe, h);
+                h = __fmaf_rn(-r2l, q, h);
+                const float ril = __fmul_rn(__fmul_rn(0.5f, y0), h);
+#pragma unroll
+                for (int rh = 0; rh < NRHS; ++rh) {
+                    if constexpr (D == 3) {
+                        const float *L = rec + 6 + 9 * rh, *l = L + 3, *M = L + 6;
+                        // r . lambda = (a . L) [exact] + (a . l + e . lambda)
+                        const float doth = __fmaf_rn(a[0], L[0], __fmaf_rn(a[1], L[1], __fmul_rn(a[2], L[2])));
+                        const float dotl = __fmaf_rn(
+                            a[0], l[0],
+                            __fmaf_rn(a[1], l[1],
+                                      __fmaf_rn(a[2], l[2],
+                                                __fmaf_rn(e[0], M[0], __fmaf_rn(e[1], M[1], __fmul_rn(e[2], M[2]))))));
+                        // s = (r . lambda) / r^2 = sch + scl
+                        const float sch = __fmul_rn(q, doth);
+                        float scl = __fmaf_rn(q, doth, -sch);
+                        scl = __fmaf_rn(q, __fmaf_rn(h, doth, dotl), scl);
+                        scl = __fmaf_rn(qe, doth, scl);
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            // v = lambda + s r, then the term v / r
+                            const float p = __fmul_rn(sch, a[c]);
+                            const float pe = __fmaf_rn(sch, a[c], -p);
+                            float vh, err;
+                            df_two_sum(L[c], p, vh, err);
+                            float vl = __fmaf_rn(sch, e[c], l[c]);
+                            vl = __fmaf_rn(scl, a[c], vl);
+                            vl = __fmaf_rn(scl, e[c], vl);
+                            vl = __fadd_rn(__fadd_rn(vl, pe), err);
+                            const float tH = __fmul_rn(y0, vh);
+                            const float tE = __fmaf_rn(y0, vh, -tH);
+                            const float tL = __fmaf_rn(y0, vl, __fmaf_rn(ril, vh, tE));
+                            df_acc(Bh[j][3 * rh + c], Bl[j][3 * rh + c], tH, tL);
+                        }
+                    } else {
+                        const float lh = rec[6 + 2 * rh], ll = rec[7 + 2 * rh];
+                        const float tH = __fmul_rn(lh, y0);
+                        const float tE = __fmaf_rn(lh, y0, -tH);
+                        const float tL = __fmaf_rn(ll, y0, __fmaf_rn(lh, ril, tE));
+                        df_acc(Bh[j][rh], Bl[j][rh], tH, tL);
+                    }
+                }
+            }
+        }
+    }
+    __device__ __forceinline__ void end_body(int body, bool include_self) {
+#pragma unroll
+        for (int j = 0; j < T; ++j) {
+            const bool keep = include_self || (tb[j] != body);
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                if (keep) df_acc(Sh[j][c], Sl[j][c], Bh[j][c], Bl[j][c]);
+                Bh[j][c] = Bl[j][c] = 0.f;
+            }
+        }
+    }
+    __device__ __forceinline__ float result(int j, int c, float &l) const {
+        l = Sl[j][c];
+        return Sh[j][c];
+    }
+};
+template <int NRHS, int T, int NT>
+using CompStokes = Comp<3, NRHS, T, NT>;
+template <int NRHS, int T, int NT>
+using CompLaplace = Comp<1, NRHS, T, NT>;
+
+// ---------------------------------------------------------------------------
 // The persistent stream-K kernel
 // ---------------------------------------------------------------------------
 template <class Pol, int NT>
@@ -731,12 +919,14 @@ struct PackedStokesB5 : PackedStokes<NRHS, TP, NT> {
     static constexpr int MINB = 5;
 };
 
+
 template <class Pol, int NT, int MINB = Pol::MINB>
 __global__ void __launch_bounds__(NT, MINB) pair_sum_kernel(PairGeom geo, PairWork work, int *err) {
     using Cfg = StageCfg<Pol, NT>;
     constexpr int REC = Cfg::REC, SREC = Cfg::STAGE_REC, C = Pol::C, TPT = Pol::TPT;
     extern __shared__ __align__(128) float smem[];
     __shared__ float dcs[2][MFS_MAX_TILE_BODIES][3];
+    __shared__ float dcl[Pol::GRID_DC ? 2 : 1][Pol::GRID_DC ? MFS_MAX_TILE_BODIES : 1][3];
     __shared__ __align__(8) uint64_t bars[2];
 
     const int g = blockIdx.x;
@@ -773,7 +963,7 @@ __global__ void __launch_bounds__(NT, MINB) pair_sum_kernel(PairGeom geo, PairWo
             const bool in_tile = idx < t_.t1;
             if (!in_tile) idx = t_.t1 - 1;  // a clamped duplicate: computed, never written
             pol.set_target(j, geo.tgt[idx]);
-            pol.load_extra(j, in_tile ? idx : -1, geo);
+            pol.load_extra(j, idx, in_tile, geo);
         }
         pol.reset();
     };
@@ -802,7 +992,14 @@ __global__ void __launch_bounds__(NT, MINB) pair_sum_kernel(PairGeom geo, PairWo
         // centre offsets of the tile's target bodies relative to this stage's source body
         for (int q = tid; q < tl.nb * 3; q += NT) {  // up to MFS_MAX_TILE_BODIES * 3 entries, NT may be fewer
             const int kb = tl.kb0 + q / 3, c = q % 3;
-            dcs[buf][q / 3][c] = (float)(geo.centres[kb * 3 + c] - geo.centres[cur.body * 3 + c]);
+            const double d = geo.centres[kb * 3 + c] - geo.centres[cur.body * 3 + c];
+            if constexpr (Pol::GRID_DC) {  // d = hi + lo with hi on the coordinate grid (exact in FP32)
+                const double dh = rint(d * MFS_XGRID) / MFS_XGRID;
+                dcs[buf][q / 3][c] = (float)dh;
+                dcl[buf][q / 3][c] = (float)(d - dh);
+            } else {
+                dcs[buf][q / 3][c] = (float)d;
+            }
         }
         const bool ok = mbar_wait_bounded(&bars[buf], (uint32_t)((si >> 1) & 1), err, wait_limit);
         if (__syncthreads_or(!ok)) {
@@ -811,7 +1008,7 @@ __global__ void __launch_bounds__(NT, MINB) pair_sum_kernel(PairGeom geo, PairWo
             return;
         }
 
-        pol.compute(smem + buf * SREC * REC, cur.nrec, dcs[buf], tl.kb0);
+        pol.compute(smem + buf * SREC * REC, cur.nrec, dcs[buf], dcl[Pol::GRID_DC ? buf : 0], tl.kb0);
 
         // end of a source body (for this tile): fold into (hi, lo), leaving self pairs out
         if ((nxt.tile < 0) || nxt.tile != cur.tile || nxt.body != cur.body) {
@@ -952,6 +1149,63 @@ __global__ void pack_sources_kernel(const float4 *src_pos, const int *src_pt_of_
     for (int q = 0; q < REC / 4; ++q) o[q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
 }
 
+// Records of the compensated policies (layout above) from FP64 body-local positions and strengths.
+// The block-floating part L of a Stokeslet strength keeps 11 significant bits on the scale of its
+// largest component; l = lambda - L is rounded to FP32 (relative 2^-24 of a number below 2^-11 of
+// lambda).  Padding records (rec_pt = -1) are all zero: the body centre with zero strength.
+template <int D, int NRHS>
+__global__ void pack_sources_comp_kernel(const double *src_local64, const int *src_pt_of_rec, const double *strength,
+                                         int nsrc, int nrec, float *records) {
+    constexpr int REC = comp_rec_floats<D, NRHS>();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrec) return;
+    float r[REC];
+#pragma unroll
+    for (int c = 0; c < REC; ++c) r[c] = 0.f;
+    const int p = src_pt_of_rec[i];
+    if (p >= 0) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double y = src_local64[3 * (size_t)p + c];
+            const double yh = rint(y * MFS_XGRID) / MFS_XGRID;
+            r[c] = (float)yh;
+            r[3 + c] = (float)(y - yh);
+        }
+#pragma unroll
+        for (int h = 0; h < NRHS; ++h) {
+            if (D == 3) {
+                double lam[3], m = 0.0;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    lam[c] = strength[((size_t)h * nsrc + p) * 3 + c];
+                    m = fmax(m, fabs(lam[c]));
+                }
+                double unit = 0.0;
+                if (m > 0.0) {
+                    int ex = 0;
+                    frexp(m, &ex);  // m < 2^ex
+                    unit = ldexp(1.0, ex - 11);
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const double L = unit > 0.0 ? rint(lam[c] / unit) * unit : 0.0;
+                    r[6 + 9 * h + c] = (float)L;
+                    r[9 + 9 * h + c] = (float)(lam[c] - L);
+                    r[12 + 9 * h + c] = (float)lam[c];
+                }
+            } else {
+                const double lam = strength[(size_t)h * nsrc + p];
+                const float lh = (float)lam;
+                r[6 + 2 * h] = lh;
+                r[7 + 2 * h] = (float)(lam - (double)lh);
+            }
+        }
+    }
+    float4 *o = reinterpret_cast<float4 *>(records + (size_t)i * REC);
+#pragma unroll
+    for (int q = 0; q < REC / 4; ++q) o[q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+}
+
 // ---------------------------------------------------------------------------
 // Host side: variant table
 // ---------------------------------------------------------------------------
@@ -959,11 +1213,16 @@ template <class Pol, int NT, int MINB = Pol::MINB>
 static cudaError_t launch_variant(const PairGeom &geo, const PairWork &work, int *err, cudaStream_t st) {
     using Cfg = StageCfg<Pol, NT>;
     auto kern = pair_sum_kernel<Pol, NT, MINB>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+    // the shared-memory limit is a per-device function attribute: set once on each device
+    static std::atomic<unsigned long long> attr_devices{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+    if (!bit || !(attr_devices.load() & bit)) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_devices.fetch_or(bit);
     }
     kern<<<work.G, NT, Cfg::SMEM, st>>>(geo, work, err);
     return cudaGetLastError();
@@ -981,8 +1240,8 @@ static int occupancy_variant() {
 
 // Scalar S(D, nrhs, targets per thread, threads); packed Stokes P(nrhs, target pairs per thread, threads)
 // Scalar S(D, nrhs, T, NT); packed Stokes P(policy, nrhs, target pairs per thread, NT);
-// centre-gradient G(nrhs, T, NT) for the adjoint
-#define MFS_VARIANTS(S, P, G)  \
+// centre-gradient G(nrhs, T, NT) for the adjoint; compensated X(policy, nrhs, T, NT) (precision = 3)
+#define MFS_VARIANTS(S, P, G, X)  \
     S(3, 1, 4, 128)         \
     S(3, 1, 2, 128)         \
     S(3, 1, 4, 256)         \
@@ -1033,17 +1292,31 @@ static int occupancy_variant() {
     G(1, 4, 128)                  \
     G(2, 2, 128)                  \
     G(3, 2, 128)                  \
-    G(4, 2, 128)
+    G(4, 2, 128)                  \
+    X(CompStokes, 1, 2, 128)      \
+    X(CompStokes, 1, 4, 128)      \
+    X(CompStokes, 1, 2, 256)      \
+    X(CompStokes, 2, 2, 128)      \
+    X(CompStokes, 3, 2, 128)      \
+    X(CompStokes, 4, 1, 128)      \
+    X(CompLaplace, 1, 4, 128)     \
+    X(CompLaplace, 1, 2, 128)     \
+    X(CompLaplace, 2, 2, 128)     \
+    X(CompLaplace, 3, 2, 128)     \
+    X(CompLaplace, 4, 2, 128)
 
 static const PairVariant kVariants[] = {
-#define S(D_, R_, T_, N_) {D_, R_, T_, N_, N_ * T_, 0, 0, "Scalar<" #D_ "," #R_ "," #T_ "," #N_ ">"},
+#define S(D_, R_, T_, N_) {D_, R_, T_, N_, N_ * T_, 0, 0, 0, "Scalar<" #D_ "," #R_ "," #T_ "," #N_ ">"},
 #define P(POL_, R_, TP_, N_) \
-    {POL_<R_, TP_, N_>::D, R_, 2 * TP_, N_, N_ * 2 * TP_, 1, 0, #POL_ "<" #R_ "," #TP_ "," #N_ ">"},
-#define G(R_, T_, N_) {3, R_, T_, N_, N_ * T_, 0, 1, "GradStokes<" #R_ "," #T_ "," #N_ ">"},
-    MFS_VARIANTS(S, P, G)
+    {POL_<R_, TP_, N_>::D, R_, 2 * TP_, N_, N_ * 2 * TP_, 1, 0, 0, #POL_ "<" #R_ "," #TP_ "," #N_ ">"},
+#define G(R_, T_, N_) {3, R_, T_, N_, N_ * T_, 0, 1, 0, "GradStokes<" #R_ "," #T_ "," #N_ ">"},
+#define X(POL_, R_, T_, N_) \
+    {POL_<R_, T_, N_>::DIM, R_, T_, N_, N_ * T_, 0, 0, 1, #POL_ "<" #R_ "," #T_ "," #N_ ">"},
+    MFS_VARIANTS(S, P, G, X)
 #undef S
 #undef P
 #undef G
+#undef X
 };
 
 const PairVariant *pair_variants(int *count) {
@@ -1051,7 +1324,10 @@ const PairVariant *pair_variants(int *count) {
     return kVariants;
 }
 
-int pair_record_floats(int D, int nrhs, int packed) { return rec_floats(D, nrhs, packed != 0); }
+int pair_record_floats(int D, int nrhs, int packed) {
+    if (packed == 2) return D == 3 ? (6 + 9 * nrhs + 3) / 4 * 4 : (6 + 2 * nrhs + 3) / 4 * 4;  // compensated
+    return rec_floats(D, nrhs, packed != 0);
+}
 
 int pair_occupancy(int vi) {
     int i = 0;
@@ -1061,10 +1337,13 @@ int pair_occupancy(int vi) {
     if (vi == i++) return occupancy_variant<POL_<R_, TP_, N_>, N_>();
 #define G(R_, T_, N_) \
     if (vi == i++) return occupancy_variant<GradStokes<R_, T_, N_>, N_>();
-    MFS_VARIANTS(S, P, G)
+#define X(POL_, R_, T_, N_) \
+    if (vi == i++) return occupancy_variant<POL_<R_, T_, N_>, N_>();
+    MFS_VARIANTS(S, P, G, X)
 #undef S
 #undef P
 #undef G
+#undef X
     return 0;
 }
 
@@ -1076,10 +1355,13 @@ cudaError_t pair_launch(int vi, const PairGeom &geo, const PairWork &work, int *
     if (vi == i++) return launch_variant<POL_<R_, TP_, N_>, N_>(geo, work, err, st);
 #define G(R_, T_, N_) \
     if (vi == i++) return launch_variant<GradStokes<R_, T_, N_>, N_>(geo, work, err, st);
-    MFS_VARIANTS(S, P, G)
+#define X(POL_, R_, T_, N_) \
+    if (vi == i++) return launch_variant<POL_<R_, T_, N_>, N_>(geo, work, err, st);
+    MFS_VARIANTS(S, P, G, X)
 #undef S
 #undef P
 #undef G
+#undef X
     return cudaErrorInvalidValue;
 }
 
@@ -1115,6 +1397,21 @@ cudaError_t pack_sources(int D, int nrhs, int packed, const float4 *src_pos, con
     return cudaErrorInvalidValue;
 }
 
+cudaError_t pack_sources_comp(int D, int nrhs, const double *src_local64, const int *src_pt_of_rec,
+                              const double *strength, int nsrc, int nrec, float *records, cudaStream_t st) {
+    const int threads = 256, blocks = (nrec + threads - 1) / threads;
+    if (nrec == 0) return cudaSuccess;
+#define PK(D_, R_)                                                                                               \
+    if (D == D_ && nrhs == R_) {                                                                                 \
+        pack_sources_comp_kernel<D_, R_><<<blocks, threads, 0, st>>>(src_local64, src_pt_of_rec, strength, nsrc, \
+                                                                     nrec, records);                             \
+        return cudaGetLastError();                                                                               \
+    }
+    PK(3, 1) PK(3, 2) PK(3, 3) PK(3, 4) PK(1, 1) PK(1, 2) PK(1, 3) PK(1, 4)
+#undef PK
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace mfs
 
 // ===========================================================================
@@ -1126,6 +1423,9 @@ cudaError_t pack_sources(int D, int nrhs, int packed, const float4 *src_pos, con
 // scratch lives in one file-scope __device__ array of fixed size, reserved when the
 // library is loaded.  The array is shared by all calls and keeps the last call's contents,
 // so calls whose GPU work overlaps (different streams, or different host threads) race.
+// A bounded device wait that gives up inside the pair kernel (the error path of every bulk copy)
+// leaves the scratch partly written; the call then fills u with NaN instead of returning a sum
+// built from stale scratch, and the caller sees the failure without a synchronising query.
 // ===========================================================================
 namespace mfs {
 namespace noalloc {
@@ -1160,9 +1460,10 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[mfs::noalloc::k
 namespace mfs {
 namespace noalloc {
 
-// Targets -> float4 (absolute coordinates, one body), sources -> duplicated FP32 records, the
-// tile list of the stream-K split and the single-body offsets; every scratch word the pair
-// kernel and the epilogue read is written here first.
+// Targets -> float4, sources -> duplicated FP32 records, the tile list of the stream-K split and
+// the single-body offsets; every scratch word the pair kernel and the epilogue read is written here
+// first.  Coordinates are taken relative to the first target in FP64 before the FP32 cast (the sum
+// is translation invariant), so the FP32 separations keep their precision wherever the points sit.
 __global__ void prep_kernel(const double *targets, int nt, const double *sources, const double *lam, int ns,
                             int nrec, int ntiles, long long nblk, int G, unsigned char *base) {
     float4 *tgt = reinterpret_cast<float4 *>(base + oTgt);
@@ -1172,13 +1473,16 @@ __global__ void prep_kernel(const double *targets, int nt, const double *sources
     const long long W = (long long)ntiles * nblk;
     const int stride = gridDim.x * blockDim.x;
     const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const double o0 = targets[0], o1 = targets[1], o2 = targets[2];  // nt >= 1
     for (int i = i0; i < nt; i += stride)
-        tgt[i] = make_float4((float)targets[3 * (size_t)i], (float)targets[3 * (size_t)i + 1],
-                             (float)targets[3 * (size_t)i + 2], __int_as_float(0));
+        tgt[i] = make_float4((float)(targets[3 * (size_t)i] - o0), (float)(targets[3 * (size_t)i + 1] - o1),
+                             (float)(targets[3 * (size_t)i + 2] - o2), __int_as_float(0));
     for (int r = i0; r < nrec; r += stride) {
         float v[6];
         if (r < ns) {
-            for (int c = 0; c < 3; ++c) v[c] = (float)sources[3 * (size_t)r + c];
+            v[0] = (float)(sources[3 * (size_t)r] - o0);
+            v[1] = (float)(sources[3 * (size_t)r + 1] - o1);
+            v[2] = (float)(sources[3 * (size_t)r + 2] - o2);
             for (int c = 0; c < 3; ++c) v[3 + c] = (float)lam[3 * (size_t)r + c];
         } else {  // padding: far away, zero strength -> exactly zero contribution
             v[0] = v[1] = v[2] = 1e15f;
@@ -1212,9 +1516,21 @@ __global__ void prep_kernel(const double *targets, int nt, const double *sources
     }
 }
 
+// u = NaN everywhere when a bounded wait of the pair kernel gave up (err set): the scratch the
+// epilogue read was then only partly written by this call.
+__global__ void poison_on_timeout_kernel(const int *err, double *u, size_t n) {
+    if (*err == 0) return;
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        u[i] = nan;
+}
+
+// Per device: the array's device address and the kernel's resident CTAs per SM, looked up on the
+// first call on that device under a lock (several host threads may make their first calls at once).
 struct DeviceScratch {
+    std::mutex mu;
     void *ptr[64] = {};
-    int occupancy = 0;
+    int occupancy[64] = {};
 };
 static DeviceScratch g_dev;
 
@@ -1233,31 +1549,38 @@ extern "C" mfs_status mfs_stokeslet_sum_noalloc(const double *targets, int32_t n
     cudaStream_t st = (cudaStream_t)stream;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MFS_ERR_CUDA;
-    if (!g_dev.ptr[dev]) {  // first call on this device: the array's device address
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return MFS_ERR_CUDA;
-        g_dev.ptr[dev] = p;
+    unsigned char *base = nullptr;
+    int occupancy = 0;
+    {
+        std::lock_guard<std::mutex> lock(g_dev.mu);
+        if (!g_dev.ptr[dev]) {  // first call on this device: the array's device address
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return MFS_ERR_CUDA;
+            g_dev.ptr[dev] = p;
+        }
+        if (g_dev.occupancy[dev] == 0) {
+            int occ = 0;
+            auto kern = pair_sum_kernel<Pol, NT>;
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, StageCfg<Pol, NT>::SMEM) !=
+                    cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, StageCfg<Pol, NT>::SMEM) !=
+                    cudaSuccess ||
+                occ <= 0)
+                return MFS_ERR_CUDA;
+            g_dev.occupancy[dev] = occ;
+        }
+        base = static_cast<unsigned char *>(g_dev.ptr[dev]);
+        occupancy = g_dev.occupancy[dev];
     }
-    unsigned char *base = static_cast<unsigned char *>(g_dev.ptr[dev]);
     if (num_sources == 0) return cudaMemsetAsync(u, 0, sizeof(double) * 3 * (size_t)num_targets, st) == cudaSuccess
                                      ? MFS_OK : MFS_ERR_CUDA;
-    if (g_dev.occupancy == 0) {
-        int occ = 0;
-        auto kern = pair_sum_kernel<Pol, NT>;
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, StageCfg<Pol, NT>::SMEM) !=
-                cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, StageCfg<Pol, NT>::SMEM) != cudaSuccess ||
-            occ <= 0)
-            return MFS_ERR_CUDA;
-        g_dev.occupancy = occ;
-    }
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MFS_ERR_CUDA;
     const int nrec = (num_sources + 3) / 4 * 4;
     const long long nblk = (nrec + MFS_BS - 1) / MFS_BS;
     const int ntiles = (num_targets + TT - 1) / TT;
     const long long W = (long long)ntiles * nblk;
-    long long G = std::min<long long>((long long)g_dev.occupancy * sms, kMaxCTAs);
+    long long G = std::min<long long>((long long)occupancy * sms, kMaxCTAs);
     if (G > W) G = W;
     prep_kernel<<<256, 256, 0, st>>>(targets, num_targets, sources, strengths, num_sources, nrec, ntiles, nblk,
                                      (int)G, base);
@@ -1282,6 +1605,7 @@ extern "C" mfs_status mfs_stokeslet_sum_noalloc(const double *targets, int32_t n
     if (launch_variant<Pol, NT>(geo, work, &meta->err, st) != cudaSuccess) return MFS_ERR_CUDA;
     pair_epilogue_kernel<3, 1><<<ntiles, 1024, 0, st>>>(work, nullptr, 0.0, 1.0 / (8.0 * MFS_PI * mu), u,
                                                        num_targets);
+    poison_on_timeout_kernel<<<sms, 256, 0, st>>>(&meta->err, u, 3 * (size_t)num_targets);
     return cudaGetLastError() == cudaSuccess ? MFS_OK : MFS_ERR_CUDA;
 }
 
