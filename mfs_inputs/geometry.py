@@ -157,6 +157,147 @@ def grow_cluster(
     return centres
 
 
+def quaternion_rotations(quats: np.ndarray) -> np.ndarray:
+    """Rotation matrices (count, 3, 3) of unit quaternions (w, x, y, z)."""
+    q = np.asarray(quats, dtype=np.float64)
+    q = q / np.linalg.norm(q, axis=1, keepdims=True)
+    w, x, y, z = q[:, 0], q[:, 1], q[:, 2], q[:, 3]
+    return np.stack([
+        np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], -1),
+        np.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], -1),
+        np.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1),
+    ], 1)
+
+
+def ellipsoid_shape_matrices(quats: np.ndarray, semi_axes) -> np.ndarray:
+    """Q_k = R_k diag(a^2, b^2, c^2) R_k^T (count, 3, 3): body k is {c_k + x : x^T Q_k^-1 x <= 1}."""
+    R = quaternion_rotations(quats)
+    return np.einsum("kij,j,klj->kil", R, np.asarray(semi_axes, dtype=np.float64) ** 2, R)
+
+
+def ellipsoid_gap(d: np.ndarray, QA: np.ndarray, QB: np.ndarray, n0=None, iters: int = 40, tol: float = 1e-14):
+    """Surface-to-surface distance of ellipsoids A (centre 0, shape matrix QA) and B (centre d, QB), batched
+    over the leading axis, with the unit normal that realises it.
+
+    For disjoint convex bodies the distance is the largest separation of their support functions,
+        gap = max_{|n| = 1}  n . d - sqrt(n^T QA n) - sqrt(n^T QB n),
+    a concave function of n maximised on the unit sphere (Riemannian Newton steps from n0 or d/|d|,
+    with backtracking).  The value is negative for overlapping bodies.  Returns (gap, n).
+    """
+    d = np.atleast_2d(np.asarray(d, dtype=np.float64))
+    QA = np.asarray(QA, dtype=np.float64).reshape(-1, 3, 3)
+    QB = np.asarray(QB, dtype=np.float64).reshape(-1, 3, 3)
+    n = d / np.linalg.norm(d, axis=1, keepdims=True) if n0 is None else np.array(n0, dtype=np.float64, ndmin=2)
+
+    def value(n):
+        a = np.sqrt(np.einsum("ki,kij,kj->k", n, QA, n))
+        b = np.sqrt(np.einsum("ki,kij,kj->k", n, QB, n))
+        return np.einsum("ki,ki->k", n, d) - a - b, a, b
+
+    f, a, b = value(n)
+    for _ in range(iters):
+        An = np.einsum("kij,kj->ki", QA, n)
+        Bn = np.einsum("kij,kj->ki", QB, n)
+        grad = d - An / a[:, None] - Bn / b[:, None]
+        ng = np.einsum("ki,ki->k", n, grad)
+        hess = -(QA / a[:, None, None] - np.einsum("ki,kj->kij", An, An) / (a ** 3)[:, None, None]) \
+               - (QB / b[:, None, None] - np.einsum("ki,kj->kij", Bn, Bn) / (b ** 3)[:, None, None])
+        # orthonormal tangent basis at n
+        t = np.where(np.abs(n[:, :1]) < 0.9, np.array([[1.0, 0.0, 0.0]]), np.array([[0.0, 1.0, 0.0]]))
+        e1 = t - np.einsum("ki,ki->k", t, n)[:, None] * n
+        e1 /= np.linalg.norm(e1, axis=1, keepdims=True)
+        e2 = np.cross(n, e1)
+        E = np.stack([e1, e2], axis=2)  # (k, 3, 2)
+        g2 = np.einsum("kia,ki->ka", E, grad)
+        if np.all(np.linalg.norm(g2, axis=1) <= tol * np.maximum(1.0, np.abs(f))):
+            break
+        H2 = np.einsum("kia,kij,kjb->kab", E, hess, E) - ng[:, None, None] * np.eye(2)
+        try:
+            xi = -np.linalg.solve(H2, g2[..., None])[..., 0]
+        except np.linalg.LinAlgError:
+            xi = g2.copy()
+        bad = np.einsum("ka,ka->k", xi, g2) <= 0.0  # not an ascent direction: use the gradient
+        xi[bad] = g2[bad]
+        step = np.einsum("kia,ka->ki", E, xi)
+        nrm = np.linalg.norm(step, axis=1, keepdims=True)
+        step = np.where(nrm > 0.5, step * (0.5 / np.maximum(nrm, 1e-300)), step)
+        alpha = np.ones(len(n))
+        for _ in range(30):  # backtracking: keep the steps that do not decrease the value
+            cand = n + alpha[:, None] * step
+            cand /= np.linalg.norm(cand, axis=1, keepdims=True)
+            fc, ac, bc = value(cand)
+            ok = fc >= f - 1e-15 * np.maximum(1.0, np.abs(f))
+            if np.all(ok):
+                break
+            alpha = np.where(ok, alpha, 0.5 * alpha)
+        n = np.where(ok[:, None], cand, n)
+        f, a, b = np.where(ok, fc, f), np.where(ok, ac, a), np.where(ok, bc, b)
+    return f, n
+
+
+def grow_ellipsoid_cluster(
+    rng: np.random.Generator,
+    Q: np.ndarray,
+    gap_lo: float,
+    gap_hi: float,
+) -> np.ndarray:
+    """Grow a cluster of ellipsoids with true surface gaps (Sec. 4.1, Sec. 4.2).
+
+    Q: (count, 3, 3) shape matrices (orientations drawn beforehand).  Body b draws g ~ U[gap_lo, gap_hi]
+    and a random unit direction u, starts far out on the ray from the centroid of the bodies placed so
+    far along u, and moves inward until its surface first comes within g of an existing body's surface
+    (ellipsoid_gap).  Every body then has a neighbour at surface gap exactly g and no body closer.  The
+    stopping point along the ray is, for each body j the ray passes, the outermost root of the convex
+    function gap_j(s) - g (Newton from the outside: the tangent never overshoots a convex function's
+    root), with bounding spheres limiting the candidates.
+    """
+    count = Q.shape[0]
+    eig = np.linalg.eigvalsh(Q)
+    Rmax = np.sqrt(eig[:, -1])  # bounding-sphere radius
+    Rmin = np.sqrt(eig[:, 0])   # inscribed-sphere radius
+    centres = np.zeros((count, 3))
+    for b in range(1, count):
+        g = rng.uniform(gap_lo, gap_hi)
+        origin = centres[:b].mean(axis=0)
+        while True:
+            u = rng.standard_normal(3)
+            u /= np.linalg.norm(u)
+            rel = centres[:b] - origin
+            along = rel @ u
+            perp2 = np.einsum("ij,ij->i", rel, rel) - along * along
+            reach = Rmax[:b] + Rmax[b] + g
+            cand = np.nonzero(perp2 < reach * reach)[0]
+            if cand.size == 0:
+                continue
+            s_hi = along[cand] + np.sqrt(reach[cand] ** 2 - perp2[cand])  # bounding spheres g apart
+            inner = Rmin[cand] + Rmin[b] + g
+            close = perp2[cand] < inner * inner
+            # where the inscribed spheres come within g, the true gap is below g: s* is at least there
+            s_floor = np.max(np.where(close, along[cand] + np.sqrt(np.maximum(inner ** 2 - perp2[cand], 0.0)),
+                                      -np.inf))
+            keep = s_hi > s_floor
+            cand, s = cand[keep], s_hi[keep].copy()
+            active = np.ones(len(cand), bool)
+            nrm = None
+            root = np.full(len(cand), -np.inf)
+            for _ in range(60):
+                d = centres[cand] - (origin + s[:, None] * u)
+                f, nrm = ellipsoid_gap(d, Q[b][None].repeat(len(cand), 0), Q[cand], n0=nrm)
+                slope = -(nrm @ u)  # d gap / d s
+                done = np.abs(f - g) <= 1e-13 * max(1.0, g)
+                root = np.where(active & done, s, root)
+                miss = active & ~done & (slope <= 0.0)  # passed the minimum above g: j never blocks
+                active &= ~done & ~miss
+                if not np.any(active):
+                    break
+                s = np.where(active, s - (f - g) / np.where(slope > 0.0, slope, 1.0), s)
+            s_star = root.max() if root.size else -np.inf
+            if np.isfinite(s_star) and s_star > 0.0:
+                break
+        centres[b] = origin + s_star * u
+    return centres
+
+
 def _ellipse_perimeter(p: np.ndarray, q: np.ndarray) -> np.ndarray:
     """Ramanujan's second approximation to the perimeter of an ellipse with semi-axes p, q."""
     h = ((p - q) / np.maximum(p + q, 1e-300)) ** 2

@@ -13,8 +13,9 @@ Workloads (the sizes are the ones the benchmark and the parity tests use):
   addition in a cube at volume fraction 0.1, min gap 0.1, M=1200, N=600,
   R_p = 0.7, forces and torques i.i.d. N(0,1), seed 2.
 * ``spheroid1000_mobility`` Stokes, 1000 prolate spheroids (1,1,2), random
-  orientations, grown cluster with gaps U[0.05,0.5] between bounding
-  spheres, M=2000, N=1000, Delta_sep = 0.25, force (0,0,-1), zero torque.
+  orientations, grown cluster with true surface-to-surface gaps U[0.05,0.5]
+  (each new body at gap g from its nearest neighbour, none closer), M=2000,
+  N=1000, Delta_sep = 0.25, force (0,0,-1), zero torque.
 * ``sphere200_adjoint``     Stokes, 200 unit spheres at volume fraction 0.15,
   min gap 0.1, M=800, N=400, forces and torques N(0,1).
 * ``batched256_mobility``   Stokes, 256 independent suspensions with body
@@ -38,6 +39,8 @@ import numpy as np
 from .geometry import (
     ellipsoid_grid,
     ellipsoid_proxy,
+    ellipsoid_shape_matrices,
+    grow_ellipsoid_cluster,
     fibonacci_sphere,
     grow_cluster,
     random_quaternions,
@@ -103,6 +106,20 @@ class Workload:
             quats=None if self.quats is None else self.quats[:nb], shape_id=self.shape_id[:nb],
             body_offsets=self.body_offsets[: k + 1].copy(), Q=cut(self.Q), F=cut(self.F), T=cut(self.T),
             mu=self.mu, seed=self.seed, description=f"first {k} suspensions of {self.name}",
+        )
+
+    def first_bodies(self, k: int) -> "Workload":
+        """The first k bodies of a one-suspension workload (for a grown cluster: the compact cluster they
+        formed before the later bodies were added), with their forces, torques or charges."""
+        if self.num_suspensions != 1:
+            raise ValueError("first_bodies needs a single suspension")
+        k = min(k, self.num_bodies)
+        cut = lambda a: None if a is None else a[..., :k, :] if a.ndim == 3 else a[:k]  # noqa: E731
+        return Workload(
+            name=f"{self.name}[:{k} bodies]", kind=self.kind, shapes=self.shapes, centres=self.centres[:k],
+            quats=None if self.quats is None else self.quats[:k], shape_id=self.shape_id[:k],
+            body_offsets=np.array([0, k], np.int32), Q=cut(self.Q), F=cut(self.F), T=cut(self.T),
+            mu=self.mu, seed=self.seed, description=f"first {k} bodies of {self.name}",
         )
 
     @property
@@ -270,8 +287,8 @@ def spheroid_cluster(
 ) -> Workload:
     rng = np.random.default_rng(seed)
     shape = spheroid_shape(m, n, a, c, dsep)
-    centres = grow_cluster(rng, count, shape.bounding_radius, gap_lo, gap_hi)
     quats = random_quaternions(rng, count)
+    centres = grow_ellipsoid_cluster(rng, ellipsoid_shape_matrices(quats, (a, a, c)), gap_lo, gap_hi)
     F = np.zeros((1, count, 3))
     F[0, :, 2] = -1.0
     return Workload(
@@ -287,7 +304,8 @@ def spheroid_cluster(
         seed=seed,
         description=(
             f"Stokes, {count} prolate spheroids ({a},{a},{c}), random orientations, grown cluster with "
-            f"bounding-sphere gaps U[{gap_lo},{gap_hi}], M={m}, N={n}, Delta_sep={dsep}, F=(0,0,-1), T=0"
+            f"surface gaps U[{gap_lo},{gap_hi}] (each body at gap g from its nearest neighbour), M={m}, N={n}, "
+            f"Delta_sep={dsep}, F=(0,0,-1), T=0"
         ),
     )
 

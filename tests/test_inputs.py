@@ -55,3 +55,49 @@ def test_workloads_are_seeded():
     assert np.all(np.diff(w.body_offsets) >= 2) and np.all(np.diff(w.body_offsets) <= 64)
     c = make_workload("two_sphere_elastance")
     assert c.off_diagonal_pairs() == 2 * 600 * 300
+
+
+def test_ellipsoid_gap_closed_forms_and_brute_force():
+    from mfs_inputs.geometry import (ellipsoid_gap, ellipsoid_shape_matrices, quaternion_rotations,
+                                     random_quaternions)
+
+    # spheres: |d| - r_A - r_B
+    f, _ = ellipsoid_gap(np.array([[3.0, 1.0, 0.0]]), np.eye(3)[None], 0.25 * np.eye(3)[None])
+    assert abs(f[0] - (np.sqrt(10.0) - 1.5)) < 1e-13
+    # (1,1,2) spheroids with parallel axes: tip to tip and side by side
+    Q = np.diag([1.0, 1.0, 4.0])[None]
+    assert abs(ellipsoid_gap(np.array([[0.0, 0.0, 4.3]]), Q, Q)[0][0] - 0.3) < 1e-13
+    assert abs(ellipsoid_gap(np.array([[2.2, 0.0, 0.0]]), Q, Q)[0][0] - 0.2) < 1e-13
+    # rotated: at least the closest pair of densely sampled surface points, and within their spacing
+    rng = np.random.default_rng(0)
+    q = random_quaternions(rng, 2)
+    QQ = ellipsoid_shape_matrices(q, (1.0, 1.0, 2.0))
+    d = np.array([[2.5, 1.0, 0.7]])
+    f, n = ellipsoid_gap(d, QQ[0][None], QQ[1][None])
+    R = quaternion_rotations(q)
+    u = rng.standard_normal((100000, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    ax = np.array([1.0, 1.0, 2.0])
+    pa, pb = (u * ax) @ R[0].T, d[0] + (u * ax) @ R[1].T
+    # the supporting planes with normal n: the gap is the slab between them (sampled surfaces reach
+    # the planes up to the sampling error)
+    slab = float((pb @ n[0]).min() - (pa @ n[0]).max())
+    assert f[0] - 1e-12 <= slab < f[0] + 1e-4
+    best = min(np.linalg.norm(pb - p, axis=1).min() for p in pa[::50])
+    assert f[0] <= best + 1e-12 and best - f[0] < 0.02
+
+
+def test_spheroid_cluster_true_surface_gaps():
+    """The 1000-spheroid cluster (first 150 bodies): every body after the first has an earlier
+    neighbour at surface gap in [0.05, 0.5], and no two bodies are closer than 0.05."""
+    from mfs_inputs.geometry import ellipsoid_gap, ellipsoid_shape_matrices
+
+    wl = make_workload("spheroid1000_mobility", count=150, m=60, n=30)
+    Q = ellipsoid_shape_matrices(wl.quats, wl.shapes[0].semi_axes)
+    i, j = np.triu_indices(wl.num_bodies, 1)
+    near = np.linalg.norm(wl.centres[j] - wl.centres[i], axis=1) < 4.0 + 0.5
+    gaps, _ = ellipsoid_gap(wl.centres[j[near]] - wl.centres[i[near]], Q[i[near]], Q[j[near]])
+    assert gaps.min() > 0.05 - 1e-9
+    for b in range(1, wl.num_bodies):
+        mine = gaps[j[near] == b]
+        assert mine.size and 0.05 - 1e-9 <= mine.min() <= 0.5 + 1e-9
