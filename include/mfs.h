@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define MFS_ABI_VERSION 3
+#define MFS_ABI_VERSION 4
 
 typedef struct mfs_ctx mfs_ctx; /* opaque; owns all internal device memory */
 
@@ -101,6 +101,17 @@ typedef struct {
                              graph with a device-side while node (the matvec and Arnoldi kernels read the
                              iteration index from device memory; no host round trip per iteration).  Not
                              with profile = 1, whose per-launch events need the host loop.  0: host loop. */
+    int32_t farfield;     /* 0 (default): every pair sum is a direct sum over all body pairs.  1: the forward
+                             pair sums (matvec, right-hand side u_0) run as an equivalent-source treecode, the
+                             GPU counterpart of the far-field acceleration the paper does with an FMM (Sec. 4):
+                             an 8-ary tree of median splits over the body centres; every body and every node
+                             gets 196 equivalent point sources on a sphere of radius r_e = (radius of its proxy
+                             points) / 0.83, fitted in FP64 by least squares to its proxies' field at 392
+                             check points at 2.5 r_e; targets at least 3 r_e from a node's centre see it
+                             through those points, nearer ones its children, down to the proxy points of the
+                             near bodies (direct, FP32 pair kernel).  Relative accuracy of the sums about
+                             1e-7; the pair work drops from O(P^2) to about O(P log P).  Needs precision 0 or
+                             2; the transposed sums and mfs_evaluate* stay direct. */
 } mfs_options;
 
 typedef struct {
@@ -112,9 +123,11 @@ typedef struct {
     double ms_setup;      /* wall time of mfs_setup (ms) */
     double ms_solve;      /* device time of the solve (ms) */
     double ms_pairs;      /* device time spent in the pair-sum kernel (ms) */
-    double pairs;         /* point pairs evaluated by the pair-sum kernel (per right-hand side) */
+    double pairs;         /* point pairs of the direct sums this solve represents (per right-hand side) */
     int32_t launches;     /* device kernels and memsets this call enqueued */
     int32_t pair_launches;/* pair-sum kernel launches of this call */
+    double pairs_evaluated; /* target-source pairs the pair kernel evaluated (per right-hand side): `pairs`
+                               for direct sums, fewer with farfield = 1 (near pairs, equivalent points) */
 } mfs_solve_info;
 
 /* Fill *opt with the defaults listed above. */

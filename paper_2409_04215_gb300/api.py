@@ -95,6 +95,7 @@ class Options(ctypes.Structure):
         ("tensor_cores", ctypes.c_int32),
         ("pair_variant", ctypes.c_int32),
         ("graphs", ctypes.c_int32),
+        ("farfield", ctypes.c_int32),
     ]
 
 
@@ -111,6 +112,7 @@ class _Info(ctypes.Structure):
         ("pairs", ctypes.c_double),
         ("launches", ctypes.c_int32),
         ("pair_launches", ctypes.c_int32),
+        ("pairs_evaluated", ctypes.c_double),
     ]
 
 
@@ -128,9 +130,10 @@ class SolveInfo:
     launches: int
     pair_launches: int
     status: int
+    pairs_evaluated: float = 0.0
 
 
-ABI_VERSION = 3  # MFS_ABI_VERSION of the header these structures mirror
+ABI_VERSION = 4  # MFS_ABI_VERSION of the header these structures mirror
 
 
 def load_library(path: Optional[str] = None):
@@ -496,7 +499,7 @@ class MFS:
 
 def _info(i: _Info, rc: int) -> SolveInfo:
     return SolveInfo(i.iters, bool(i.converged), i.matvecs, i.lanes, i.rel_residual, i.ms_setup, i.ms_solve,
-                     i.ms_pairs, i.pairs, i.launches, i.pair_launches, rc)
+                     i.ms_pairs, i.pairs, i.launches, i.pair_launches, rc, i.pairs_evaluated)
 
 
 def mobility(mfs: "MFS", centres, F, T):

@@ -10,7 +10,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmfs.so")
-SOURCES = ["pair_kernel.cu", "precond.cu", "gmres.cu", "tc_gemm.cu", "stress.cu", "mfs_api.cu"]
+SOURCES = ["pair_kernel.cu", "precond.cu", "gmres.cu", "tc_gemm.cu", "stress.cu", "farfield.cu", "mfs_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC"]
 

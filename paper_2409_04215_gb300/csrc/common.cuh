@@ -33,6 +33,8 @@ struct PairTile {
     int B0, B1;          // source bodies of the suspension [B0, B1)
     long long u0, u1;    // global unit range of this tile
     int gA, gB;          // first and last CTA whose share meets this tile
+    int L0, L1;          // L0 >= 0: the tile's sources are the segments of interaction-list entries
+                         // [L0, L1) (PairGeom::lst_*) instead of the bodies [B0, B1)
 };
 
 // Compensated pair sums split body-local coordinates and centre differences at multiples of
@@ -50,6 +52,12 @@ struct PairGeom {
     const float *tgt_w = nullptr;  // gradient kernel only: target strengths w, FP32 [nrhs][ntargets][3]
     // compensated kernels only: body-local targets split as x = hi + lo, hi a multiple of 1/MFS_XGRID
     const float4 *tgt_hi = nullptr, *tgt_lo = nullptr;  // [ntargets] (x, y, z, unused)
+    // interaction lists (tiles with L0 >= 0): entry e names source segment lst_seg[e], whose records
+    // are [seg_rec0[s], seg_rec1[s]) (blocks of MFS_BS), and starts at global unit lst_cum[e]
+    // (lst_cum has one entry more than lst_seg: the units of the last tile end at its last value)
+    const int *lst_seg = nullptr;
+    const long long *lst_cum = nullptr;
+    const int *seg_rec0 = nullptr, *seg_rec1 = nullptr;
 };
 
 struct PairWork {
@@ -62,6 +70,7 @@ struct PairWork {
     int tile_targets;
     int include_self;          // 1: self pairs included (right-hand side u_0)
     double *src_grad = nullptr;  // gradient kernel only: per source body sums, FP64 [P][3] (atomic adds)
+    const int *tperm = nullptr;  // epilogue: target t's value goes to (and its base is read at) tperm[t]
 };
 
 // ---------------------------------------------------------------------------

@@ -2,6 +2,9 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <vector>
+
 #include "common.cuh"
 
 namespace mfs {
@@ -133,6 +136,39 @@ cudaError_t stress_f32(int nrhs, const float4 *tgt, const float *nrm, int np, co
 cudaError_t stress_f64(int nrhs, const double *tgt_local, const int *tbody, const double *nrm, int np,
                        const double *src_local, const int *src_off, int sum_N, const double *lam, const int *sb0,
                        const int *sb1, const double *centres, double *p_out, double *t_out, cudaStream_t st);
+
+// ---- far field of the pair sums: equivalent-source treecode (farfield.cu) ----
+constexpr int FF_NE = 196;            // equivalent points per node (a Fibonacci sphere of radius r_e)
+constexpr int FF_NC = 392;            // check points per node (radius FF_CHECK * r_e), least-squares fit
+constexpr double FF_CHECK = 2.5;      // check radius / equivalent radius
+constexpr double FF_SRC_RATIO = 0.83; // a node's source radius / its equivalent radius
+constexpr double FF_KAPPA = 3.0;      // a target this many equivalent radii from a node's centre sees the node
+                                      // through its equivalent points
+struct FFNode {
+    double c[3] = {0, 0, 0};  // centre
+    double rs = 0.0;          // radius of the node's proxy sources about c
+    double re = 0.0;          // equivalent radius rs / FF_SRC_RATIO
+    int body = -1;            // the body of a leaf, -1 for a group
+    int first = 0, count = 0; // descendant bodies: order[first .. first + count)
+    int nchild = 0;
+    int child[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+struct FFTree {
+    std::vector<FFNode> nodes;
+    std::vector<int> order;  // bodies in tree (depth-first leaf) order
+    std::vector<int> pos;    // pos[body] = its index in `order`
+    std::vector<int> roots;  // one per suspension
+};
+// The 8-ary median-split tree of each suspension's bodies (centres [P][3], source radii rsrc [P]).
+void ff_build_tree(int P, const double *centres, const double *rsrc, int S, const int *body_off, FFTree &t);
+// Interaction list of the target bodies `tbodies` (original ids; target radii rtgt): segment ids, a
+// body's proxy points as its tree position q < P, a node's equivalent points as P + node.  With
+// self_skip, a single target body's own proxy points are left out.
+void ff_interaction_list(const FFTree &t, int root, const std::vector<int> &tbodies, const double *centres,
+                         const double *rtgt, int self_skip, std::vector<int> &segs);
+// mu[h][node][e][d] *= re[node] (the fit was made on the unit sphere; the kernels are homogeneous of
+// degree -1).
+cudaError_t ff_scale(double *mu, const double *re, int nodes, int per_node, int nrhs, cudaStream_t st);
 
 // ---- GMRES (gmres.cu): L independent lanes, lane l owns vector entries [seg_off[l], seg_off[l+1]) ----
 struct GmresDev {

@@ -162,6 +162,36 @@ struct mfs_ctx {
     float *w32_d = nullptr;       // [max_rhs][sum_M][3] FP32 adjoint strengths
     double *eye6_d = nullptr;     // [nshapes][36] identity (K_N [u; w] expansion)
 
+    // far field of the pair sums (opt.farfield = 1): equivalent-source treecode (farfield.cu)
+    struct FarField {
+        bool ready = false;
+        FFTree tree;
+        int nodes = 0;
+        std::vector<double> rsrc, rtgt;              // per body: radius of its proxy / collocation points
+        double *PinvT = nullptr;                     // [D FF_NC][D FF_NE]: transposed pseudo-inverse of the
+                                                     // check <- equivalent map on the unit sphere (FP64)
+        double *centres = nullptr;                   // [P + nodes][3]: bodies in tree order, then the nodes
+        double *re = nullptr;                        // [nodes] equivalent radii
+        float4 *eq_pos = nullptr;                    // [nodes FF_NE] equivalent points about their node's centre
+        int *eq_pt = nullptr;                        // identity record -> point map (packing)
+        float4 *chk_pos = nullptr;                   // [nodes FF_NC] check points, w = P + node
+        float4 *tgt = nullptr;                       // [sum_M] targets in tree order, w = tree position
+        int *tperm = nullptr;                        // [sum_M] tree-order target -> caller's target index
+        int *seg_rec0 = nullptr, *seg_rec1 = nullptr;  // [P + nodes] record range of every segment
+        std::vector<int> seg_rec0_h, seg_rec1_h;
+        float *rec = nullptr;                        // proxy records, then equivalent records
+        int rec_floats = 0;
+        double *ucheck = nullptr;                    // [max_rhs][nodes FF_NC][D]
+        double *mu = nullptr;                        // [max_rhs][nodes FF_NE][D]
+        struct Plan {
+            PairPlan up, ev;
+            int *lst_seg_up = nullptr, *lst_seg_ev = nullptr;
+            long long *lst_cum_up = nullptr, *lst_cum_ev = nullptr;
+            double pairs_up = 0.0, pairs_ev = 0.0;   // target-source pairs one application evaluates
+        };
+        std::map<int, Plan> plans;                   // key: variant * 2 + include_self
+    } ff;
+
     int sm_count = 0;
     std::string last_error;
     std::vector<void *> allocs;
@@ -398,6 +428,7 @@ mfs_status build_plan_for(mfs_ctx *ctx, int variant, int include_self, const std
             tl.skip = (!include_self && tl.nb == 1) ? kb0 : -1;
             tl.B0 = B0;
             tl.B1 = B1;
+            tl.L0 = tl.L1 = -1;
             long long u = 0;
             for (int b = B0; b < B1; ++b)
                 if (b != tl.skip) u += boff[b + 1] - boff[b];
@@ -513,6 +544,9 @@ __global__ void combine_raw_kernel(const double *raw, const double *base, double
     if (i < n) out[i] = (base ? beta * base[i] : 0.0) + scale * raw[i];
 }
 
+mfs_status ff_pair_apply(mfs_ctx *ctx, int variant, const double *strength, double *out, const double *base,
+                         double beta, double scale, int nrhs, int include_self, cudaStream_t st);
+
 mfs_status pair_apply(mfs_ctx *ctx, const double *strength, double *out, const double *base, double beta,
                       double sign, int nrhs, int include_self, cudaStream_t st) {
     const double scale = sign * kernel_scale(ctx);
@@ -532,6 +566,7 @@ mfs_status pair_apply(mfs_ctx *ctx, const double *strength, double *out, const d
         ctx->last_error = "no pair-kernel variant for this nrhs";
         return MFS_ERR_INVALID_ARG;
     }
+    if (ctx->ff.ready) return ff_pair_apply(ctx, variant, strength, out, base, beta, scale, nrhs, include_self, st);
     PairPlan *plan = nullptr;
     CKS(get_plan(ctx, variant, include_self, &plan));
     CK(pack_for(ctx, variant, strength, nrhs, st));
@@ -553,6 +588,223 @@ mfs_status pair_apply(mfs_ctx *ctx, const double *strength, double *out, const d
         ctx->pair_launches += 1;
     }
     CK(pair_epilogue(ctx->D, nrhs, w, base, beta, scale, out, ctx->sumM, st));
+    return MFS_OK;
+}
+
+// Tiles over targets grouped into consecutive groups (group g: targets [toff[g], toff[g+1]), its id in
+// the geometry's centre table gid0 + g), never crossing a group boundary listed in `cuts`, each tile
+// with the interaction list that list_of(g0, g1) gives for its groups g0..g1; seg_blocks[s] blocks of
+// MFS_BS records per segment s.  Uploads the tiles and the lists (PairGeom::lst_seg, lst_cum).
+template <class ListFn>
+mfs_status build_plan_lists(mfs_ctx *ctx, int variant, int include_self, const std::vector<int> &toff, int gid0,
+                            const std::vector<int> &cuts, const std::vector<long long> &seg_blocks,
+                            const std::vector<int> &seg_recs, ListFn list_of, PairPlan &plan, int **lst_seg_d,
+                            long long **lst_cum_d, double &pairs) {
+    int count = 0;
+    const PairVariant *vv = pair_variants(&count);
+    const PairVariant &v = vv[variant];
+    const int TT = v.tile_targets;
+    const int C = v.D * v.nrhs;
+    std::vector<PairTile> tiles;
+    std::vector<int> lst;
+    std::vector<long long> cum{0};
+    std::vector<int> segs;
+    long long units = 0;
+    pairs = 0.0;
+    const int ngroups = (int)toff.size() - 1;
+    std::vector<int> tgroup(toff.back());
+    for (int g = 0; g < ngroups; ++g)
+        for (int t = toff[g]; t < toff[g + 1]; ++t) tgroup[t] = g;
+    for (size_t ci = 0; ci + 1 < cuts.size(); ++ci) {
+        const int t_end = toff[cuts[ci + 1]];
+        int t = toff[cuts[ci]];
+        while (t < t_end) {
+            int t1 = std::min(t + TT, t_end);
+            const int g0 = tgroup[t];
+            int g1 = tgroup[t1 - 1];
+            if (g1 - g0 + 1 > MFS_MAX_TILE_BODIES) {
+                g1 = g0 + MFS_MAX_TILE_BODIES - 1;
+                t1 = toff[g1 + 1];
+            }
+            PairTile tl;
+            tl.t0 = t;
+            tl.t1 = t1;
+            tl.kb0 = gid0 + g0;
+            tl.nb = g1 - g0 + 1;
+            tl.skip = -1;
+            tl.B0 = tl.B1 = 0;
+            segs.clear();
+            list_of(g0, g1, segs);
+            tl.L0 = (int)lst.size();
+            long long u = 0;
+            for (int sgi : segs) {
+                lst.push_back(sgi);
+                u += seg_blocks[sgi];
+                cum.push_back(units + u);
+                pairs += (double)(t1 - t) * seg_recs[sgi];
+            }
+            tl.L1 = (int)lst.size();
+            tl.u0 = units;
+            tl.u1 = units + u;
+            units += u;
+            tiles.push_back(tl);
+            t = t1;
+        }
+    }
+    const int occ = pair_occupancy(variant);
+    if (occ <= 0) {
+        ctx->last_error = "pair kernel variant cannot be resident on this GPU";
+        return MFS_ERR_CUDA;
+    }
+    long long G = (long long)occ * ctx->sm_count;
+    if (G > units) G = std::max<long long>(units, 1);
+    const long long W = std::max<long long>(units, 1);
+    for (auto &tl : tiles) {
+        if (tl.u1 == tl.u0) {
+            tl.gA = tl.gB = -1;
+            continue;
+        }
+        auto owner = [&](long long u) { return (int)(((u + 1) * G - 1) / W); };
+        tl.gA = owner(tl.u0);
+        tl.gB = owner(tl.u1 - 1);
+    }
+    plan.variant = variant;
+    plan.include_self = include_self;
+    plan.tile_targets = TT;
+    plan.G = (int)G;
+    plan.ntiles = (int)tiles.size();
+    plan.total_units = units;
+    CK(ctx->alloc(&plan.tiles, std::max<size_t>(tiles.size(), 1)));
+    CK(cudaMemcpy(plan.tiles, tiles.data(), sizeof(PairTile) * tiles.size(), cudaMemcpyHostToDevice));
+    CK(ctx->alloc(&plan.partial, (size_t)G * 2 * TT * C));
+    CK(ctx->alloc(&plan.direct, (size_t)std::max(toff.back(), 1) * C));
+    CK(ctx->alloc(lst_seg_d, std::max<size_t>(lst.size(), 1)));
+    CK(ctx->alloc(lst_cum_d, cum.size()));
+    if (!lst.empty()) CK(cudaMemcpy(*lst_seg_d, lst.data(), sizeof(int) * lst.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(*lst_cum_d, cum.data(), sizeof(long long) * cum.size(), cudaMemcpyHostToDevice));
+    return MFS_OK;
+}
+
+// The far-field plans of one pair-kernel variant: the upward sums (each node's check points against
+// its descendant bodies' proxy points) and the evaluation (targets in tree order against their
+// interaction lists).
+mfs_status ff_get_plan(mfs_ctx *ctx, int variant, int include_self, mfs_ctx::FarField::Plan **out) {
+    auto &F = ctx->ff;
+    const int key = variant * 2 + include_self;
+    auto it = F.plans.find(key);
+    if (it != F.plans.end()) {
+        *out = &it->second;
+        return MFS_OK;
+    }
+    mfs_ctx::FarField::Plan pl;
+    const int P = ctx->P, nodes = F.nodes;
+    std::vector<long long> seg_blocks(P + nodes);
+    std::vector<int> seg_recs(P + nodes);
+    for (int sg = 0; sg < P + nodes; ++sg) {
+        seg_recs[sg] = F.seg_rec1_h[sg] - F.seg_rec0_h[sg];
+        seg_blocks[sg] = (seg_recs[sg] + MFS_BS - 1) / MFS_BS;
+    }
+    // upward: one group per node, tiles never span two nodes
+    std::vector<int> toff_up(nodes + 1), cuts_up(nodes + 1);
+    for (int n = 0; n <= nodes; ++n) {
+        toff_up[n] = n * FF_NC;
+        cuts_up[n] = n;
+    }
+    CKS(build_plan_lists(ctx, variant, 1, toff_up, P, cuts_up, seg_blocks, seg_recs,
+                         [&](int g0, int g1, std::vector<int> &segs) {
+                             for (int n = g0; n <= g1; ++n)
+                                 for (int q = F.tree.nodes[n].first; q < F.tree.nodes[n].first + F.tree.nodes[n].count;
+                                      ++q)
+                                     segs.push_back(q);
+                         },
+                         pl.up, &pl.lst_seg_up, &pl.lst_cum_up, pl.pairs_up));
+    // evaluation: groups are the bodies in tree order; tiles stay inside a suspension
+    std::vector<int> toff_ev(P + 1, 0);
+    for (int q = 0; q < P; ++q) {
+        const int b = F.tree.order[q];
+        toff_ev[q + 1] = toff_ev[q] + (ctx->tgt_off[b + 1] - ctx->tgt_off[b]);
+    }
+    std::vector<int> cuts_ev(ctx->S + 1);
+    for (int sp = 0; sp <= ctx->S; ++sp) cuts_ev[sp] = ctx->body_off[sp];
+    std::vector<int> suspension_of(P);
+    for (int sp = 0; sp < ctx->S; ++sp)
+        for (int b = ctx->body_off[sp]; b < ctx->body_off[sp + 1]; ++b) suspension_of[b] = sp;
+    std::vector<int> tb;
+    CKS(build_plan_lists(ctx, variant, include_self, toff_ev, 0, cuts_ev, seg_blocks, seg_recs,
+                         [&](int g0, int g1, std::vector<int> &segs) {
+                             tb.clear();
+                             for (int q = g0; q <= g1; ++q) tb.push_back(F.tree.order[q]);
+                             ff_interaction_list(F.tree, F.tree.roots[suspension_of[tb[0]]], tb, ctx->centres.data(),
+                                                 F.rtgt.data(), !include_self, segs);
+                         },
+                         pl.ev, &pl.lst_seg_ev, &pl.lst_cum_ev, pl.pairs_ev));
+    pl.ev.include_self = include_self;
+    it = F.plans.emplace(key, pl).first;
+    *out = &it->second;
+    return MFS_OK;
+}
+
+// One pair-kernel launch on the far-field geometry, bracketed by profiling events like pair_apply's.
+mfs_status ff_launch(mfs_ctx *ctx, int variant, const PairGeom &g, const PairWork &w, cudaStream_t st) {
+    if (w.total_units == 0) return MFS_OK;
+    const size_t slot = 2 * (size_t)ctx->pair_launches;
+    if (ctx->opt.profile) {
+        while (ctx->pev.size() < slot + 2) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            ctx->pev.push_back(e);
+        }
+        CK(cudaEventRecord(ctx->pev[slot], st));
+    }
+    CK(pair_launch(variant, g, w, ctx->err_d, st));
+    if (ctx->opt.profile) CK(cudaEventRecord(ctx->pev[slot + 1], st));
+    ctx->launches += 1;
+    ctx->pair_launches += 1;
+    return MFS_OK;
+}
+
+// out = beta * base + scale * (pair sum of strengths) through the treecode: proxy records, the
+// upward check sums, the equivalent strengths (FP64 product with the pseudo-inverse, radius scale),
+// their records, then the evaluation over the interaction lists (results written back in the
+// caller's target order).
+mfs_status ff_pair_apply(mfs_ctx *ctx, int variant, const double *strength, double *out, const double *base,
+                         double beta, double scale, int nrhs, int include_self, cudaStream_t st) {
+    auto &F = ctx->ff;
+    mfs_ctx::FarField::Plan *pl = nullptr;
+    CKS(ff_get_plan(ctx, variant, include_self, &pl));
+    int vc = 0;
+    const PairVariant *vv = pair_variants(&vc);
+    const int D = ctx->D, nodes = F.nodes;
+    const int REC = pair_record_floats(D, nrhs, vv[variant].packed);
+    CK(pack_sources(D, nrhs, vv[variant].packed, ctx->src_pos_d, ctx->rec_pt_d, strength, ctx->sumN, ctx->nrec, F.rec,
+                    st));
+    PairGeom g;
+    g.src = F.rec;
+    g.src_off = nullptr;
+    g.blk_off = nullptr;
+    g.centres = F.centres;
+    g.lst_seg = pl->lst_seg_up;
+    g.lst_cum = pl->lst_cum_up;
+    g.seg_rec0 = F.seg_rec0;
+    g.seg_rec1 = F.seg_rec1;
+    g.tgt = F.chk_pos;
+    g.ntargets = nodes * FF_NC;
+    const PairWork wu = work_of(pl->up);
+    CKS(ff_launch(ctx, variant, g, wu, st));
+    CK(pair_epilogue(D, nrhs, wu, nullptr, 0.0, 1.0, F.ucheck, nodes * FF_NC, st));
+    CK(gemm_rm64(nrhs * nodes, D * FF_NE, D * FF_NC, F.ucheck, F.PinvT, F.mu, st));
+    CK(ff_scale(F.mu, F.re, nodes, D * FF_NE, nrhs, st));
+    CK(pack_sources(D, nrhs, vv[variant].packed, F.eq_pos, F.eq_pt, F.mu, nodes * FF_NE, nodes * FF_NE,
+                    F.rec + (size_t)ctx->nrec * REC, st));
+    g.lst_seg = pl->lst_seg_ev;
+    g.lst_cum = pl->lst_cum_ev;
+    g.tgt = F.tgt;
+    g.ntargets = ctx->sumM;
+    PairWork we = work_of(pl->ev);
+    we.tperm = F.tperm;
+    CKS(ff_launch(ctx, variant, g, we, st));
+    CK(pair_epilogue(D, nrhs, we, base, beta, scale, out, ctx->sumM, st));
+    ctx->launches += 7;
     return MFS_OK;
 }
 
@@ -1042,6 +1294,7 @@ void mfs_default_options(mfs_options *opt) {
     opt->tensor_cores = 1;
     opt->pair_variant = -1;
     opt->graphs = 1;
+    opt->farfield = 0;
 }
 
 int32_t mfs_abi_version(void) { return MFS_ABI_VERSION; }
@@ -1262,6 +1515,181 @@ static mfs_status ensure_dirichlet(mfs_ctx *ctx, cudaStream_t st) {
         if (!ctx->shapes[s].fs[1].built) status = build_shape_factors(ctx, solver, s, 1, st);
     cusolverDnDestroy(solver);
     return status;
+}
+
+// n points of the Fibonacci lattice on the unit sphere (z_i = 1 - (2i+1)/n, golden-angle longitudes).
+static void unit_fibonacci(int n, std::vector<double> &p) {
+    const double ga = 2.0 * MFS_PI / (((1.0 + std::sqrt(5.0)) / 2.0) * ((1.0 + std::sqrt(5.0)) / 2.0));
+    p.resize(3 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        const double z = 1.0 - (2.0 * i + 1.0) / n, rho = std::sqrt(std::max(0.0, 1.0 - z * z));
+        p[3 * i] = rho * std::cos(ga * i);
+        p[3 * i + 1] = rho * std::sin(ga * i);
+        p[3 * i + 2] = z;
+    }
+}
+
+// The far-field structures (opt.farfield = 1): the tree, the FP64 pseudo-inverse of the map from
+// equivalent strengths on the unit sphere to the field at the check points (truncated at 1e-12 of the
+// largest singular value; least squares, FF_NC > FF_NE), and the tree-ordered geometry.
+static mfs_status ff_setup(mfs_ctx *ctx, cudaStream_t st) {
+    auto &F = ctx->ff;
+    const int P = ctx->P, D = ctx->D;
+    F.rsrc.assign(P, 0.0);
+    F.rtgt.assign(P, 0.0);
+    for (int k = 0; k < P; ++k) {
+        const ShapeHost &sh = ctx->shapes[ctx->shape_id[k]];
+        for (int j = 0; j < sh.N; ++j)
+            F.rsrc[k] = std::max(F.rsrc[k], std::sqrt(sh.Y0[3 * j] * sh.Y0[3 * j] + sh.Y0[3 * j + 1] * sh.Y0[3 * j + 1] +
+                                                      sh.Y0[3 * j + 2] * sh.Y0[3 * j + 2]));
+        for (int i = 0; i < sh.M; ++i)
+            F.rtgt[k] = std::max(F.rtgt[k], std::sqrt(sh.X0[3 * i] * sh.X0[3 * i] + sh.X0[3 * i + 1] * sh.X0[3 * i + 1] +
+                                                      sh.X0[3 * i + 2] * sh.X0[3 * i + 2]));
+    }
+    ff_build_tree(P, ctx->centres.data(), F.rsrc.data(), ctx->S, ctx->body_off.data(), F.tree);
+    const int nodes = F.nodes = (int)F.tree.nodes.size();
+
+    // check <- equivalent map on the unit sphere (raw kernel: 1/r or (I + r r^T / r^2) / r), column-major
+    std::vector<double> ue, uc;
+    unit_fibonacci(FF_NE, ue);
+    unit_fibonacci(FF_NC, uc);
+    const int m = D * FF_NC, n = D * FF_NE;
+    std::vector<double> A((size_t)m * n);
+    for (int i = 0; i < FF_NC; ++i)
+        for (int j = 0; j < FF_NE; ++j) {
+            double r[3], r2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                r[a] = FF_CHECK * uc[3 * i + a] - ue[3 * j + a];
+                r2 += r[a] * r[a];
+            }
+            const double ri = 1.0 / std::sqrt(r2);
+            for (int a = 0; a < D; ++a)
+                for (int b = 0; b < D; ++b) {
+                    const double v = D == 1 ? ri : ((a == b ? ri : 0.0) + r[a] * r[b] * ri * ri * ri);
+                    A[(size_t)(D * j + b) * m + (D * i + a)] = v;
+                }
+        }
+    cusolverDnHandle_t solver = nullptr;
+    if (cusolverDnCreate(&solver) != CUSOLVER_STATUS_SUCCESS) {
+        ctx->last_error = "cusolverDnCreate failed";
+        return MFS_ERR_CUDA;
+    }
+    cusolverDnSetStream(solver, st);
+    double *A_d = nullptr, *U_d = nullptr, *S_d = nullptr, *VT_d = nullptr, *work = nullptr;
+    int *info_d = nullptr, lwork = 0, info_h = 0;
+    bool ok = cudaMalloc(&A_d, sizeof(double) * A.size()) == cudaSuccess &&
+              cudaMalloc(&U_d, sizeof(double) * (size_t)m * n) == cudaSuccess &&
+              cudaMalloc(&S_d, sizeof(double) * n) == cudaSuccess &&
+              cudaMalloc(&VT_d, sizeof(double) * (size_t)n * n) == cudaSuccess &&
+              cudaMalloc(&info_d, sizeof(int)) == cudaSuccess &&
+              cudaMemcpy(A_d, A.data(), sizeof(double) * A.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+              cusolverDnDgesvd_bufferSize(solver, m, n, &lwork) == CUSOLVER_STATUS_SUCCESS &&
+              cudaMalloc(&work, sizeof(double) * std::max(lwork, 1)) == cudaSuccess;
+    signed char jobu = 'S', jobvt = 'S';
+    ok = ok && cusolverDnDgesvd(solver, jobu, jobvt, m, n, A_d, m, S_d, U_d, m, VT_d, n, work, lwork, nullptr,
+                                info_d) == CUSOLVER_STATUS_SUCCESS;
+    std::vector<double> U((size_t)m * n), S(n), VT((size_t)n * n);
+    ok = ok && cudaMemcpy(&info_h, info_d, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && info_h == 0 &&
+         cudaMemcpy(U.data(), U_d, sizeof(double) * U.size(), cudaMemcpyDeviceToHost) == cudaSuccess &&
+         cudaMemcpy(S.data(), S_d, sizeof(double) * n, cudaMemcpyDeviceToHost) == cudaSuccess &&
+         cudaMemcpy(VT.data(), VT_d, sizeof(double) * VT.size(), cudaMemcpyDeviceToHost) == cudaSuccess;
+    cudaFree(A_d); cudaFree(U_d); cudaFree(S_d); cudaFree(VT_d); cudaFree(work); cudaFree(info_d);
+    cusolverDnDestroy(solver);
+    if (!ok || !(S[0] > 0.0)) {
+        cudaGetLastError();
+        ctx->last_error = "far field: SVD of the check <- equivalent map failed";
+        return MFS_ERR_CUDA;
+    }
+    // PinvT[i][j] = sum_k U[i][k] / s_k VT[k][j] (row-major m x n) over the kept singular values
+    std::vector<double> PinvT((size_t)m * n, 0.0), row(n);
+    for (int k = 0; k < n; ++k) {
+        if (!(S[k] > 1e-12 * S[0])) continue;
+        const double inv = 1.0 / S[k];
+        for (int j = 0; j < n; ++j) row[j] = inv * VT[(size_t)j * n + k];
+        for (int i = 0; i < m; ++i) {
+            const double u = U[(size_t)k * m + i];
+            double *o = &PinvT[(size_t)i * n];
+            for (int j = 0; j < n; ++j) o[j] += u * row[j];
+        }
+    }
+
+    // tree-ordered geometry and segments: proxy segment q (tree position) = body order[q], node segment
+    // P + node = its equivalent points
+    std::vector<double> cen(3 * (size_t)(P + nodes)), re(nodes);
+    for (int q = 0; q < P; ++q)
+        for (int a = 0; a < 3; ++a) cen[3 * q + a] = ctx->centres[3 * F.tree.order[q] + a];
+    for (int nd = 0; nd < nodes; ++nd) {
+        for (int a = 0; a < 3; ++a) cen[3 * (P + nd) + a] = F.tree.nodes[nd].c[a];
+        re[nd] = F.tree.nodes[nd].re;
+    }
+    std::vector<float4> eq((size_t)nodes * FF_NE), chk((size_t)nodes * FF_NC);
+    std::vector<int> eq_pt((size_t)nodes * FF_NE);
+    for (int nd = 0; nd < nodes; ++nd) {
+        float w;
+        const int id = P + nd;
+        std::memcpy(&w, &id, sizeof(float));
+        for (int e = 0; e < FF_NE; ++e) {
+            eq[(size_t)nd * FF_NE + e] = make_float4((float)(re[nd] * ue[3 * e]), (float)(re[nd] * ue[3 * e + 1]),
+                                                     (float)(re[nd] * ue[3 * e + 2]), 0.f);
+            eq_pt[(size_t)nd * FF_NE + e] = nd * FF_NE + e;
+        }
+        for (int c = 0; c < FF_NC; ++c)
+            chk[(size_t)nd * FF_NC + c] =
+                make_float4((float)(FF_CHECK * re[nd] * uc[3 * c]), (float)(FF_CHECK * re[nd] * uc[3 * c + 1]),
+                            (float)(FF_CHECK * re[nd] * uc[3 * c + 2]), w);
+    }
+    std::vector<float4> tpos(ctx->sumM), tff(ctx->sumM);
+    CK(cudaMemcpy(tpos.data(), ctx->tgt_pos_d, sizeof(float4) * ctx->sumM, cudaMemcpyDeviceToHost));
+    std::vector<int> tperm(ctx->sumM);
+    int t = 0;
+    for (int q = 0; q < P; ++q) {
+        const int b = F.tree.order[q];
+        float w;
+        std::memcpy(&w, &q, sizeof(float));
+        for (int i = ctx->tgt_off[b]; i < ctx->tgt_off[b + 1]; ++i, ++t) {
+            tff[t] = make_float4(tpos[i].x, tpos[i].y, tpos[i].z, w);
+            tperm[t] = i;
+        }
+    }
+    F.seg_rec0_h.resize(P + nodes);
+    F.seg_rec1_h.resize(P + nodes);
+    for (int q = 0; q < P; ++q) {
+        const int b = F.tree.order[q];
+        F.seg_rec0_h[q] = ctx->rec_off[b];
+        F.seg_rec1_h[q] = ctx->rec_off[b + 1];  // padded to a multiple of 4 (zero-strength padding records)
+    }
+    for (int nd = 0; nd < nodes; ++nd) {
+        F.seg_rec0_h[P + nd] = ctx->nrec + nd * FF_NE;
+        F.seg_rec1_h[P + nd] = ctx->nrec + (nd + 1) * FF_NE;
+    }
+    const int R = ctx->opt.max_rhs;
+    F.rec_floats = std::max(pair_record_floats(D, R, 0), D == 3 ? pair_record_floats(D, R, 1) : 0);
+    CK(ctx->alloc(&F.PinvT, PinvT.size()));
+    CK(ctx->alloc(&F.centres, cen.size()));
+    CK(ctx->alloc(&F.re, re.size()));
+    CK(ctx->alloc(&F.eq_pos, eq.size()));
+    CK(ctx->alloc(&F.eq_pt, eq_pt.size()));
+    CK(ctx->alloc(&F.chk_pos, chk.size()));
+    CK(ctx->alloc(&F.tgt, tff.size()));
+    CK(ctx->alloc(&F.tperm, tperm.size()));
+    CK(ctx->alloc(&F.seg_rec0, F.seg_rec0_h.size()));
+    CK(ctx->alloc(&F.seg_rec1, F.seg_rec1_h.size()));
+    CK(ctx->alloc(&F.rec, (size_t)(ctx->nrec + (size_t)nodes * FF_NE) * F.rec_floats));
+    CK(ctx->alloc(&F.ucheck, (size_t)R * nodes * FF_NC * D));
+    CK(ctx->alloc(&F.mu, (size_t)R * nodes * FF_NE * D));
+    CK(cudaMemcpy(F.PinvT, PinvT.data(), sizeof(double) * PinvT.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(F.centres, cen.data(), sizeof(double) * cen.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(F.re, re.data(), sizeof(double) * re.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(F.eq_pos, eq.data(), sizeof(float4) * eq.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(F.eq_pt, eq_pt.data(), sizeof(int) * eq_pt.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(F.chk_pos, chk.data(), sizeof(float4) * chk.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(F.tgt, tff.data(), sizeof(float4) * tff.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(F.tperm, tperm.data(), sizeof(int) * tperm.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(F.seg_rec0, F.seg_rec0_h.data(), sizeof(int) * F.seg_rec0_h.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(F.seg_rec1, F.seg_rec1_h.data(), sizeof(int) * F.seg_rec1_h.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemset(F.rec, 0, sizeof(float) * (size_t)(ctx->nrec + (size_t)nodes * FF_NE) * F.rec_floats));
+    F.ready = true;
+    return MFS_OK;
 }
 
 static mfs_status setup_impl(mfs_ctx *ctx, mfs_kind kind, const mfs_bodies *bodies, int32_t num_shapes,
@@ -1497,6 +1925,7 @@ static mfs_status setup_impl(mfs_ctx *ctx, mfs_kind kind, const mfs_bodies *bodi
     CK(cudaEventCreate(&ctx->ev1));
     CK(cudaEventCreate(&ctx->evp0));
     CK(cudaEventCreate(&ctx->evp1));
+    if (ctx->opt.farfield) CKS(ff_setup(ctx, st));
     CK(cudaStreamSynchronize(st));
     ctx->ms_setup = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return MFS_OK;
@@ -1586,6 +2015,10 @@ mfs_status mfs_setup(mfs_ctx **out, mfs_kind kind, const mfs_bodies *bodies, int
         ctx->opt.restart > 1023 || !(ctx->opt.mu > 0.0) || !(ctx->opt.gmres_tol >= 0.0) ||
         ctx->opt.precision < 0 || ctx->opt.precision > 3 || !(ctx->opt.eps_trunc >= 0.0)) {
         g_setup_error = "mfs_setup: invalid options";
+        return MFS_ERR_INVALID_ARG;
+    }
+    if (ctx->opt.farfield != 0 && (ctx->opt.farfield != 1 || (ctx->opt.precision != 0 && ctx->opt.precision != 2))) {
+        g_setup_error = "mfs_setup: farfield must be 0 or 1, and 1 needs precision 0 or 2 (FP32 pair sums)";
         return MFS_ERR_INVALID_ARG;
     }
     if (ctx->opt.max_iter > ctx->opt.restart) {
@@ -1756,6 +2189,14 @@ static mfs_status finish_info(mfs_ctx *ctx, mfs_solve_info *info, const SolveSta
         info->ms_solve = ms;
         info->ms_pairs = ctx->pair_ms_acc;
         info->pairs = pair_count(ctx, 0) * ss.matvecs + (rhs_pairs ? pair_count(ctx, 1) : 0.0);
+        info->pairs_evaluated = info->pairs;
+        if (ctx->ff.ready) {  // what the treecode's launches evaluated for the same sums
+            auto evaluated = [&](int include_self) {
+                const auto it = ctx->ff.plans.find(forward_variant(ctx, nrhs) * 2 + include_self);
+                return it == ctx->ff.plans.end() ? 0.0 : it->second.pairs_up + it->second.pairs_ev;
+            };
+            info->pairs_evaluated = evaluated(0) * ss.matvecs + (rhs_pairs ? evaluated(1) : 0.0);
+        }
     }
     if (ss.breakdown) {
         ctx->last_error = "GMRES breakdown: non-finite residual";

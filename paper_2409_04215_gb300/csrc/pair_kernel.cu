@@ -101,13 +101,37 @@ __device__ __forceinline__ int tile_of_unit(const PairTile *tiles, int ntiles, l
 }
 
 // The stage that starts at global unit u (u < uend), at most max_blocks blocks long.
-__device__ __forceinline__ Stage make_stage(const PairTile *tiles, int ntiles, const long long *blk_off,
-                                            const int *src_off, long long u, long long uend, int max_blocks,
-                                            int hint_tile) {
+__device__ __forceinline__ Stage make_stage(const PairTile *tiles, int ntiles, const PairGeom &geo, long long u,
+                                            long long uend, int max_blocks, int hint_tile) {
     Stage st;
     int t = hint_tile;
     if (t < 0 || !(tiles[t].u0 <= u && u < tiles[t].u1)) t = tile_of_unit(tiles, ntiles, u);
     const PairTile tl = tiles[t];
+    const long long seg_end_u = tl.u1 < uend ? tl.u1 : uend;
+    if (tl.L0 >= 0) {  // interaction list: the entry e with lst_cum[e] <= u < lst_cum[e + 1]
+        int lo = tl.L0, hi = tl.L1 - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (geo.lst_cum[mid] <= u) lo = mid; else hi = mid - 1;
+        }
+        const int seg = geo.lst_seg[lo];
+        const int blk = (int)(u - geo.lst_cum[lo]);
+        const int seg_blocks = (int)(geo.lst_cum[lo + 1] - geo.lst_cum[lo]);
+        int n = seg_blocks - blk;
+        if (n > max_blocks) n = max_blocks;
+        if (n > seg_end_u - u) n = (int)(seg_end_u - u);
+        st.tile = t;
+        st.body = seg;
+        st.rec0 = geo.seg_rec0[seg] + blk * MFS_BS;
+        int rec_end = geo.seg_rec0[seg] + (blk + n) * MFS_BS;
+        if (rec_end > geo.seg_rec1[seg]) rec_end = geo.seg_rec1[seg];
+        st.nrec = rec_end - st.rec0;
+        st.u = u;
+        st.nblk = n;
+        return st;
+    }
+    const long long *blk_off = geo.blk_off;
+    const int *src_off = geo.src_off;
     long long gbl = blk_off[tl.B0] + (u - tl.u0);
     if (tl.skip >= 0 && gbl >= blk_off[tl.skip]) gbl += blk_off[tl.skip + 1] - blk_off[tl.skip];
     int lo = tl.B0, hi = tl.B1 - 1;  // body with blk_off[b] <= gbl
@@ -118,8 +142,7 @@ __device__ __forceinline__ Stage make_stage(const PairTile *tiles, int ntiles, c
     const int b = lo;
     const int blk = (int)(gbl - blk_off[b]);
     const int body_blocks = (int)(blk_off[b + 1] - blk_off[b]);
-    const long long seg_end = tl.u1 < uend ? tl.u1 : uend;
-    const long long rem = seg_end - u;
+    const long long rem = seg_end_u - u;
     int n = body_blocks - blk;
     if (n > max_blocks) n = max_blocks;
     if (n > rem) n = (int)rem;
@@ -945,7 +968,7 @@ __global__ void __launch_bounds__(NT, MINB) pair_sum_kernel(PairGeom geo, PairWo
     __syncthreads();
 
     const PairTile *tiles = work.tiles;
-    Stage cur = make_stage(tiles, work.ntiles, geo.blk_off, geo.src_off, ubeg, uend, Cfg::STAGE_BLOCKS, -1);
+    Stage cur = make_stage(tiles, work.ntiles, geo, ubeg, uend, Cfg::STAGE_BLOCKS, -1);
     const int first_tile = cur.tile;
     if (tid == 0) {
         mbar_arrive_expect_tx(&bars[0], (uint32_t)(cur.nrec * REC * 4));
@@ -982,7 +1005,7 @@ __global__ void __launch_bounds__(NT, MINB) pair_sum_kernel(PairGeom geo, PairWo
                 while (hint < work.ntiles && tiles[hint].u1 <= unext) ++hint;
                 if (hint >= work.ntiles) hint = -1;
             }
-            nxt = make_stage(tiles, work.ntiles, geo.blk_off, geo.src_off, unext, uend, Cfg::STAGE_BLOCKS, hint);
+            nxt = make_stage(tiles, work.ntiles, geo, unext, uend, Cfg::STAGE_BLOCKS, hint);
             if (tid == 0) {
                 mbar_arrive_expect_tx(&bars[buf ^ 1], (uint32_t)(nxt.nrec * REC * 4));
                 bulk_g2s(smem + (buf ^ 1) * SREC * REC, geo.src + (size_t)nxt.rec0 * REC,
@@ -1103,7 +1126,7 @@ __global__ void __launch_bounds__(1024) pair_epilogue_kernel(PairWork work, cons
             }
         }
         const int h = c / D, d = c % D;
-        const size_t o = ((size_t)h * ntargets + t) * D + d;
+        const size_t o = ((size_t)h * ntargets + (work.tperm ? work.tperm[t] : t)) * D + d;
         const double b = base ? beta * base[o] : 0.0;
         out[o] = b + scale * v;
     }
@@ -1504,6 +1527,7 @@ __global__ void prep_kernel(const double *targets, int nt, const double *sources
         tl.u1 = tl.u0 + nblk;
         tl.gA = (int)(((tl.u0 + 1) * G - 1) / W);
         tl.gB = (int)((tl.u1 * G - 1) / W);
+        tl.L0 = tl.L1 = -1;
         tiles[t] = tl;
     }
     if (i0 == 0) {

@@ -1,0 +1,119 @@
+"""The far-field accelerator of the pair sums (mfs_options.farfield = 1): an equivalent-source treecode,
+the GPU counterpart of the FMM the paper uses for its large runs (Sec. 4).
+
+Its sums are an approximation of the direct sums, so the oracle here is the direct sum itself: the
+treecode's matvec of Eq. 2esysprec and its all-pairs right-hand side (Eq. stou0) are held to the
+oracle's FP64 direct sums (relative 2-norm 1e-6, the matvec bar) on a 400-body cluster of Type T
+ellipsoids, on sampled targets of the 10 000-body cluster of Sec. 4.2, against the GPU's own direct
+sums on several suspensions and on the Laplace kernel, and its mobility solve to the stored 100-sphere
+oracle solution (1e-5).
+"""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from mfs_inputs import make_workload  # noqa: E402
+from oracle import Problem  # noqa: E402
+
+from test_gpu_parity import _ctx, _rel  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+
+
+def _rigid_field(pr, wl, seed):
+    """A rigid motion of every body at its collocation points, v + omega x (x - c) (Eq. Kdef)."""
+    V = np.random.default_rng(seed).standard_normal((pr.P, 6))
+    return np.concatenate([(V[k, :3] + np.cross(V[k, 3:], pr.X[k] - wl.centres[k])).reshape(-1)
+                           for k in range(pr.P)])
+
+
+def test_farfield_matvec_and_rhs_type_t_cluster():
+    wl = make_workload("ellipsoidT5000_mobility", count=400, n_v=16)
+    pr = Problem(wl)
+    ctx = _ctx(wl, farfield=1)
+    bodies = list(range(pr.P))
+    gam = _rigid_field(pr, wl, 1)
+    y = ctx.matvec(torch.tensor(gam.reshape(1, -1, 3), device="cuda")).cpu().numpy().reshape(-1)
+    assert _rel(y, pr.matvec(bodies, gam)) < 1e-6
+    s = np.random.default_rng(2).standard_normal((1, ctx.sum_N, 3))
+    u = ctx.pair_sum(torch.tensor(s, device="cuda"), include_self=True).cpu().numpy().reshape(-1)
+    ref = np.concatenate(pr.pair_sum(bodies, pr.split(bodies, s.reshape(-1), on="proxy"), include_self=True))
+    assert _rel(u, ref) < 1e-6
+    ctx.close()
+
+
+def test_farfield_matches_direct_on_suspensions_and_rhs():
+    """Several suspensions (one of a single body: an empty interaction list), 4 right-hand sides:
+    treecode against the direct GPU sums, white-noise strengths."""
+    wl = make_workload("batched256_mobility", num_suspensions=6, p_lo=1, p_hi=40, m=120, n=60, seed=9)
+    direct, tree = _ctx(wl), _ctx(wl, farfield=1)
+    s = torch.tensor(np.random.default_rng(3).standard_normal((4, direct.sum_N, 3)), device="cuda")
+    for include_self in (False, True):
+        a = direct.pair_sum(s, include_self=include_self).cpu().numpy()
+        b = tree.pair_sum(s, include_self=include_self).cpu().numpy()
+        for h in range(4):
+            assert _rel(b[h].reshape(-1), a[h].reshape(-1)) < 1e-6, (include_self, h)
+    direct.close()
+    tree.close()
+
+
+def test_farfield_laplace_elastance():
+    wl = make_workload("sphere100_elastance", m=300, n=150)
+    direct, tree = _ctx(wl), _ctx(wl, farfield=1)
+    s = torch.tensor(np.random.default_rng(4).standard_normal((1, direct.sum_N, 1)), device="cuda")
+    a = direct.pair_sum(s, include_self=True).cpu().numpy().reshape(-1)
+    b = tree.pair_sum(s, include_self=True).cpu().numpy().reshape(-1)
+    assert _rel(b, a) < 1e-6
+    Q = torch.tensor(wl.Q[None], device="cuda")
+    Va, _ = direct.solve_elastance(Q)
+    Vb, info = tree.solve_elastance(Q)
+    assert info.converged and _rel(Vb.cpu().numpy(), Va.cpu().numpy()) < 1e-5
+    direct.close()
+    tree.close()
+
+
+def test_farfield_sphere100_solve_against_golden():
+    g = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                    "sphere100_mobility_oracle.json")))
+    wl = make_workload("sphere100_mobility")
+    ctx = _ctx(wl, farfield=1)
+    U, W, info = ctx.solve_mobility(torch.tensor(wl.F, device="cuda"), torch.tensor(wl.T, device="cuda"))
+    assert info.converged
+    got = np.concatenate([U.cpu().numpy()[0], W.cpu().numpy()[0]], 1)
+    assert _rel(got, np.concatenate([np.array(g["U"]), np.array(g["Omega"])], 1)) < 1e-5
+    assert info.pairs_evaluated < info.pairs  # the treecode evaluated fewer pairs than the direct sums hold
+    ctx.close()
+
+
+def test_farfield_type_t_10000_sampled():
+    """Sec. 4.2's 10 000-ellipsoid cluster at its full discretisation (N_v = 34): the treecode matvec on
+    three sampled target bodies against the oracle's sums over all 9 999 other bodies."""
+    wl = make_workload("ellipsoidT10000_mobility")
+    ctx = _ctx(wl, farfield=1, max_iter=60, restart=60)
+    pr = Problem(wl)
+    bodies = list(range(pr.P))
+    gam = _rigid_field(pr, wl, 5)
+    y = ctx.matvec(torch.tensor(gam.reshape(1, -1, 3), device="cuda")).cpu().numpy().reshape(-1)
+    g = pr.split(bodies, gam)
+    sample = [0, 4321, 9999]
+    lam_hat = {k: pr.pinv_apply(k, g[k], project=True) for k in bodies}
+    ref = pr.pair_sum(bodies, [lam_hat[k] for k in bodies], include_self=False, target_bodies=sample)
+    got = pr.split(bodies, y)
+    num = sum(np.sum((got[k] - g[k] - r) ** 2) for k, r in zip(sample, ref))
+    den = sum(np.sum((g[k] + r) ** 2) for k, r in zip(sample, ref))
+    assert np.sqrt(num / den) < 1e-6
+    ctx.close()
