@@ -10,8 +10,17 @@ any size.
   gradient of L = sum |U_k|^2 equals 2 x the velocities and rotations of a forward solve driven by
   (F, T) = (U, 0).
 * 256 suspensions x 4 right-hand sides: two sampled suspensions (the smallest and one of about 20
-  bodies) against oracle solves of each right-hand side.
+  bodies) against oracle solves of each right-hand side run here, and 16 suspensions (the largest, the
+  two with the most spheroids, sizes spread over the rest) against the stored oracle solves of
+  tests/golden, every right-hand side, element-wise.
+* 1000 spheroids, the solve: the first 100 bodies of the grown cluster (true surface gaps U[0.05,0.5])
+  at the full discretisation, (U, Omega) within 1e-5 of the stored oracle solve.
+* 200 spheres, the adjoint against the oracle: the 24 spheres nearest the centre of the 200-sphere
+  box, M = 800, N = 400: the centre, force and torque gradients within 1e-4 of the oracle's adjoint.
 """
+
+import json
+import os
 
 import numpy as np
 import pytest
@@ -106,4 +115,76 @@ def test_batched256_sampled_suspensions():
             Ur, Wr, _ = pr.solve_mobility(sub.F[h], sub.T[h], tol=1e-12)
             got = np.concatenate([U[h, b0:b1], W[h, b0:b1]], 1)
             assert _rel(got, np.concatenate([Ur, Wr], 1)) < 1e-5, (s, h)
+    ctx.close()
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _element_rel(got, ref):
+    """max |got - ref| / max |ref| (element-wise agreement on the scale of the solution)."""
+    return float(np.abs(got - ref).max() / np.abs(ref).max())
+
+
+def test_batched256_sixteen_suspensions_against_golden():
+    from paper_2409_04215_gb300 import MFS
+
+    g = json.load(open(os.path.join(GOLDEN, "batched256_mobility_oracle.json")))
+    wl = make_workload("batched256_mobility")
+    ctx = MFS.from_workload(wl, max_iter=100, restart=100)
+    U, W, info = ctx.solve_mobility(torch.tensor(wl.F, device="cuda"), torch.tensor(wl.T, device="cuda"))
+    assert info.converged
+    U, W = U.cpu().numpy(), W.cpu().numpy()
+    sizes = np.diff(wl.body_offsets)
+    chosen = sorted(int(s) for s in g["suspensions"])
+    assert len(chosen) == 16 and int(np.argmax(sizes)) in chosen
+    assert max(g["suspensions"][str(s)]["spheroids"] for s in chosen) >= 30
+    for s in chosen:
+        ref = g["suspensions"][str(s)]
+        b0, b1 = wl.body_offsets[s], wl.body_offsets[s + 1]
+        for h in range(4):
+            got = np.concatenate([U[h, b0:b1], W[h, b0:b1]], 1)
+            want = np.concatenate([np.array(ref["U"][h]), np.array(ref["Omega"][h])], 1)
+            assert _element_rel(got, want) < 1e-5, (s, h, _element_rel(got, want))
+    ctx.close()
+
+
+def test_spheroid1000_sub100_solve_against_golden():
+    from paper_2409_04215_gb300 import MFS
+
+    g = json.load(open(os.path.join(GOLDEN, "spheroid1000_sub100_mobility_oracle.json")))
+    wl = make_workload("spheroid1000_mobility").first_bodies(100)
+    ctx = MFS.from_workload(wl)
+    U, W, info = ctx.solve_mobility(torch.tensor(wl.F, device="cuda"), torch.tensor(wl.T, device="cuda"))
+    assert info.converged
+    got = np.concatenate([U.cpu().numpy()[0], W.cpu().numpy()[0]], 1)
+    want = np.concatenate([np.array(g["U"]), np.array(g["Omega"])], 1)
+    assert _rel(got, want) < 1e-5, _rel(got, want)
+    ctx.close()
+
+
+def _central_subset(wl, count):
+    """The `count` bodies of a one-suspension workload nearest the centre of its bounding box."""
+    from mfs_inputs.workloads import Workload
+
+    mid = 0.5 * (wl.centres.min(axis=0) + wl.centres.max(axis=0))
+    keep = np.sort(np.argsort(np.linalg.norm(wl.centres - mid, axis=1))[:count])
+    return Workload(f"{wl.name}[central {count}]", wl.kind, wl.shapes, wl.centres[keep], None,
+                    wl.shape_id[keep], np.array([0, count], np.int32), F=wl.F[:, keep], T=wl.T[:, keep],
+                    mu=wl.mu, seed=wl.seed)
+
+
+def test_sphere200_adjoint_subset_against_oracle():
+    from paper_2409_04215_gb300 import MFS
+
+    wl = _central_subset(make_workload("sphere200_adjoint"), 24)
+    ctx = MFS.from_workload(wl, gmres_tol=1e-10)
+    U, W, _ = ctx.solve_mobility(torch.tensor(wl.F[:1], device="cuda"), torch.tensor(wl.T[:1], device="cuda"))
+    dc, dF, dT = ctx.mobility_vjp(2.0 * U, torch.zeros_like(W), want_force_grads=True)
+    pr = Problem(wl)
+    Ur, Wr, _ = pr.solve_mobility(wl.F[0], wl.T[0], tol=1e-13)
+    gc, gF, gT = pr.mobility_vjp(wl.F[0], wl.T[0], 2.0 * Ur, np.zeros_like(Wr))
+    assert _element_rel(dc.cpu().numpy(), gc) < 1e-4
+    assert _element_rel(dF.cpu().numpy()[0], gF) < 1e-4
+    assert _element_rel(dT.cpu().numpy()[0], gT) < 1e-4
     ctx.close()
