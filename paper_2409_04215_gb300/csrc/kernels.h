@@ -70,7 +70,7 @@ cudaError_t splitk_reduce(int S, size_t mn, const double *P, float *C32, double 
 struct alignas(64) TcMap {
     unsigned char bytes[128];  // an encoded CUtensorMap
 };
-struct TcOperands {  // kernel parameter: TF32 pieces of the factor (b) and of the columns (a)
+struct TcOperands {  // kernel parameter: the factor as FP32 (hi, lo) planes (b[0], b[1]), the columns' TF32 pieces (a)
     TcMap b[3];
     TcMap a[3];
 };
@@ -79,14 +79,15 @@ bool make_tc_map(TcMap &out, const float *ptr, int rows, int ld, int box_rows);
 int tc_gemm_bn(int m, int pieces);
 int tc_gemm_chunks(int m, int n, int k, int sm_count, int pieces);
 int tc_gemm_sz(int k, int S);
-// P[z][m][n] = sum_{k in chunk z} A[m][k] B[n][k] as (hi, lo) float pairs, from `pieces` (2 or 3) TF32
-// pieces of each operand (maps b[0..pieces), a[0..pieces)); S from tc_gemm_chunks, P holds
+// P[z][m][n] = sum_{k in chunk z} A[m][k] B[n][k] as (hi, lo) float pairs, products of `pieces` (2 or 3)
+// TF32 pieces per operand: the factor B given as FP32 (hi, lo) planes (maps b[0], b[1]; cut into pieces
+// in shared memory), the columns A as pieces (maps a[0..pieces)); S from tc_gemm_chunks, P holds
 // tc_gemm_sz(k, S) * m * n pairs.
 cudaError_t tc_gemm(int pieces, const TcMap *b, const TcMap *a, int m, int n, int k, int S, float2 *P, int *err,
                     cudaStream_t st);
-// FP64 [rows][cols] -> pieces dst[p][cols][ld_dst] (transposed, zero K padding), p at offset p * pstride.
-cudaError_t split_pieces_transpose(const double *src, int rows, int cols, float *dst, int ld_dst, size_t pstride,
-                                   int pieces, cudaStream_t st);
+// FP64 [rows][cols] -> FP32 (hi, lo) planes dst[0 or 1][cols][ld_dst] (transposed, zero K padding).
+cudaError_t split_hilo_transpose(const double *src, int rows, int cols, float *dst, int ld_dst, size_t pstride,
+                                 cudaStream_t st);
 // pieces src[p][rows][ld_src] (first cols valid) -> dst[p][cols][ld_dst] (transposed, zero padding to
 // ld_dst >= rows), p at offsets p * sstride and p * dstride.
 cudaError_t transpose_pieces(const float *src, int rows, int cols, int ld_src, size_t sstride, float *dst, int ld_dst,

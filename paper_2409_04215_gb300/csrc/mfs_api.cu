@@ -45,10 +45,10 @@ struct FactorSet {
     bool built = false;
     ShapeDev dev{};
     bool tc_ready = false;
-    float *Utp = nullptr, *Wptp = nullptr, *Wrtp = nullptr;  // [piece][r or dN][ld]
+    float *Utp = nullptr, *Wptp = nullptr, *Wrtp = nullptr;  // FP32 (hi, lo) planes [2][r or dN][ld]
     size_t ut_stride = 0, wt_stride = 0;
     TcMap mU[3], mWp[3], mWr[3];
-    // the transposed apply (adjoint), built on first use: pieces of U [dM][ld2] and of W^T [r][ld2]
+    // the transposed apply (adjoint), built on first use: (hi, lo) planes of U [dM][ld2] and of W^T [r][ld2]
     bool tcT_ready = false;
     float *Un = nullptr, *WpT = nullptr, *WrT = nullptr;
     size_t un_stride = 0;
@@ -1025,19 +1025,19 @@ mfs_status ensure_transposed(mfs_ctx *ctx) {
         CK(ctx->alloc(&sh.PkT, need));
         CK(ctx->alloc(&sh.O64, (size_t)R * nb * m));
         FactorSet &fx = sh.fs[0];
-        if (fx.tc_ready) {  // tensor cores: the factor pieces transposed (exact), their maps, chunk results
+        if (fx.tc_ready) {  // tensor cores: the factor planes transposed (exact), their maps, chunk results
             const int np = sh.pieces;
             fx.un_stride = (size_t)m * sh.ld2;
-            CK(ctx->alloc(&fx.Un, np * fx.un_stride));
-            CK(ctx->alloc(&fx.WpT, np * fx.wt_stride));
-            CK(ctx->alloc(&fx.WrT, np * fx.wt_stride));
-            // U^T pieces [r][ld1] -> U pieces [dM][ld2]; W pieces [dN][ld2] -> W^T pieces [r][ld2]
-            CK(transpose_pieces(fx.Utp, n, m, sh.ld1, fx.ut_stride, fx.Un, sh.ld2, fx.un_stride, np, 0));
-            CK(transpose_pieces(fx.Wptp, n, n, sh.ld2, fx.wt_stride, fx.WpT, sh.ld2, fx.wt_stride, np, 0));
-            CK(transpose_pieces(fx.Wrtp, n, n, sh.ld2, fx.wt_stride, fx.WrT, sh.ld2, fx.wt_stride, np, 0));
+            CK(ctx->alloc(&fx.Un, 2 * fx.un_stride));
+            CK(ctx->alloc(&fx.WpT, 2 * fx.wt_stride));
+            CK(ctx->alloc(&fx.WrT, 2 * fx.wt_stride));
+            // U^T planes [r][ld1] -> U planes [dM][ld2]; W planes [dN][ld2] -> W^T planes [r][ld2]
+            CK(transpose_pieces(fx.Utp, n, m, sh.ld1, fx.ut_stride, fx.Un, sh.ld2, fx.un_stride, 2, 0));
+            CK(transpose_pieces(fx.Wptp, n, n, sh.ld2, fx.wt_stride, fx.WpT, sh.ld2, fx.wt_stride, 2, 0));
+            CK(transpose_pieces(fx.Wrtp, n, n, sh.ld2, fx.wt_stride, fx.WrT, sh.ld2, fx.wt_stride, 2, 0));
             CK(cudaDeviceSynchronize());
             bool enc = true;
-            for (int p = 0; p < np; ++p)
+            for (int p = 0; p < 2; ++p)
                 enc = enc && make_tc_map(fx.mUn[p], fx.Un + p * fx.un_stride, m, sh.ld2, 128) &&
                       make_tc_map(fx.mWpT[p], fx.WpT + p * fx.wt_stride, n, sh.ld2, 128) &&
                       make_tc_map(fx.mWrT[p], fx.WrT + p * fx.wt_stride, n, sh.ld2, 128);
@@ -1400,27 +1400,27 @@ static mfs_status build_shape_factors(mfs_ctx *ctx, cusolverDnHandle_t solver, i
         return MFS_ERR_ILL_CONDITIONED;
     }
     if (want_tc) {
-        // K-major TF32 pieces: U^T [r][ld1], Wp^T and Wr^T [dN][ld2], from the FP64 factors; zero K padding
+        // K-major FP32 (hi, lo) planes: U^T [r][ld1], Wp^T and Wr^T [dN][ld2], from the FP64 factors; zero
+        // K padding.  The kernel cuts them into TF32 pieces in shared memory.
         sh.pieces = ctx->opt.tensor_cores == 2 ? 2 : 3;
-        const int np = sh.pieces;
         sh.ld1 = (m + 31) / 32 * 32;
         sh.ld2 = (n + 31) / 32 * 32;
         fx.ut_stride = (size_t)n * sh.ld1;
         fx.wt_stride = (size_t)n * sh.ld2;
-        ok = ctx->alloc(&fx.Utp, np * fx.ut_stride) == cudaSuccess &&
-             ctx->alloc(&fx.Wptp, np * fx.wt_stride) == cudaSuccess &&
-             ctx->alloc(&fx.Wrtp, np * fx.wt_stride) == cudaSuccess;
+        ok = ctx->alloc(&fx.Utp, 2 * fx.ut_stride) == cudaSuccess &&
+             ctx->alloc(&fx.Wptp, 2 * fx.wt_stride) == cudaSuccess &&
+             ctx->alloc(&fx.Wrtp, 2 * fx.wt_stride) == cudaSuccess;
         if (!ok) {
             ctx->last_error = "device allocation for the tensor-core factors failed";
             return MFS_ERR_OOM;
         }
-        CK(split_pieces_transpose(sd.U64, m, n, fx.Utp, sh.ld1, fx.ut_stride, np, st));
-        CK(split_pieces_transpose(sd.Wp64, n, n, fx.Wptp, sh.ld2, fx.wt_stride, np, st));
-        CK(split_pieces_transpose(sd.Wr64, n, n, fx.Wrtp, sh.ld2, fx.wt_stride, np, st));
+        CK(split_hilo_transpose(sd.U64, m, n, fx.Utp, sh.ld1, fx.ut_stride, st));
+        CK(split_hilo_transpose(sd.Wp64, n, n, fx.Wptp, sh.ld2, fx.wt_stride, st));
+        CK(split_hilo_transpose(sd.Wr64, n, n, fx.Wrtp, sh.ld2, fx.wt_stride, st));
         CK(cudaStreamSynchronize(st));
         const int box = 128;  // factor rows per CTA (MMA M)
         bool enc = true;
-        for (int p = 0; p < np; ++p)
+        for (int p = 0; p < 2; ++p)
             enc = enc && make_tc_map(fx.mU[p], fx.Utp + p * fx.ut_stride, n, sh.ld1, box) &&
                   make_tc_map(fx.mWp[p], fx.Wptp + p * fx.wt_stride, n, sh.ld2, box) &&
                   make_tc_map(fx.mWr[p], fx.Wrtp + p * fx.wt_stride, n, sh.ld2, box);

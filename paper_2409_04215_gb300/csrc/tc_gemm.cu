@@ -16,13 +16,17 @@
 //
 // The factor (B: U^T or W^T of the one-body SVD, Eq. pseudo) is the MMA's M side (128 rows per CTA),
 // the gathered columns (A) its N side (<= 256), so a handful of bodies still fills the 128-row MMA.
+// The factor is the bulk of the traffic, so it is stored as an FP32 pair (hi, lo) = (fl(x), fl(x - hi))
+// (8 bytes per element, exact to about 2^-48) and cut into its TF32 pieces in shared memory after the
+// TMA load; the columns arrive as pieces.
 //
-// Per CTA (128 threads): warp 0 lane 0 issues TMA loads (cp.async.bulk.tensor, 128-byte swizzle)
-// into a two-stage ring, warp 1 lane 0 issues the MMAs and commits each stage back to the loader,
-// warp 2 owns the TMEM allocation, and all four warps read the accumulators with tcgen05.ld (warp w
-// reads TMEM lanes 32w..32w+31) and write the (hi, lo) partials.  Every wait is bounded; on a timeout the
-// CTA records an error flag, waits for the MMAs it issued, agrees (block vote), frees its TMEM and
-// returns.
+// Per CTA (192 threads): warp 0 lane 0 issues TMA loads (cp.async.bulk.tensor, 128-byte swizzle)
+// into a two-stage ring, warps 2 to 5 cut each landed factor tile (hi, lo) into its TF32 pieces in
+// place (the three tiles share one layout, so the cut is element-wise at equal offsets) and release it
+// to warp 1 lane 0, which issues the MMAs and commits each stage back to the loader; warp 2 owns the
+// TMEM allocation, and warps 0 to 3 read the accumulators with tcgen05.ld (warp w reads TMEM lanes
+// 32w..32w+31) and write the (hi, lo) partials.  Every wait is bounded; on a timeout the CTA records an
+// error flag, waits for the MMAs it issued, agrees (block vote), frees its TMEM and returns.
 #include <cuda.h>
 
 #include <cstring>
@@ -37,6 +41,8 @@ constexpr int BM = 128;              // factor rows per CTA (MMA M)
 constexpr int BK = 32;               // K elements per stage (128 bytes: one swizzle row)
 constexpr int STAGES = 2;
 constexpr int B_TILE = BM * BK * 4;  // bytes of one 128 x 32 FP32 factor tile (16 KB)
+constexpr int THREADS = 192;         // warps 0-3: TMA, MMA, TMEM, epilogue; warps 2-5: cutting pieces
+constexpr int CUTTERS = 128;         // threads of warps 2-5
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     // K-major operand, 128-byte swizzle: start address >> 4 (bits 0-13), leading byte offset unused
@@ -150,21 +156,22 @@ __device__ __forceinline__ void split_pieces(double x, int pieces, float *p) {
 }
 }  // namespace tc
 
-// grid: (ceil(n / 128), ceil(m / BN), chunks); block 128; dynamic smem tc_gemm_smem(BN, PIECES)
+// grid: (ceil(n / 128), ceil(m / BN), chunks); block tc::THREADS; dynamic smem tc_gemm_smem(BN, PIECES)
 template <int PIECES>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(tc::THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ TcOperands ops, int m, int n, int k, int kchunk, int BN, int tmem_cols,
                    int nacc, float2 *P, int *err) {
     using namespace tc;
     using TT = Terms<PIECES>;
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
+    __shared__ __align__(8) uint64_t full_bar[STAGES], cut_bar[STAGES], empty_bar[STAGES], done_bar;
     __shared__ uint32_t tmem_base_sh;
     // 1024-byte aligned tiles (128-byte swizzle atoms are 8 rows x 128 bytes)
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     const uint32_t a_tile = (uint32_t)BN * BK * 4;
     const uint32_t stage_bytes = PIECES * (B_TILE + a_tile);
+    const uint32_t load_bytes = 2 * B_TILE + PIECES * a_tile;  // factor (hi, lo), column pieces
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n0 = blockIdx.x * BM, m0 = blockIdx.y * BN;
     const int kb0 = blockIdx.z * kchunk;
@@ -175,6 +182,7 @@ __global__ void __launch_bounds__(128, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full_bar[s], 1);
+            mbar_init(&cut_bar[s], CUTTERS / 32);  // one arrival per cutting warp
             mbar_init(&empty_bar[s], 1);
         }
         mbar_init(&done_bar, 1);
@@ -199,14 +207,45 @@ __global__ void __launch_bounds__(128, 1)
             if (!ok) break;
             const uint32_t st = base + s * stage_bytes;
             const uint32_t fb = smem_u32(&full_bar[s]);
-            mbar_arrive_expect_tx(&full_bar[s], stage_bytes);
+            mbar_arrive_expect_tx(&full_bar[s], load_bytes);
             const int kx = kb0 + i * BK;
 #pragma unroll
-            for (int p = 0; p < PIECES; ++p) {
+            for (int p = 0; p < 2; ++p)  // factor hi and lo into piece slots 0 and 1
                 tma_load_2d(st + p * B_TILE, reinterpret_cast<const CUtensorMap *>(&ops.b[p]), kx, n0, fb);
+#pragma unroll
+            for (int p = 0; p < PIECES; ++p)
                 tma_load_2d(st + PIECES * B_TILE + p * a_tile, reinterpret_cast<const CUtensorMap *>(&ops.a[p]), kx,
                             m0, fb);
+        }
+    } else if (warp >= 2) {  // cut the landed factor tile (hi, lo) into TF32 pieces, in place
+        const int ct = threadIdx.x - 64;  // 0 .. CUTTERS - 1
+        for (int i = 0; i < nk && ok; ++i) {
+            const int s = i % STAGES;
+            ok = mbar_wait_bounded(&full_bar[s], (uint32_t)((i / STAGES) & 1), err, limit);
+            if (!ok) break;
+            float4 *t0 = reinterpret_cast<float4 *>(smem_raw + (base - raw) + s * stage_bytes);
+            float4 *t1 = t0 + B_TILE / 16;
+            float4 *t2 = t1 + B_TILE / 16;
+            for (int v = ct; v < B_TILE / 16; v += CUTTERS) {
+                const float4 h = t0[v], l = t1[v];
+                float p0[4], p1[4], p2[4];
+                const float hv[4] = {h.x, h.y, h.z, h.w}, lv[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    float q[3];
+                    tc::split_pieces_df(hv[e], lv[e], PIECES, q);
+                    p0[e] = q[0];
+                    p1[e] = q[1];
+                    p2[e] = q[2];
+                }
+                t0[v] = make_float4(p0[0], p0[1], p0[2], p0[3]);
+                t1[v] = make_float4(p1[0], p1[1], p1[2], p1[3]);
+                if (PIECES == 3) t2[v] = make_float4(p2[0], p2[1], p2[2], p2[3]);
             }
+            // the pieces are read by the tensor cores (async proxy) after this warp's release
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive_expect_tx(&cut_bar[s], 0);
         }
     } else if (warp == 1 && lane == 0) {  // MMA issuer
         const uint32_t idesc = instr_desc_tf32(BM, BN);
@@ -215,7 +254,7 @@ __global__ void __launch_bounds__(128, 1)
             const int s = i % STAGES;
             // the leading term of stage i goes to main accumulator i % nacc (TMEM columns BN * (i % nacc) ...)
             const uint32_t dmain = tmem + (uint32_t)(BN * (i % nacc));
-            ok = mbar_wait_bounded(&full_bar[s], (uint32_t)((i / STAGES) & 1), err, limit);
+            ok = mbar_wait_bounded(&cut_bar[s], (uint32_t)((i / STAGES) & 1), err, limit);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t st = base + s * stage_bytes;
@@ -242,7 +281,7 @@ __global__ void __launch_bounds__(128, 1)
     // everybody: wait for the accumulators (bounded), then agree on success
     bool good = mbar_wait_bounded(&done_bar, 0u, err, limit);
     good = __syncthreads_and(good && ok) != 0;
-    if (good) {
+    if (good && warp < 4) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int row = n0 + 32 * warp + lane;  // TMEM lane = factor row
         const int used = min(nacc, nk);          // main accumulators written by at least one stage
@@ -277,18 +316,21 @@ __global__ void __launch_bounds__(128, 1)
 // ---------------------------------------------------------------------------
 // Operand pieces
 // ---------------------------------------------------------------------------
-// dst[p][c][r] = piece p of src[r][c] (an FP64 factor stored [rows][cols] becomes K-major [cols][ld_dst]);
-// columns rows..ld_dst of each piece are zero.
-__global__ void split_pieces_transpose_kernel(const double *src, int rows, int cols, float *dst, int ld_dst,
-                                              size_t pstride, int pieces) {
+// dst[0][c][r] = fl(src[r][c]), dst[1][c][r] = fl(src[r][c] - dst[0][c][r]): an FP64 factor stored
+// [rows][cols] as K-major FP32 (hi, lo) planes [cols][ld_dst], columns rows..ld_dst zero.
+__global__ void split_hilo_transpose_kernel(const double *src, int rows, int cols, float *dst, int ld_dst,
+                                            size_t pstride) {
     const size_t total = (size_t)cols * ld_dst;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const int c = (int)(i / ld_dst), r = (int)(i % ld_dst);
-        float p[3] = {0.f, 0.f, 0.f};
-        if (r < rows) tc::split_pieces(src[(size_t)r * cols + c], pieces, p);  // zero K padding otherwise
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-            if (q < pieces) dst[q * pstride + i] = p[q];
+        float hi = 0.f, lo = 0.f;
+        if (r < rows) {
+            const double x = src[(size_t)r * cols + c];
+            hi = (float)x;
+            lo = (float)(x - (double)hi);
+        }
+        dst[i] = hi;
+        dst[pstride + i] = lo;
     }
 }
 
@@ -388,11 +430,10 @@ cudaError_t transpose_pieces(const float *src, int rows, int cols, int ld_src, s
     return cudaGetLastError();
 }
 
-cudaError_t split_pieces_transpose(const double *src, int rows, int cols, float *dst, int ld_dst, size_t pstride,
-                                   int pieces, cudaStream_t st) {
+cudaError_t split_hilo_transpose(const double *src, int rows, int cols, float *dst, int ld_dst, size_t pstride,
+                                 cudaStream_t st) {
     if (cols == 0) return cudaSuccess;
-    if (pieces < 2 || pieces > 3) return cudaErrorInvalidValue;
-    split_pieces_transpose_kernel<<<1024, 256, 0, st>>>(src, rows, cols, dst, ld_dst, pstride, pieces);
+    split_hilo_transpose_kernel<<<1024, 256, 0, st>>>(src, rows, cols, dst, ld_dst, pstride);
     return cudaGetLastError();
 }
 
@@ -515,7 +556,8 @@ static cudaError_t tc_layout(int BN, int &nacc, int &cols) {
     const size_t smem = tc_gemm_smem(BN, PIECES);
     int &resident = cache[BN / 16];
     if (resident == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, tc_gemm_kernel<PIECES>, 128, smem);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, tc_gemm_kernel<PIECES>, tc::THREADS,
+                                                                      smem);
         if (e != cudaSuccess) return e;
         if (resident < 1) return cudaErrorInvalidConfiguration;
     }
@@ -543,7 +585,8 @@ static cudaError_t tc_gemm_launch(const TcMap *b, const TcMap *a, int m, int n, 
     std::memcpy(ops.b, b, PIECES * sizeof(TcMap));
     std::memcpy(ops.a, a, PIECES * sizeof(TcMap));
     dim3 grid((n + tc::BM - 1) / tc::BM, (m + BN - 1) / BN, Sz);
-    tc_gemm_kernel<PIECES><<<grid, 128, tc_gemm_smem(BN, PIECES), st>>>(ops, m, n, k, kchunk, BN, cols, nacc, P, err);
+    tc_gemm_kernel<PIECES><<<grid, tc::THREADS, tc_gemm_smem(BN, PIECES), st>>>(ops, m, n, k, kchunk, BN, cols, nacc, P,
+                                                                            err);
     return cudaGetLastError();
 }
 
