@@ -137,6 +137,21 @@ __device__ __forceinline__ float tf32_rna(float x) {
     return __uint_as_float(t);
 }
 
+// The nearest TF32 value (10 explicit mantissa bits), ties away from zero, by integer operations on the
+// bits of a finite x: half a TF32 unit in the last place added to the magnitude, the 13 low bits cleared
+// (a carry into the exponent is the rounding up into the next binade).
+__device__ __forceinline__ float tf32_round_bits(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xffffe000u);
+}
+
+// The same split as split_pieces_df with the integer rounding (the cut inside the GEMM kernel).
+__device__ __forceinline__ void split_pieces_bits(float hi, float lo, int pieces, float *p) {
+    p[0] = tf32_round_bits(hi);
+    const float rem = (hi - p[0]) + lo;
+    p[1] = tf32_round_bits(rem);
+    p[2] = pieces == 3 ? tf32_round_bits(rem - p[1]) : 0.f;
+}
+
 // (hi + lo) ~ p[0] + p[1] (+ p[2]) with FP32 arithmetic only: hi - tf32(hi) is exact.
 __device__ __forceinline__ void split_pieces_df(float hi, float lo, int pieces, float *p) {
     p[0] = tf32_rna(hi);
@@ -233,7 +248,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     float q[3];
-                    tc::split_pieces_df(hv[e], lv[e], PIECES, q);
+                    tc::split_pieces_bits(hv[e], lv[e], PIECES, q);
                     p0[e] = q[0];
                     p1[e] = q[1];
                     p2[e] = q[2];
