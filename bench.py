@@ -82,6 +82,9 @@ def _args():
                     help="secondary workloads: also time the FP64 reference GPU solve (precision = 1)")
     ap.add_argument("--farfield", action="store_true",
                     help="secondary workloads: forward pair sums through the equivalent-source treecode (farfield = 1)")
+    ap.add_argument("--farfield-separation", type=float, default=3.0,
+                    help="with --farfield: equivalent radii a target keeps from a node it sees through its "
+                         "equivalent points (mfs_options.farfield_separation)")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 2, 3],
                     help="mfs_options.precision of a secondary measurement (3: compensated double-FP32 pair "
                          "sums); any value but 0 runs the named workload as a secondary line, not the benchmark")
@@ -314,6 +317,7 @@ def secondary(args):
         opts["precision"] = args.precision
     if args.farfield:
         opts["farfield"] = 1
+        opts["farfield_separation"] = args.farfield_separation
     ctx = MFS.from_workload(wl, profile=1, **opts)
     setup_s = time.perf_counter() - t0
     laplace = wl.kind == "laplace"

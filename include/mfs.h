@@ -112,6 +112,9 @@ typedef struct {
                              near bodies (direct, FP32 pair kernel).  Relative accuracy of the sums about
                              1e-7; the pair work drops from O(P^2) to about O(P log P).  Needs precision 0 or
                              2; the transposed sums and mfs_evaluate* stay direct. */
+    double farfield_separation; /* farfield = 1: a target uses a node's equivalent points when it is at least
+                                   this many equivalent radii from the node's centre; default 3, allowed
+                                   [2.5, 10] (2.5 = the check sphere; smaller is faster and less accurate). */
 } mfs_options;
 
 typedef struct {

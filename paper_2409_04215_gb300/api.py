@@ -96,6 +96,7 @@ class Options(ctypes.Structure):
         ("pair_variant", ctypes.c_int32),
         ("graphs", ctypes.c_int32),
         ("farfield", ctypes.c_int32),
+        ("farfield_separation", ctypes.c_double),
     ]
 
 

@@ -7,7 +7,8 @@
 // FF_NE equivalent point sources on a sphere of radius r_e around its centre whose field reproduces
 // that of the node's proxy sources outside it.  The equivalent strengths are the least-squares fit
 // of the sources' field on FF_NC check points at radius FF_CHECK * r_e (the "upward" step, run on the
-// device), and a target at least FF_KAPPA * r_e from a node's centre sees the node through them.
+// device), and a target at least kappa * r_e from a node's centre (kappa = farfield_separation, 3 by
+// default) sees the node through them.
 // Targets nearer than that see the node's children, down to the bodies' own proxy points.  Both the
 // fit's right-hand side and the final sums are ordinary pair sums over interaction lists, so the
 // device work is the pair kernel plus one FP64 matrix product per apply.
@@ -126,19 +127,19 @@ void ff_build_tree(int P, const double *centres, const double *rsrc, int S, cons
 }
 
 void ff_interaction_list(const FFTree &t, int root, const std::vector<int> &tbodies, const double *centres,
-                         const double *rtgt, int self_skip, std::vector<int> &segs) {
+                         const double *rtgt, double kappa, int self_skip, std::vector<int> &segs) {
     const int P = (int)t.order.size();
     std::vector<int> stack{root};
     while (!stack.empty()) {
         const int ni = stack.back();
         stack.pop_back();
         const FFNode &n = t.nodes[ni];
-        // far: every target point of the set is at least FF_KAPPA r_e from the node's centre
+        // far: every target point of the set is at least kappa r_e from the node's centre
         bool far = true;
         for (int b : tbodies) {
             double d2 = 0.0;
             for (int a = 0; a < 3; ++a) d2 += (centres[3 * b + a] - n.c[a]) * (centres[3 * b + a] - n.c[a]);
-            if (std::sqrt(d2) - rtgt[b] < FF_KAPPA * n.re) {
+            if (std::sqrt(d2) - rtgt[b] < kappa * n.re) {
                 far = false;
                 break;
             }

@@ -143,8 +143,8 @@ constexpr int FF_NE = 196;            // equivalent points per node (a Fibonacci
 constexpr int FF_NC = 392;            // check points per node (radius FF_CHECK * r_e), least-squares fit
 constexpr double FF_CHECK = 2.5;      // check radius / equivalent radius
 constexpr double FF_SRC_RATIO = 0.83; // a node's source radius / its equivalent radius
-constexpr double FF_KAPPA = 3.0;      // a target this many equivalent radii from a node's centre sees the node
-                                      // through its equivalent points
+// (a target at least mfs_options.farfield_separation equivalent radii from a node's centre sees the node
+// through its equivalent points)
 struct FFNode {
     double c[3] = {0, 0, 0};  // centre
     double rs = 0.0;          // radius of the node's proxy sources about c
@@ -166,7 +166,7 @@ void ff_build_tree(int P, const double *centres, const double *rsrc, int S, cons
 // body's proxy points as its tree position q < P, a node's equivalent points as P + node.  With
 // self_skip, a single target body's own proxy points are left out.
 void ff_interaction_list(const FFTree &t, int root, const std::vector<int> &tbodies, const double *centres,
-                         const double *rtgt, int self_skip, std::vector<int> &segs);
+                         const double *rtgt, double kappa, int self_skip, std::vector<int> &segs);
 // mu[h][node][e][d] *= re[node] (the fit was made on the unit sphere; the kernels are homogeneous of
 // degree -1).
 cudaError_t ff_scale(double *mu, const double *re, int nodes, int per_node, int nrhs, cudaStream_t st);

@@ -735,7 +735,7 @@ mfs_status ff_get_plan(mfs_ctx *ctx, int variant, int include_self, mfs_ctx::Far
                              tb.clear();
                              for (int q = g0; q <= g1; ++q) tb.push_back(F.tree.order[q]);
                              ff_interaction_list(F.tree, F.tree.roots[suspension_of[tb[0]]], tb, ctx->centres.data(),
-                                                 F.rtgt.data(), !include_self, segs);
+                                                 F.rtgt.data(), ctx->opt.farfield_separation, !include_self, segs);
                          },
                          pl.ev, &pl.lst_seg_ev, &pl.lst_cum_ev, pl.pairs_ev));
     pl.ev.include_self = include_self;
@@ -1295,6 +1295,7 @@ void mfs_default_options(mfs_options *opt) {
     opt->pair_variant = -1;
     opt->graphs = 1;
     opt->farfield = 0;
+    opt->farfield_separation = 3.0;
 }
 
 int32_t mfs_abi_version(void) { return MFS_ABI_VERSION; }
@@ -2019,6 +2020,10 @@ mfs_status mfs_setup(mfs_ctx **out, mfs_kind kind, const mfs_bodies *bodies, int
     }
     if (ctx->opt.farfield != 0 && (ctx->opt.farfield != 1 || (ctx->opt.precision != 0 && ctx->opt.precision != 2))) {
         g_setup_error = "mfs_setup: farfield must be 0 or 1, and 1 needs precision 0 or 2 (FP32 pair sums)";
+        return MFS_ERR_INVALID_ARG;
+    }
+    if (ctx->opt.farfield == 1 && !(ctx->opt.farfield_separation >= FF_CHECK && ctx->opt.farfield_separation <= 10.0)) {
+        g_setup_error = "mfs_setup: farfield_separation must lie in [2.5, 10]";
         return MFS_ERR_INVALID_ARG;
     }
     if (ctx->opt.max_iter > ctx->opt.restart) {
