@@ -104,6 +104,11 @@ cudaError_t gather_rotate_pieces(int D, const double *gamma, int sum_MD, const i
 cudaError_t gemm_splitk(int m, int n, int k, int S, const float *A, const float *B, double *P, float *C32,
                         double *C64, cudaStream_t st, bool trans_b = false);  // trans_b: B stored [n][k]
 cudaError_t gemm_rm64(int m, int n, int k, const double *A, const double *B, double *C, cudaStream_t st);
+// The same product split over K into S chunks (gemm_rm64_chunks), partials P [S][m][n] summed in chunk
+// order into C (deterministic); S = 1 is gemm_rm64.
+int gemm_rm64_chunks(int m, int n, int k, int sm_count);
+cudaError_t gemm_rm64_splitk(int m, int n, int k, int S, const double *A, const double *B, double *P, double *C,
+                             cudaStream_t st);
 // Scatter: lambda (FP64 [nrhs][sum_N][D]) at the columns' bodies = R_k * Lcol (rotate back).
 cudaError_t scatter_rotate(int D, const float *L, const double *L64, const int *col_body, const int *col_rhs,
                            const int *body_src_off, const float *rot, const double *rot64, int ncols, int dN,

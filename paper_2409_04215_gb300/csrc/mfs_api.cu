@@ -183,6 +183,7 @@ struct mfs_ctx {
         int rec_floats = 0;
         double *ucheck = nullptr;                    // [max_rhs][nodes FF_NC][D]
         double *mu = nullptr;                        // [max_rhs][nodes FF_NE][D]
+        double *fit_chunks = nullptr;                // split-K partials of the fit product
         struct Plan {
             PairPlan up, ev;
             int *lst_seg_up = nullptr, *lst_seg_ev = nullptr;
@@ -792,7 +793,8 @@ mfs_status ff_pair_apply(mfs_ctx *ctx, int variant, const double *strength, doub
     const PairWork wu = work_of(pl->up);
     CKS(ff_launch(ctx, variant, g, wu, st));
     CK(pair_epilogue(D, nrhs, wu, nullptr, 0.0, 1.0, F.ucheck, nodes * FF_NC, st));
-    CK(gemm_rm64(nrhs * nodes, D * FF_NE, D * FF_NC, F.ucheck, F.PinvT, F.mu, st));
+    const int Sk = gemm_rm64_chunks(nrhs * nodes, D * FF_NE, D * FF_NC, ctx->sm_count);
+    CK(gemm_rm64_splitk(nrhs * nodes, D * FF_NE, D * FF_NC, Sk, F.ucheck, F.PinvT, F.fit_chunks, F.mu, st));
     CK(ff_scale(F.mu, F.re, nodes, D * FF_NE, nrhs, st));
     CK(pack_sources(D, nrhs, vv[variant].packed, F.eq_pos, F.eq_pt, F.mu, nodes * FF_NE, nodes * FF_NE,
                     F.rec + (size_t)ctx->nrec * REC, st));
@@ -1678,6 +1680,14 @@ static mfs_status ff_setup(mfs_ctx *ctx, cudaStream_t st) {
     CK(ctx->alloc(&F.rec, (size_t)(ctx->nrec + (size_t)nodes * FF_NE) * F.rec_floats));
     CK(ctx->alloc(&F.ucheck, (size_t)R * nodes * FF_NC * D));
     CK(ctx->alloc(&F.mu, (size_t)R * nodes * FF_NE * D));
+    {
+        size_t chunk_doubles = 1;
+        for (int h = 1; h <= R; ++h) {
+            const int S = gemm_rm64_chunks(h * nodes, D * FF_NE, D * FF_NC, ctx->sm_count);
+            if (S > 1) chunk_doubles = std::max(chunk_doubles, (size_t)S * h * nodes * FF_NE * D);
+        }
+        CK(ctx->alloc(&F.fit_chunks, chunk_doubles));
+    }
     CK(cudaMemcpy(F.PinvT, PinvT.data(), sizeof(double) * PinvT.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(F.centres, cen.data(), sizeof(double) * cen.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(F.re, re.data(), sizeof(double) * re.size(), cudaMemcpyHostToDevice));

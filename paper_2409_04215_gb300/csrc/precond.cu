@@ -305,31 +305,35 @@ cudaError_t scatter_rotate(int D, const float *L, const double *L64, const int *
 
 // ---------------------------------------------------------------------------
 // Row-major GEMM C[m][n] = A[m][k] B[k][n]: 64x64 output tile, 16-deep k slices in shared
-// memory, 4x4 outputs per thread (256 threads).  FP32 (matvec) and FP64 (reference path).
+// memory, 4x4 outputs per thread (256 threads).  FP32 (matvec) and FP64 (reference path, far-field
+// fits).  With gridDim.z > 1, CTA z sums only k in [z kchunk, (z + 1) kchunk) and writes its partial
+// product to C + z m n (a split over K, summed afterwards in a fixed order).
 // ---------------------------------------------------------------------------
 template <typename TT>
 __global__ void __launch_bounds__(256) gemm_rm_kernel(int m, int n, int k, const TT *__restrict__ A,
-                                                      const TT *__restrict__ B, TT *__restrict__ C) {
+                                                      const TT *__restrict__ B, TT *__restrict__ C, int kchunk) {
     constexpr int BM = 64, BN = 64, BK = 16;
     __shared__ TT As[BK][BM + 4];
     __shared__ TT Bs[BK][BN + 4];
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int kbeg = blockIdx.z * kchunk, kend = min(k, kbeg + kchunk);
+    C += (size_t)blockIdx.z * m * n;
     TT acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0;
-    for (int k0 = 0; k0 < k; k0 += BK) {
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
         for (int e = threadIdx.x; e < BM * BK; e += 256) {  // A tile: rows m0.., cols k0..
             const int r = e / BK, c = e % BK;
             const int gm = m0 + r, gk = k0 + c;
-            As[c][r] = (gm < m && gk < k) ? A[(size_t)gm * k + gk] : TT(0);
+            As[c][r] = (gm < m && gk < kend) ? A[(size_t)gm * k + gk] : TT(0);
         }
         for (int e = threadIdx.x; e < BK * BN; e += 256) {
             const int r = e / BN, c = e % BN;
             const int gk = k0 + r, gn = n0 + c;
-            Bs[r][c] = (gk < k && gn < n) ? B[(size_t)gk * n + gn] : TT(0);
+            Bs[r][c] = (gk < kend && gn < n) ? B[(size_t)gk * n + gn] : TT(0);
         }
         __syncthreads();
 #pragma unroll
@@ -474,14 +478,42 @@ cudaError_t gemm_splitk(int m, int n, int k, int S, const float *A, const float 
 cudaError_t gemm_rm(int m, int n, int k, const float *A, const float *B, float *C, cudaStream_t st) {
     if (m == 0 || n == 0) return cudaSuccess;
     dim3 grid((n + 63) / 64, (m + 63) / 64);
-    gemm_rm_kernel<float><<<grid, 256, 0, st>>>(m, n, k, A, B, C);
+    gemm_rm_kernel<float><<<grid, 256, 0, st>>>(m, n, k, A, B, C, k);
     return cudaGetLastError();
 }
 
 cudaError_t gemm_rm64(int m, int n, int k, const double *A, const double *B, double *C, cudaStream_t st) {
     if (m == 0 || n == 0) return cudaSuccess;
     dim3 grid((n + 63) / 64, (m + 63) / 64);
-    gemm_rm_kernel<double><<<grid, 256, 0, st>>>(m, n, k, A, B, C);
+    gemm_rm_kernel<double><<<grid, 256, 0, st>>>(m, n, k, A, B, C, k);
+    return cudaGetLastError();
+}
+
+int gemm_rm64_chunks(int m, int n, int k, int sm_count) {
+    const int tiles = ((n + 63) / 64) * ((m + 63) / 64);
+    int s = (2 * sm_count) / std::max(tiles, 1);  // about two CTAs per SM
+    s = std::min(s, (k + 127) / 128);               // chunks of at least 128 of K
+    return std::max(s, 1);
+}
+
+__global__ void sum_chunks_kernel(int S, size_t mn, const double *__restrict__ P, double *__restrict__ C) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < mn; i += (size_t)gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int z = 0; z < S; ++z) v += P[(size_t)z * mn + i];
+        C[i] = v;
+    }
+}
+
+cudaError_t gemm_rm64_splitk(int m, int n, int k, int S, const double *A, const double *B, double *P, double *C,
+                             cudaStream_t st) {
+    if (m == 0 || n == 0) return cudaSuccess;
+    if (S <= 1) return gemm_rm64(m, n, k, A, B, C, st);
+    const int kchunk = ((k + S - 1) / S + 15) / 16 * 16;
+    const int Sz = (k + kchunk - 1) / kchunk;
+    dim3 grid((n + 63) / 64, (m + 63) / 64, Sz);
+    gemm_rm_kernel<double><<<grid, 256, 0, st>>>(m, n, k, A, B, P, kchunk);
+    const size_t mn = (size_t)m * n;
+    sum_chunks_kernel<<<(unsigned)std::min<size_t>((mn + 255) / 256, 4096), 256, 0, st>>>(Sz, mn, P, C);
     return cudaGetLastError();
 }
 
