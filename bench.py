@@ -597,12 +597,16 @@ def main():
                     "speedup_vs_direct_solve": (ms / args.steps) / ms_ff}
         ctx_ff.close()
 
-    # the FP32 peak checked on this GPU now: f32x2 and scalar FMA on independent chains (outside the
-    # timed region; about 30 ms of device time)
+    # the FP32 peak checked on this GPU now: f32x2 and scalar FMA on independent chains, and f32x2
+    # whose three operands are all fresh registers (the operand pattern of the pair kernel's inner
+    # loop); outside the timed region, about 50 ms of device time
     from paper_2409_04215_gb300.api import fp32_fma_rate
 
     probe = {"ffma2_tflops": fp32_fma_rate(True), "ffma_tflops": fp32_fma_rate(False),
-             "how": "mfs_fp32_fma_rate: 8 independent fma chains per thread, 32 warps per SM, one ~15 ms launch"}
+             "ffma2_distinct_operands_tflops": fp32_fma_rate(mode=2),
+             "how": "mfs_fp32_fma_rate: 8 independent fma chains per thread, 32 warps per SM, one ~15 ms launch "
+                    "each; ffma2/ffma with loop-constant b and c, ffma2_distinct_operands with three operand "
+                    "registers rewritten every step"}
     roofline["peak_probe"] = probe
     roofline["frac_of_probe"] = achieved / probe["ffma2_tflops"]
 

@@ -331,13 +331,19 @@ const char *mfs_pair_variant_info(int32_t index, int32_t *d, int32_t *nrhs, int3
 /*
  * mfs_fp32_fma_rate -- measured FP32 FMA throughput of the current device (TFLOP/s, an FMA counted as
  * two flops), the denominator check for the pair kernel's share of peak.  The paper has no
- * counterpart.  packed = 0 times scalar fma.rn.f32, packed = 1 the f32x2 form the Stokeslet kernel
- * issues; each on 8 independent chains per thread, 32 resident warps per SM, one launch of about
+ * counterpart.  Each mode runs 8 dependency chains per thread of 256-thread CTAs, one launch of about
  * 10-20 ms after a short warm-up launch, timed with CUDA events on `stream` (the call synchronises
- * that stream).  Allocates and frees a few KB (stream-ordered).  *tflops is set to 0 on failure;
- * packed outside {0, 1} or a NULL tflops returns MFS_ERR_INVALID_ARG.
+ * that stream):
+ *   mode 0: scalar fma.rn.f32, a <- a b + c with loop-constant b and c, 32 resident warps per SM;
+ *   mode 1: the f32x2 form the Stokeslet kernel issues, otherwise as mode 0;
+ *   mode 2: f32x2 whose three operands are distinct registers rewritten every step (no operand is a
+ *           loop constant, as in the pair kernel's inner loop), 32 warps per SM;
+ *   mode 3: mode 1 at 8 resident warps per SM (two per scheduler, the Stokeslet kernel's occupancy);
+ *   mode 4: mode 2 at 8 resident warps per SM.
+ * Allocates and frees a few KB (stream-ordered).  *tflops is set to 0 on failure; a mode outside
+ * 0..4 or a NULL tflops returns MFS_ERR_INVALID_ARG.
  */
-mfs_status mfs_fp32_fma_rate(int32_t packed, double *tflops, void *stream);
+mfs_status mfs_fp32_fma_rate(int32_t mode, double *tflops, void *stream);
 
 /*
  * mfs_selftest_bounded_wait -- exercises the error path of the kernels' bounded device waits (the

@@ -201,14 +201,15 @@ def pair_variants():
         i += 1
 
 
-def fp32_fma_rate(packed: bool = True, stream=None) -> float:
+def fp32_fma_rate(packed: bool = True, stream=None, mode: int | None = None) -> float:
     """Measured FP32 FMA throughput of the current CUDA device in TFLOP/s (mfs_fp32_fma_rate):
-    f32x2 fma when packed, else scalar fma.  Synchronises the stream."""
+    f32x2 fma when packed, else scalar fma; `mode` (0-4, see mfs.h) overrides `packed` and selects
+    the operand pattern and occupancy.  Synchronises the stream."""
     lib = load_library()
     out = ctypes.c_double()
     torch = _torch()
     st = _stream_ptr(stream, torch.device("cuda", torch.cuda.current_device()))
-    rc = lib.mfs_fp32_fma_rate(1 if packed else 0, ctypes.byref(out), st)
+    rc = lib.mfs_fp32_fma_rate((1 if packed else 0) if mode is None else int(mode), ctypes.byref(out), st)
     if rc != MFS_OK:
         raise MFSError(rc, "mfs_fp32_fma_rate failed")
     return out.value

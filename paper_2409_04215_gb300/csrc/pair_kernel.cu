@@ -1641,7 +1641,6 @@ namespace fmaprobe {
 
 constexpr int kChains = 8;     // independent dependency chains per thread
 constexpr int kThreads = 256;  // threads per CTA
-constexpr int kCtasPerSm = 4;  // 32 resident warps per SM
 constexpr int kIters = 1 << 18;
 
 // a <- a * b + c on kChains independent chains; b < 1 and c > 0 keep every value near c / (1 - b)
@@ -1682,26 +1681,66 @@ __global__ void __launch_bounds__(kThreads) fma_rate_kernel(float b, float c, in
     }
 }
 
+// f32x2 FMAs whose three operands are distinct registers, each rewritten every step (no operand
+// is a loop constant, as in the pair kernel's inner loop, where dx, sc, lambda and the sums all
+// change).  Half of the chains hold values near 1 (x), half values near t = 1e-15 (y):
+// x' = x1 * y + x2 stays near x2 and y' = y1 * y2 + y3 near y3, so every value stays a normal
+// FP32 number.  Two register banks alternate, so the kChains FMAs of a step are independent.
+__global__ void __launch_bounds__(kThreads) fma_rate_distinct_kernel(float t, int iters, float *sink) {
+    constexpr int H = kChains / 2;
+    const float seed = 0.5f + 1e-3f * (float)(threadIdx.x & 31);
+    u64 a[kChains], b[kChains];
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        a[i] = f2_pack(seed + (float)i, seed - 0.25f * (float)i);
+        a[H + i] = f2_pack(t * (seed + (float)i), t * (seed + 0.5f * (float)i));
+    }
+    for (int it = 0; it < iters; it += 2) {
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+            b[i] = f2_fma(a[(i + 1) % H], a[H + (i + 2) % H], a[(i + 3) % H]);
+            b[H + i] = f2_fma(a[H + (i + 1) % H], a[H + (i + 2) % H], a[H + (i + 3) % H]);
+        }
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+            a[i] = f2_fma(b[(i + 1) % H], b[H + (i + 2) % H], b[(i + 3) % H]);
+            a[H + i] = f2_fma(b[H + (i + 1) % H], b[H + (i + 2) % H], b[H + (i + 3) % H]);
+        }
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) {
+        float lo, hi;
+        f2_unpack(a[i], lo, hi);
+        s += lo + hi;
+    }
+    if (s == -1.0f) sink[blockIdx.x] = s;
+}
+
 }  // namespace fmaprobe
 }  // namespace mfs
 
-extern "C" mfs_status mfs_fp32_fma_rate(int32_t packed, double *tflops, void *stream) {
+extern "C" mfs_status mfs_fp32_fma_rate(int32_t mode, double *tflops, void *stream) {
     using namespace mfs::fmaprobe;
-    if (!tflops || (packed != 0 && packed != 1)) return MFS_ERR_INVALID_ARG;
+    if (!tflops || mode < 0 || mode > 4) return MFS_ERR_INVALID_ARG;
     *tflops = 0.0;
     cudaStream_t st = (cudaStream_t)stream;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
         return MFS_ERR_CUDA;
-    const int grid = sms * kCtasPerSm;
+    // modes 0-2: 4 CTAs of 8 warps per SM (32 warps); modes 3-4: one CTA (8 warps, 2 per scheduler)
+    const int grid = sms * (mode >= 3 ? 1 : 4);
+    const bool distinct = (mode == 2 || mode == 4);
     float *sink = nullptr;
     if (cudaMallocAsync(&sink, sizeof(float) * grid, st) != cudaSuccess) return MFS_ERR_OOM;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     mfs_status rc = MFS_ERR_CUDA;
     if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
         auto launch = [&](int iters) {
-            if (packed)
+            if (distinct)
+                fma_rate_distinct_kernel<<<grid, kThreads, 0, st>>>(1e-15f, iters, sink);
+            else if (mode != 0)
                 fma_rate_kernel<true><<<grid, kThreads, 0, st>>>(0.9999999f, 1e-7f, iters, sink);
             else
                 fma_rate_kernel<false><<<grid, kThreads, 0, st>>>(0.9999999f, 1e-7f, iters, sink);
@@ -1713,7 +1752,7 @@ extern "C" mfs_status mfs_fp32_fma_rate(int32_t packed, double *tflops, void *st
         float ms = 0.f;
         if (cudaGetLastError() == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
             cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms > 0.f) {
-            const double fmas = (double)grid * kThreads * kChains * (packed ? 2.0 : 1.0) * kIters;
+            const double fmas = (double)grid * kThreads * kChains * (mode != 0 ? 2.0 : 1.0) * kIters;
             *tflops = 2.0 * fmas / (ms * 1e-3) / 1e12;
             rc = MFS_OK;
         }

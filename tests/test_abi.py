@@ -63,7 +63,8 @@ def test_setup_rejects_bad_input_without_gpu(lib_path):
     assert rc == 1  # MFS_ERR_INVALID_ARG
     assert b"invalid" in lib.mfs_setup_error()
     val = ctypes.c_double(-1.0)
-    assert lib.mfs_fp32_fma_rate(2, ctypes.byref(val), None) == 1  # packed must be 0 or 1
+    assert lib.mfs_fp32_fma_rate(5, ctypes.byref(val), None) == 1  # mode must be 0..4
+    assert lib.mfs_fp32_fma_rate(-1, ctypes.byref(val), None) == 1
     assert lib.mfs_fp32_fma_rate(1, None, None) == 1
     assert lib.mfs_selftest_bounded_wait(2, 10, None) == 1  # arrive must be 0 or 1
     assert lib.mfs_selftest_bounded_wait(0, 0, None) == 1  # at least one poll
