@@ -152,7 +152,9 @@ mfs_status mfs_setup(mfs_ctx **out, mfs_kind kind, const mfs_bodies *bodies, int
                      void *stream);
 
 /* Move the bodies: new centres [P][3] (host or device).  One-body factors are reused
- * (they depend on shape and orientation only, Remark congruent). */
+ * (they depend on shape and orientation only, Remark congruent).  With farfield = 1 the treecode's
+ * tree, node geometry and interaction lists are rebuilt for the new positions (host work and a few
+ * uploads; captured graphs are dropped and recaptured on the next solve).  Synchronises the device. */
 mfs_status mfs_update_centers(mfs_ctx *ctx, const double *centers, void *stream);
 
 /*

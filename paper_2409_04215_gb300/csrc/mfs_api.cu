@@ -1532,30 +1532,13 @@ static void unit_fibonacci(int n, std::vector<double> &p) {
     }
 }
 
-// The far-field structures (opt.farfield = 1): the tree, the FP64 pseudo-inverse of the map from
-// equivalent strengths on the unit sphere to the field at the check points (truncated at 1e-12 of the
-// largest singular value; least squares, FF_NC > FF_NE), and the tree-ordered geometry.
-static mfs_status ff_setup(mfs_ctx *ctx, cudaStream_t st) {
+// The transposed pseudo-inverse of the check <- equivalent map on the unit sphere (raw kernel: 1/r or
+// (I + r r^T / r^2) / r), FP64, truncated at 1e-12 of the largest singular value; least squares
+// (FF_NC > FF_NE).  It depends on the kernel only, so a context computes it once.
+static mfs_status ff_unit_pinv(mfs_ctx *ctx, const std::vector<double> &ue, const std::vector<double> &uc,
+                               cudaStream_t st) {
     auto &F = ctx->ff;
-    const int P = ctx->P, D = ctx->D;
-    F.rsrc.assign(P, 0.0);
-    F.rtgt.assign(P, 0.0);
-    for (int k = 0; k < P; ++k) {
-        const ShapeHost &sh = ctx->shapes[ctx->shape_id[k]];
-        for (int j = 0; j < sh.N; ++j)
-            F.rsrc[k] = std::max(F.rsrc[k], std::sqrt(sh.Y0[3 * j] * sh.Y0[3 * j] + sh.Y0[3 * j + 1] * sh.Y0[3 * j + 1] +
-                                                      sh.Y0[3 * j + 2] * sh.Y0[3 * j + 2]));
-        for (int i = 0; i < sh.M; ++i)
-            F.rtgt[k] = std::max(F.rtgt[k], std::sqrt(sh.X0[3 * i] * sh.X0[3 * i] + sh.X0[3 * i + 1] * sh.X0[3 * i + 1] +
-                                                      sh.X0[3 * i + 2] * sh.X0[3 * i + 2]));
-    }
-    ff_build_tree(P, ctx->centres.data(), F.rsrc.data(), ctx->S, ctx->body_off.data(), F.tree);
-    const int nodes = F.nodes = (int)F.tree.nodes.size();
-
-    // check <- equivalent map on the unit sphere (raw kernel: 1/r or (I + r r^T / r^2) / r), column-major
-    std::vector<double> ue, uc;
-    unit_fibonacci(FF_NE, ue);
-    unit_fibonacci(FF_NC, uc);
+    const int D = ctx->D;
     const int m = D * FF_NC, n = D * FF_NE;
     std::vector<double> A((size_t)m * n);
     for (int i = 0; i < FF_NC; ++i)
@@ -1615,7 +1598,73 @@ static mfs_status ff_setup(mfs_ctx *ctx, cudaStream_t st) {
             for (int j = 0; j < n; ++j) o[j] += u * row[j];
         }
     }
+    CK(ctx->alloc(&F.PinvT, PinvT.size()));
+    CK(cudaMemcpy(F.PinvT, PinvT.data(), sizeof(double) * PinvT.size(), cudaMemcpyHostToDevice));
+    return MFS_OK;
+}
 
+// Frees the far-field structures that depend on the body centres (all but the pseudo-inverse) and
+// drops the captured graphs that hold their addresses.
+static void ff_release_geometry(mfs_ctx *ctx) {
+    auto &F = ctx->ff;
+    ctx->drop_graphs();
+    for (auto &kv : F.plans) {
+        auto &pl = kv.second;
+        for (PairPlan *pp : {&pl.up, &pl.ev}) {
+            ctx->release(pp->tiles);
+            ctx->release(pp->partial);
+            ctx->release(pp->direct);
+        }
+        ctx->release(pl.lst_seg_up);
+        ctx->release(pl.lst_cum_up);
+        ctx->release(pl.lst_seg_ev);
+        ctx->release(pl.lst_cum_ev);
+    }
+    F.plans.clear();
+    ctx->release(F.centres);
+    ctx->release(F.re);
+    ctx->release(F.eq_pos);
+    ctx->release(F.eq_pt);
+    ctx->release(F.chk_pos);
+    ctx->release(F.tgt);
+    ctx->release(F.tperm);
+    ctx->release(F.seg_rec0);
+    ctx->release(F.seg_rec1);
+    ctx->release(F.rec);
+    ctx->release(F.ucheck);
+    ctx->release(F.mu);
+    ctx->release(F.fit_chunks);
+    F.centres = F.ucheck = F.mu = F.fit_chunks = F.re = nullptr;
+    F.eq_pos = F.chk_pos = F.tgt = nullptr;
+    F.eq_pt = F.tperm = F.seg_rec0 = F.seg_rec1 = nullptr;
+    F.rec = nullptr;
+    F.ready = false;
+}
+
+// The far-field structures (opt.farfield = 1): the tree, the FP64 pseudo-inverse of the map from
+// equivalent strengths on the unit sphere to the field at the check points (ff_unit_pinv, once per
+// context), and the tree-ordered geometry (again after every mfs_update_centers).
+static mfs_status ff_setup(mfs_ctx *ctx, cudaStream_t st) {
+    auto &F = ctx->ff;
+    const int P = ctx->P, D = ctx->D;
+    F.rsrc.assign(P, 0.0);
+    F.rtgt.assign(P, 0.0);
+    for (int k = 0; k < P; ++k) {
+        const ShapeHost &sh = ctx->shapes[ctx->shape_id[k]];
+        for (int j = 0; j < sh.N; ++j)
+            F.rsrc[k] = std::max(F.rsrc[k], std::sqrt(sh.Y0[3 * j] * sh.Y0[3 * j] + sh.Y0[3 * j + 1] * sh.Y0[3 * j + 1] +
+                                                      sh.Y0[3 * j + 2] * sh.Y0[3 * j + 2]));
+        for (int i = 0; i < sh.M; ++i)
+            F.rtgt[k] = std::max(F.rtgt[k], std::sqrt(sh.X0[3 * i] * sh.X0[3 * i] + sh.X0[3 * i + 1] * sh.X0[3 * i + 1] +
+                                                      sh.X0[3 * i + 2] * sh.X0[3 * i + 2]));
+    }
+    ff_build_tree(P, ctx->centres.data(), F.rsrc.data(), ctx->S, ctx->body_off.data(), F.tree);
+    const int nodes = F.nodes = (int)F.tree.nodes.size();
+
+    std::vector<double> ue, uc;
+    unit_fibonacci(FF_NE, ue);
+    unit_fibonacci(FF_NC, uc);
+    if (!F.PinvT) CKS(ff_unit_pinv(ctx, ue, uc, st));  // independent of the centres: kept across moves
     // tree-ordered geometry and segments: proxy segment q (tree position) = body order[q], node segment
     // P + node = its equivalent points
     std::vector<double> cen(3 * (size_t)(P + nodes)), re(nodes);
@@ -1667,7 +1716,6 @@ static mfs_status ff_setup(mfs_ctx *ctx, cudaStream_t st) {
     }
     const int R = ctx->opt.max_rhs;
     F.rec_floats = std::max(pair_record_floats(D, R, 0), D == 3 ? pair_record_floats(D, R, 1) : 0);
-    CK(ctx->alloc(&F.PinvT, PinvT.size()));
     CK(ctx->alloc(&F.centres, cen.size()));
     CK(ctx->alloc(&F.re, re.size()));
     CK(ctx->alloc(&F.eq_pos, eq.size()));
@@ -1688,7 +1736,6 @@ static mfs_status ff_setup(mfs_ctx *ctx, cudaStream_t st) {
         }
         CK(ctx->alloc(&F.fit_chunks, chunk_doubles));
     }
-    CK(cudaMemcpy(F.PinvT, PinvT.data(), sizeof(double) * PinvT.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(F.centres, cen.data(), sizeof(double) * cen.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(F.re, re.data(), sizeof(double) * re.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(F.eq_pos, eq.data(), sizeof(float4) * eq.size(), cudaMemcpyHostToDevice));
@@ -2088,6 +2135,11 @@ mfs_status mfs_update_centers(mfs_ctx *ctx, const double *centers, void *stream)
         }
     CK(cudaMemcpyAsync(ctx->centres_d, ctx->centres.data(), sizeof(double) * 3 * ctx->P, cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
+    if (ctx->ff.ready) {  // the treecode's tree, node centres and interaction lists follow the bodies
+        CK(cudaDeviceSynchronize());
+        ff_release_geometry(ctx);
+        CKS(ff_setup(ctx, st));
+    }
     return MFS_OK;
 }
 

@@ -126,3 +126,70 @@ def test_farfield_type_t_10000_sampled():
     ed = err(_ctx(wl, max_iter=60, restart=60))
     print(f"10 000 ellipsoids, sampled matvec error: separation 3: {e3:.2e}, 2.5: {e25:.2e}, direct: {ed:.2e}")
     assert e3 < 1e-6 and e25 < 1e-6 and ed < 1e-6
+
+
+def test_farfield_follows_moved_bodies():
+    """mfs_update_centers with the treecode: the tree, node geometry and interaction lists are rebuilt,
+    so the matvec at the new positions matches a direct context moved the same way (and one set up
+    there), twice in a row, and a solve after the move matches the oracle's."""
+    wl = make_workload("sphere100_mobility", count=40, m=300, n=150, seed=21)
+    tree, direct = _ctx(wl, farfield=1), _ctx(wl)
+    s = torch.tensor(np.random.default_rng(22).standard_normal((1, tree.sum_N, 3)), device="cuda")
+    rng = np.random.default_rng(23)
+    centres = wl.centres.copy()
+    for step in range(2):
+        # a rigid shift of the whole cluster plus a shuffle of which body sits where (a new tree)
+        centres = centres[rng.permutation(len(centres))] + rng.standard_normal(3)
+        tree.update_centers(centres)
+        direct.update_centers(centres)
+        moved = make_workload("sphere100_mobility", count=40, m=300, n=150, seed=21)
+        moved.centres = centres
+        pr = Problem(moved)
+        # pair sums of white-noise strengths, and the matvec of a rigid motion (smooth: no amplification
+        # of FP32 rounding through the one-body pseudo-inverse)
+        a = direct.pair_sum(s, include_self=False).cpu().numpy().reshape(-1)
+        b = tree.pair_sum(s, include_self=False).cpu().numpy().reshape(-1)
+        assert _rel(b, a) < 1e-6, step
+        gam = torch.tensor(_rigid_field(pr, moved, 30 + step).reshape(1, -1, 3), device="cuda")
+        a = direct.matvec(gam).cpu().numpy().reshape(-1)
+        b = tree.matvec(gam).cpu().numpy().reshape(-1)
+        assert _rel(b, a) < 1e-6, step
+    U, W, info = tree.solve_mobility(torch.tensor(wl.F[:1], device="cuda"), torch.tensor(wl.T[:1], device="cuda"))
+    Ur, Wr, _ = pr.solve_mobility(wl.F[0], wl.T[0], tol=1e-12)
+    assert info.converged
+    got = np.concatenate([U.cpu().numpy()[0], W.cpu().numpy()[0]], 1)
+    assert _rel(got, np.concatenate([Ur, Wr], 1)) < 1e-5
+    tree.close()
+    direct.close()
+
+
+def test_farfield_dirichlet_and_adjoint():
+    """The other solves on the treecode's forward sums: resistance (Sec. 2.2) and the mobility adjoint
+    (its forward solve and right-hand side use the treecode; the transposed sums stay direct) against
+    the same solves with direct sums, and capacitance (Sec. 2.1) on the Laplace kernel."""
+    wl = make_workload("sphere100_mobility", count=40, m=300, n=150, seed=24)
+    direct, tree = _ctx(wl, gmres_tol=1e-9), _ctx(wl, farfield=1, gmres_tol=1e-9)
+    rng = np.random.default_rng(25)
+    Uin, Win = rng.standard_normal((1, wl.num_bodies, 3)), rng.standard_normal((1, wl.num_bodies, 3))
+    Fa, Ta, ia = direct.solve_resistance(Uin, Win)
+    Fb, Tb, ib = tree.solve_resistance(Uin, Win)
+    assert ia.converged and ib.converged
+    assert _rel(np.concatenate([Fb.numpy(), Tb.numpy()], 2), np.concatenate([Fa.numpy(), Ta.numpy()], 2)) < 1e-5
+    F, T = torch.tensor(wl.F[:1], device="cuda"), torch.tensor(wl.T[:1], device="cuda")
+    grads = []
+    for ctx in (direct, tree):
+        U, W, _ = ctx.solve_mobility(F, T)
+        dc, dF, dT = ctx.mobility_vjp(2.0 * U, 0.6 * W, want_force_grads=True)
+        grads.append(np.concatenate([dc.cpu().numpy().reshape(-1), dF.cpu().numpy().reshape(-1),
+                                     dT.cpu().numpy().reshape(-1)]))
+    assert _rel(grads[1], grads[0]) < 1e-4
+    direct.close()
+    tree.close()
+    lw = make_workload("sphere100_elastance", count=40, m=300, n=150)
+    direct, tree = _ctx(lw, gmres_tol=1e-9), _ctx(lw, farfield=1, gmres_tol=1e-9)
+    phi = np.random.default_rng(26).standard_normal((2, lw.num_bodies))
+    qa, _ = direct.solve_capacitance(phi)
+    qb, info = tree.solve_capacitance(phi)
+    assert info.converged and _rel(qb.numpy(), qa.numpy()) < 1e-5
+    direct.close()
+    tree.close()
