@@ -125,6 +125,8 @@ struct mfs_ctx {
 
     // work buffers
     float *rec_d = nullptr;      // packed source records (max_rhs)
+    int rec_floats = 0;          // floats per record allocated in rec_d (and recT_floats in recT_d)
+    int recT_floats = 0;
     double *lam_d = nullptr;     // [max_rhs][sumN][D]
     double *raw_d = nullptr;     // FP64 reference pair sums [max_rhs][sumM][D]
     std::map<int, PairPlan> plans;  // key: variant * 4 + include_self * 2 + transposed
@@ -165,6 +167,15 @@ struct mfs_ctx {
     // far field of the pair sums (opt.farfield = 1): equivalent-source treecode (farfield.cu)
     struct FarField {
         bool ready = false;
+        // the roles of the point sets: forward sums (proxy sources, collocation targets) or the
+        // adjoint's transposed sums (collocation sources, proxy targets)
+        bool src_colloc = false;
+        const float4 *src_pos = nullptr;             // [nsrc] body-local source positions
+        const int *rec_pt = nullptr;                 // [nrec] source record -> point (-1: padding)
+        const float4 *tgt_pos = nullptr;             // [ntgt] body-local target positions
+        const std::vector<int> *rec_off = nullptr;   // [P + 1] padded record offsets of the sources
+        const std::vector<int> *tgt_off = nullptr;   // [P + 1] target offsets
+        int nsrc = 0, nrec = 0, ntgt = 0;
         FFTree tree;
         int nodes = 0;
         std::vector<double> rsrc, rtgt;              // per body: radius of its proxy / collocation points
@@ -191,7 +202,7 @@ struct mfs_ctx {
             double pairs_up = 0.0, pairs_ev = 0.0;   // target-source pairs one application evaluates
         };
         std::map<int, Plan> plans;                   // key: variant * 2 + include_self
-    } ff;
+    } ff, ffT;                                       // forward sums; transposed sums (adjoint)
 
     int sm_count = 0;
     std::string last_error;
@@ -229,6 +240,8 @@ struct mfs_ctx {
         for (cudaEvent_t e : pev) cudaEventDestroy(e);
     }
 };
+
+static mfs_status ff_setup(mfs_ctx *ctx, mfs_ctx::FarField &F, cudaStream_t st);  // far-field structures
 
 namespace {
 
@@ -527,6 +540,9 @@ PairGeom geom_of(mfs_ctx *ctx) {
 cudaError_t pack_for(mfs_ctx *ctx, int variant, const double *strength, int nrhs, cudaStream_t st) {
     int vc = 0;
     const PairVariant *vv = pair_variants(&vc);
+    // the record buffer holds every layout this context's entries use; anything else is refused
+    if (pair_record_floats(ctx->D, nrhs, vv[variant].comp ? 2 : vv[variant].packed) > ctx->rec_floats)
+        return cudaErrorInvalidValue;
     if (vv[variant].comp)
         return pack_sources_comp(ctx->D, nrhs, ctx->src_local64_d, ctx->rec_pt_d, strength, ctx->sumN, ctx->nrec,
                                  ctx->rec_d, st);
@@ -545,8 +561,8 @@ __global__ void combine_raw_kernel(const double *raw, const double *base, double
     if (i < n) out[i] = (base ? beta * base[i] : 0.0) + scale * raw[i];
 }
 
-mfs_status ff_pair_apply(mfs_ctx *ctx, int variant, const double *strength, double *out, const double *base,
-                         double beta, double scale, int nrhs, int include_self, cudaStream_t st);
+mfs_status ff_pair_apply(mfs_ctx *ctx, mfs_ctx::FarField &F, int variant, const double *strength, double *out,
+                         const double *base, double beta, double scale, int nrhs, int include_self, cudaStream_t st);
 
 mfs_status pair_apply(mfs_ctx *ctx, const double *strength, double *out, const double *base, double beta,
                       double sign, int nrhs, int include_self, cudaStream_t st) {
@@ -567,7 +583,8 @@ mfs_status pair_apply(mfs_ctx *ctx, const double *strength, double *out, const d
         ctx->last_error = "no pair-kernel variant for this nrhs";
         return MFS_ERR_INVALID_ARG;
     }
-    if (ctx->ff.ready) return ff_pair_apply(ctx, variant, strength, out, base, beta, scale, nrhs, include_self, st);
+    if (ctx->ff.ready)
+        return ff_pair_apply(ctx, ctx->ff, variant, strength, out, base, beta, scale, nrhs, include_self, st);
     PairPlan *plan = nullptr;
     CKS(get_plan(ctx, variant, include_self, &plan));
     CK(pack_for(ctx, variant, strength, nrhs, st));
@@ -689,8 +706,8 @@ mfs_status build_plan_lists(mfs_ctx *ctx, int variant, int include_self, const s
 // The far-field plans of one pair-kernel variant: the upward sums (each node's check points against
 // its descendant bodies' proxy points) and the evaluation (targets in tree order against their
 // interaction lists).
-mfs_status ff_get_plan(mfs_ctx *ctx, int variant, int include_self, mfs_ctx::FarField::Plan **out) {
-    auto &F = ctx->ff;
+mfs_status ff_get_plan(mfs_ctx *ctx, mfs_ctx::FarField &F, int variant, int include_self,
+                       mfs_ctx::FarField::Plan **out) {
     const int key = variant * 2 + include_self;
     auto it = F.plans.find(key);
     if (it != F.plans.end()) {
@@ -723,7 +740,7 @@ mfs_status ff_get_plan(mfs_ctx *ctx, int variant, int include_self, mfs_ctx::Far
     std::vector<int> toff_ev(P + 1, 0);
     for (int q = 0; q < P; ++q) {
         const int b = F.tree.order[q];
-        toff_ev[q + 1] = toff_ev[q] + (ctx->tgt_off[b + 1] - ctx->tgt_off[b]);
+        toff_ev[q + 1] = toff_ev[q] + ((*F.tgt_off)[b + 1] - (*F.tgt_off)[b]);
     }
     std::vector<int> cuts_ev(ctx->S + 1);
     for (int sp = 0; sp <= ctx->S; ++sp) cuts_ev[sp] = ctx->body_off[sp];
@@ -768,17 +785,19 @@ mfs_status ff_launch(mfs_ctx *ctx, int variant, const PairGeom &g, const PairWor
 // upward check sums, the equivalent strengths (FP64 product with the pseudo-inverse, radius scale),
 // their records, then the evaluation over the interaction lists (results written back in the
 // caller's target order).
-mfs_status ff_pair_apply(mfs_ctx *ctx, int variant, const double *strength, double *out, const double *base,
-                         double beta, double scale, int nrhs, int include_self, cudaStream_t st) {
-    auto &F = ctx->ff;
+mfs_status ff_pair_apply(mfs_ctx *ctx, mfs_ctx::FarField &F, int variant, const double *strength, double *out,
+                         const double *base, double beta, double scale, int nrhs, int include_self, cudaStream_t st) {
     mfs_ctx::FarField::Plan *pl = nullptr;
-    CKS(ff_get_plan(ctx, variant, include_self, &pl));
+    CKS(ff_get_plan(ctx, F, variant, include_self, &pl));
     int vc = 0;
     const PairVariant *vv = pair_variants(&vc);
     const int D = ctx->D, nodes = F.nodes;
     const int REC = pair_record_floats(D, nrhs, vv[variant].packed);
-    CK(pack_sources(D, nrhs, vv[variant].packed, ctx->src_pos_d, ctx->rec_pt_d, strength, ctx->sumN, ctx->nrec, F.rec,
-                    st));
+    if (REC > F.rec_floats) {
+        ctx->last_error = "far field: record layout larger than its buffer";
+        return MFS_ERR_INVALID_ARG;
+    }
+    CK(pack_sources(D, nrhs, vv[variant].packed, F.src_pos, F.rec_pt, strength, F.nsrc, F.nrec, F.rec, st));
     PairGeom g;
     g.src = F.rec;
     g.src_off = nullptr;
@@ -797,15 +816,15 @@ mfs_status ff_pair_apply(mfs_ctx *ctx, int variant, const double *strength, doub
     CK(gemm_rm64_splitk(nrhs * nodes, D * FF_NE, D * FF_NC, Sk, F.ucheck, F.PinvT, F.fit_chunks, F.mu, st));
     CK(ff_scale(F.mu, F.re, nodes, D * FF_NE, nrhs, st));
     CK(pack_sources(D, nrhs, vv[variant].packed, F.eq_pos, F.eq_pt, F.mu, nodes * FF_NE, nodes * FF_NE,
-                    F.rec + (size_t)ctx->nrec * REC, st));
+                    F.rec + (size_t)F.nrec * REC, st));
     g.lst_seg = pl->lst_seg_ev;
     g.lst_cum = pl->lst_cum_ev;
     g.tgt = F.tgt;
-    g.ntargets = ctx->sumM;
+    g.ntargets = F.ntgt;
     PairWork we = work_of(pl->ev);
     we.tperm = F.tperm;
     CKS(ff_launch(ctx, variant, g, we, st));
-    CK(pair_epilogue(D, nrhs, we, base, beta, scale, out, ctx->sumM, st));
+    CK(pair_epilogue(D, nrhs, we, base, beta, scale, out, F.ntgt, st));
     ctx->launches += 7;
     return MFS_OK;
 }
@@ -965,7 +984,8 @@ mfs_status ensure_gmres(mfs_ctx *ctx, int nrhs) {
 // Adjoint (transposed) operators
 // ---------------------------------------------------------------------------
 // The transposed geometry: proxy points as targets (float4 with body bits), collocation points
-// as sources packed into records with their own padded offsets; plus adjoint scratch.
+// as sources packed into records with their own padded offsets; plus adjoint scratch; with
+// farfield = 1 the treecode of the transposed sums (collocation sources, proxy targets).
 mfs_status ensure_transposed(mfs_ctx *ctx) {
     if (ctx->trans_ready) return MFS_OK;
     const int P = ctx->P, R = ctx->opt.max_rhs;
@@ -994,6 +1014,7 @@ mfs_status ensure_transposed(mfs_ctx *ctx) {
         tp[q].w = kb;
     }
     const int recf = std::max(pair_record_floats(3, R, 0), pair_record_floats(3, R, 1));
+    ctx->recT_floats = recf;
     CK(ctx->alloc(&ctx->tgtT_pos_d, ctx->sumN));
     CK(ctx->alloc(&ctx->recT_d, (size_t)ctx->nrecT * recf));
     CK(ctx->alloc(&ctx->recT_off_d, P + 1));
@@ -1057,6 +1078,19 @@ mfs_status ensure_transposed(mfs_ctx *ctx) {
             fx.tcT_ready = true;
         }
     }
+    if (ctx->opt.farfield) {
+        auto &F = ctx->ffT;
+        F.src_colloc = true;
+        F.src_pos = ctx->tgt_pos_d;
+        F.rec_pt = ctx->rec_ptT_d;
+        F.nsrc = ctx->sumM;
+        F.nrec = ctx->nrecT;
+        F.rec_off = &ctx->recT_off;
+        F.tgt_pos = ctx->tgtT_pos_d;
+        F.tgt_off = &ctx->src_off;
+        F.ntgt = ctx->sumN;
+        CKS(ff_setup(ctx, F, 0));
+    }
     ctx->trans_ready = true;
     return MFS_OK;
 }
@@ -1065,8 +1099,14 @@ mfs_status ensure_transposed(mfs_ctx *ctx) {
 // self pairs included or not.  w: [nrhs][sum_M][3], z: [nrhs][sum_N][3], both FP64 on the device.
 mfs_status pair_apply_T(mfs_ctx *ctx, const double *w, double *z, int nrhs, int include_self, cudaStream_t st) {
     const int variant = fp32_variant(ctx, 3, nrhs);
+    if (ctx->ffT.ready)
+        return ff_pair_apply(ctx, ctx->ffT, variant, w, z, nullptr, 0.0, kernel_scale(ctx), nrhs, include_self, st);
     int vc = 0;
     const PairVariant *vv = pair_variants(&vc);
+    if (pair_record_floats(3, nrhs, vv[variant].packed) > ctx->recT_floats) {
+        ctx->last_error = "transposed pair sum: record layout larger than its buffer";
+        return MFS_ERR_INVALID_ARG;
+    }
     PairPlan *plan = nullptr;
     CKS(get_plan(ctx, variant, include_self, &plan, 1));
     CK(pack_sources(3, nrhs, vv[variant].packed, ctx->tgt_pos_d, ctx->rec_ptT_d, w, ctx->sumM, ctx->nrecT,
@@ -1535,9 +1575,8 @@ static void unit_fibonacci(int n, std::vector<double> &p) {
 // The transposed pseudo-inverse of the check <- equivalent map on the unit sphere (raw kernel: 1/r or
 // (I + r r^T / r^2) / r), FP64, truncated at 1e-12 of the largest singular value; least squares
 // (FF_NC > FF_NE).  It depends on the kernel only, so a context computes it once.
-static mfs_status ff_unit_pinv(mfs_ctx *ctx, const std::vector<double> &ue, const std::vector<double> &uc,
-                               cudaStream_t st) {
-    auto &F = ctx->ff;
+static mfs_status ff_unit_pinv(mfs_ctx *ctx, mfs_ctx::FarField &F, const std::vector<double> &ue,
+                               const std::vector<double> &uc, cudaStream_t st) {
     const int D = ctx->D;
     const int m = D * FF_NC, n = D * FF_NE;
     std::vector<double> A((size_t)m * n);
@@ -1605,8 +1644,7 @@ static mfs_status ff_unit_pinv(mfs_ctx *ctx, const std::vector<double> &ue, cons
 
 // Frees the far-field structures that depend on the body centres (all but the pseudo-inverse) and
 // drops the captured graphs that hold their addresses.
-static void ff_release_geometry(mfs_ctx *ctx) {
-    auto &F = ctx->ff;
+static void ff_release_geometry(mfs_ctx *ctx, mfs_ctx::FarField &F) {
     ctx->drop_graphs();
     for (auto &kv : F.plans) {
         auto &pl = kv.second;
@@ -1644,19 +1682,21 @@ static void ff_release_geometry(mfs_ctx *ctx) {
 // The far-field structures (opt.farfield = 1): the tree, the FP64 pseudo-inverse of the map from
 // equivalent strengths on the unit sphere to the field at the check points (ff_unit_pinv, once per
 // context), and the tree-ordered geometry (again after every mfs_update_centers).
-static mfs_status ff_setup(mfs_ctx *ctx, cudaStream_t st) {
-    auto &F = ctx->ff;
+static mfs_status ff_setup(mfs_ctx *ctx, mfs_ctx::FarField &F, cudaStream_t st) {
     const int P = ctx->P, D = ctx->D;
     F.rsrc.assign(P, 0.0);
     F.rtgt.assign(P, 0.0);
     for (int k = 0; k < P; ++k) {
         const ShapeHost &sh = ctx->shapes[ctx->shape_id[k]];
+        double rp = 0.0, rc = 0.0;  // radii of the proxy and collocation points about the centre
         for (int j = 0; j < sh.N; ++j)
-            F.rsrc[k] = std::max(F.rsrc[k], std::sqrt(sh.Y0[3 * j] * sh.Y0[3 * j] + sh.Y0[3 * j + 1] * sh.Y0[3 * j + 1] +
-                                                      sh.Y0[3 * j + 2] * sh.Y0[3 * j + 2]));
+            rp = std::max(rp, std::sqrt(sh.Y0[3 * j] * sh.Y0[3 * j] + sh.Y0[3 * j + 1] * sh.Y0[3 * j + 1] +
+                                        sh.Y0[3 * j + 2] * sh.Y0[3 * j + 2]));
         for (int i = 0; i < sh.M; ++i)
-            F.rtgt[k] = std::max(F.rtgt[k], std::sqrt(sh.X0[3 * i] * sh.X0[3 * i] + sh.X0[3 * i + 1] * sh.X0[3 * i + 1] +
-                                                      sh.X0[3 * i + 2] * sh.X0[3 * i + 2]));
+            rc = std::max(rc, std::sqrt(sh.X0[3 * i] * sh.X0[3 * i] + sh.X0[3 * i + 1] * sh.X0[3 * i + 1] +
+                                        sh.X0[3 * i + 2] * sh.X0[3 * i + 2]));
+        F.rsrc[k] = F.src_colloc ? rc : rp;
+        F.rtgt[k] = F.src_colloc ? rp : rc;
     }
     ff_build_tree(P, ctx->centres.data(), F.rsrc.data(), ctx->S, ctx->body_off.data(), F.tree);
     const int nodes = F.nodes = (int)F.tree.nodes.size();
@@ -1664,7 +1704,11 @@ static mfs_status ff_setup(mfs_ctx *ctx, cudaStream_t st) {
     std::vector<double> ue, uc;
     unit_fibonacci(FF_NE, ue);
     unit_fibonacci(FF_NC, uc);
-    if (!F.PinvT) CKS(ff_unit_pinv(ctx, ue, uc, st));  // independent of the centres: kept across moves
+    if (!F.PinvT) {  // independent of the centres (kept across moves) and of the roles (shared)
+        const auto &other = &F == &ctx->ff ? ctx->ffT : ctx->ff;
+        if (other.PinvT) F.PinvT = other.PinvT;
+        else CKS(ff_unit_pinv(ctx, F, ue, uc, st));
+    }
     // tree-ordered geometry and segments: proxy segment q (tree position) = body order[q], node segment
     // P + node = its equivalent points
     std::vector<double> cen(3 * (size_t)(P + nodes)), re(nodes);
@@ -1690,15 +1734,15 @@ static mfs_status ff_setup(mfs_ctx *ctx, cudaStream_t st) {
                 make_float4((float)(FF_CHECK * re[nd] * uc[3 * c]), (float)(FF_CHECK * re[nd] * uc[3 * c + 1]),
                             (float)(FF_CHECK * re[nd] * uc[3 * c + 2]), w);
     }
-    std::vector<float4> tpos(ctx->sumM), tff(ctx->sumM);
-    CK(cudaMemcpy(tpos.data(), ctx->tgt_pos_d, sizeof(float4) * ctx->sumM, cudaMemcpyDeviceToHost));
-    std::vector<int> tperm(ctx->sumM);
+    std::vector<float4> tpos(F.ntgt), tff(F.ntgt);
+    CK(cudaMemcpy(tpos.data(), F.tgt_pos, sizeof(float4) * F.ntgt, cudaMemcpyDeviceToHost));
+    std::vector<int> tperm(F.ntgt);
     int t = 0;
     for (int q = 0; q < P; ++q) {
         const int b = F.tree.order[q];
         float w;
         std::memcpy(&w, &q, sizeof(float));
-        for (int i = ctx->tgt_off[b]; i < ctx->tgt_off[b + 1]; ++i, ++t) {
+        for (int i = (*F.tgt_off)[b]; i < (*F.tgt_off)[b + 1]; ++i, ++t) {
             tff[t] = make_float4(tpos[i].x, tpos[i].y, tpos[i].z, w);
             tperm[t] = i;
         }
@@ -1707,15 +1751,15 @@ static mfs_status ff_setup(mfs_ctx *ctx, cudaStream_t st) {
     F.seg_rec1_h.resize(P + nodes);
     for (int q = 0; q < P; ++q) {
         const int b = F.tree.order[q];
-        F.seg_rec0_h[q] = ctx->rec_off[b];
-        F.seg_rec1_h[q] = ctx->rec_off[b + 1];  // padded to a multiple of 4 (zero-strength padding records)
+        F.seg_rec0_h[q] = (*F.rec_off)[b];
+        F.seg_rec1_h[q] = (*F.rec_off)[b + 1];  // padded to a multiple of 4 (zero-strength padding records)
     }
     for (int nd = 0; nd < nodes; ++nd) {
-        F.seg_rec0_h[P + nd] = ctx->nrec + nd * FF_NE;
-        F.seg_rec1_h[P + nd] = ctx->nrec + (nd + 1) * FF_NE;
+        F.seg_rec0_h[P + nd] = F.nrec + nd * FF_NE;
+        F.seg_rec1_h[P + nd] = F.nrec + (nd + 1) * FF_NE;
     }
     const int R = ctx->opt.max_rhs;
-    F.rec_floats = std::max(pair_record_floats(D, R, 0), D == 3 ? pair_record_floats(D, R, 1) : 0);
+    F.rec_floats = std::max(pair_record_floats(D, R, 0), pair_record_floats(D, R, 1));  // plain or f32x2 policies
     CK(ctx->alloc(&F.centres, cen.size()));
     CK(ctx->alloc(&F.re, re.size()));
     CK(ctx->alloc(&F.eq_pos, eq.size()));
@@ -1725,7 +1769,7 @@ static mfs_status ff_setup(mfs_ctx *ctx, cudaStream_t st) {
     CK(ctx->alloc(&F.tperm, tperm.size()));
     CK(ctx->alloc(&F.seg_rec0, F.seg_rec0_h.size()));
     CK(ctx->alloc(&F.seg_rec1, F.seg_rec1_h.size()));
-    CK(ctx->alloc(&F.rec, (size_t)(ctx->nrec + (size_t)nodes * FF_NE) * F.rec_floats));
+    CK(ctx->alloc(&F.rec, (size_t)(F.nrec + (size_t)nodes * FF_NE) * F.rec_floats));
     CK(ctx->alloc(&F.ucheck, (size_t)R * nodes * FF_NC * D));
     CK(ctx->alloc(&F.mu, (size_t)R * nodes * FF_NE * D));
     {
@@ -1745,7 +1789,7 @@ static mfs_status ff_setup(mfs_ctx *ctx, cudaStream_t st) {
     CK(cudaMemcpy(F.tperm, tperm.data(), sizeof(int) * tperm.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(F.seg_rec0, F.seg_rec0_h.data(), sizeof(int) * F.seg_rec0_h.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(F.seg_rec1, F.seg_rec1_h.data(), sizeof(int) * F.seg_rec1_h.size(), cudaMemcpyHostToDevice));
-    CK(cudaMemset(F.rec, 0, sizeof(float) * (size_t)(ctx->nrec + (size_t)nodes * FF_NE) * F.rec_floats));
+    CK(cudaMemset(F.rec, 0, sizeof(float) * (size_t)(F.nrec + (size_t)nodes * FF_NE) * F.rec_floats));
     F.ready = true;
     return MFS_OK;
 }
@@ -1972,8 +2016,11 @@ static mfs_status setup_impl(mfs_ctx *ctx, mfs_kind kind, const mfs_bodies *bodi
     if (status != MFS_OK) return status;
 
     // work buffers
-    const int recf = std::max({pair_record_floats(D, R, 0), D == 3 ? pair_record_floats(D, R, 1) : 0,
+    // every layout a forward pair-kernel entry of this kind may use: plain, f32x2 (Stokes and Laplace),
+    // compensated
+    const int recf = std::max({pair_record_floats(D, R, 0), pair_record_floats(D, R, 1),
                                ctx->opt.precision == 3 ? pair_record_floats(D, R, 2) : 0});
+    ctx->rec_floats = recf;
     CK(ctx->alloc(&ctx->rec_d, (size_t)ctx->nrec * recf));
     CK(cudaMemset(ctx->rec_d, 0, sizeof(float) * (size_t)ctx->nrec * recf));
     CK(ctx->alloc(&ctx->lam_d, (size_t)R * ctx->sumN * D));
@@ -1983,7 +2030,19 @@ static mfs_status setup_impl(mfs_ctx *ctx, mfs_kind kind, const mfs_bodies *bodi
     CK(cudaEventCreate(&ctx->ev1));
     CK(cudaEventCreate(&ctx->evp0));
     CK(cudaEventCreate(&ctx->evp1));
-    if (ctx->opt.farfield) CKS(ff_setup(ctx, st));
+    if (ctx->opt.farfield) {  // forward sums: proxy sources, collocation targets
+        auto &F = ctx->ff;
+        F.src_colloc = false;
+        F.src_pos = ctx->src_pos_d;
+        F.rec_pt = ctx->rec_pt_d;
+        F.nsrc = ctx->sumN;
+        F.nrec = ctx->nrec;
+        F.rec_off = &ctx->rec_off;
+        F.tgt_pos = ctx->tgt_pos_d;
+        F.tgt_off = &ctx->tgt_off;
+        F.ntgt = ctx->sumM;
+        CKS(ff_setup(ctx, F, st));
+    }
     CK(cudaStreamSynchronize(st));
     ctx->ms_setup = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return MFS_OK;
@@ -2135,10 +2194,11 @@ mfs_status mfs_update_centers(mfs_ctx *ctx, const double *centers, void *stream)
         }
     CK(cudaMemcpyAsync(ctx->centres_d, ctx->centres.data(), sizeof(double) * 3 * ctx->P, cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
-    if (ctx->ff.ready) {  // the treecode's tree, node centres and interaction lists follow the bodies
+    for (auto *F : {&ctx->ff, &ctx->ffT}) {  // the treecodes' trees, node centres and lists follow the bodies
+        if (!F->ready) continue;
         CK(cudaDeviceSynchronize());
-        ff_release_geometry(ctx);
-        CKS(ff_setup(ctx, st));
+        ff_release_geometry(ctx, *F);
+        CKS(ff_setup(ctx, *F, st));
     }
     return MFS_OK;
 }

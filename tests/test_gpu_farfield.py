@@ -193,3 +193,34 @@ def test_farfield_dirichlet_and_adjoint():
     assert info.converged and _rel(qb.numpy(), qa.numpy()) < 1e-5
     direct.close()
     tree.close()
+
+
+def test_farfield_transposed_sums():
+    """The adjoint's transposed pair sums through their own treecode (collocation points as sources,
+    proxy points as targets), before and after a move.  A^T applies (S_L^+)^T after the pair sum, which
+    amplifies FP32-level errors of the sum on this coarse grid (the direct FP32 path lands about 5e-5
+    from the FP64 GPU path on a rigid-motion w), so the bar is relative: the treecode's A^T w is held
+    to the FP64 GPU path within 1.5x the direct FP32 path's own error (plus 1e-6)."""
+    wl = make_workload("sphere100_mobility", count=40, m=300, n=150, seed=27)
+    tree, direct = _ctx(wl, farfield=1), _ctx(wl)
+    ref = _ctx(wl, precision=1, autotune=0)
+    pr = Problem(wl)
+    for step in range(2):
+        if step:
+            centres = wl.centres[np.random.default_rng(28).permutation(wl.num_bodies)] + 0.5
+            for ctx in (tree, direct, ref):
+                ctx.update_centers(centres)
+            moved = make_workload("sphere100_mobility", count=40, m=300, n=150, seed=27)
+            moved.centres = centres
+            pr = Problem(moved)
+            wl = moved
+        rigid = _rigid_field(pr, wl, 40 + step)
+        noise = np.random.default_rng(50 + step).standard_normal(rigid.size)
+        for v in (rigid, noise):
+            w = torch.tensor(v.reshape(1, -1, 3), device="cuda")
+            r = ref.matvec_transposed(w).cpu().numpy().reshape(-1)
+            e_dir = _rel(direct.matvec_transposed(w).cpu().numpy().reshape(-1), r)
+            e_tree = _rel(tree.matvec_transposed(w).cpu().numpy().reshape(-1), r)
+            assert e_tree <= 1.5 * e_dir + 1e-6, (step, e_tree, e_dir)
+    for ctx in (tree, direct, ref):
+        ctx.close()
