@@ -114,8 +114,8 @@ typedef struct {
                              2.  Every forward pair sum uses it (the solves, mfs_matvec, mfs_pair_sum); the
                              transposed sums of mfs_matvec_transposed and mfs_mobility_vjp use a second tree
                              with the roles swapped (collocation points as sources, proxy points as targets,
-                             built on first use); the VJP's centre-gradient kernel and mfs_evaluate* stay
-                             direct. */
+                             built on first use), and so does the VJP's centre gradient (its target side on
+                             the first tree, its source side on the second); mfs_evaluate* stay direct. */
     double farfield_separation; /* farfield = 1: a target uses a node's equivalent points when it is at least
                                    this many equivalent radii from the node's centre; default 3, allowed
                                    [2.5, 10] (2.5 = the check sphere; smaller is faster and less accurate). */

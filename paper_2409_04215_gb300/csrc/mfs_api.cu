@@ -195,6 +195,7 @@ struct mfs_ctx {
         double *ucheck = nullptr;                    // [max_rhs][nodes FF_NC][D]
         double *mu = nullptr;                        // [max_rhs][nodes FF_NE][D]
         double *fit_chunks = nullptr;                // split-K partials of the fit product
+        float *wt = nullptr;                         // [max_rhs][ntgt][3] target weights in tree order (gradient)
         struct Plan {
             PairPlan up, ev;
             int *lst_seg_up = nullptr, *lst_seg_ev = nullptr;
@@ -781,32 +782,34 @@ mfs_status ff_launch(mfs_ctx *ctx, int variant, const PairGeom &g, const PairWor
     return MFS_OK;
 }
 
-// out = beta * base + scale * (pair sum of strengths) through the treecode: proxy records, the
-// upward check sums, the equivalent strengths (FP64 product with the pseudo-inverse, radius scale),
-// their records, then the evaluation over the interaction lists (results written back in the
-// caller's target order).
-mfs_status ff_pair_apply(mfs_ctx *ctx, mfs_ctx::FarField &F, int variant, const double *strength, double *out,
-                         const double *base, double beta, double scale, int nrhs, int include_self, cudaStream_t st) {
-    mfs_ctx::FarField::Plan *pl = nullptr;
-    CKS(ff_get_plan(ctx, F, variant, include_self, &pl));
-    int vc = 0;
-    const PairVariant *vv = pair_variants(&vc);
-    const int D = ctx->D, nodes = F.nodes;
-    const int REC = pair_record_floats(D, nrhs, vv[variant].packed);
-    if (REC > F.rec_floats) {
-        ctx->last_error = "far field: record layout larger than its buffer";
-        return MFS_ERR_INVALID_ARG;
-    }
-    CK(pack_sources(D, nrhs, vv[variant].packed, F.src_pos, F.rec_pt, strength, F.nsrc, F.nrec, F.rec, st));
+// The geometry of a far-field launch: the tree-ordered centres and the segments' record ranges.
+static PairGeom ff_geom(const mfs_ctx::FarField &F) {
     PairGeom g;
     g.src = F.rec;
     g.src_off = nullptr;
     g.blk_off = nullptr;
     g.centres = F.centres;
-    g.lst_seg = pl->lst_seg_up;
-    g.lst_cum = pl->lst_cum_up;
     g.seg_rec0 = F.seg_rec0;
     g.seg_rec1 = F.seg_rec1;
+    return g;
+}
+
+// The upward step of the treecode: the sources (records in the layout of `variant`, packed into
+// F.rec) summed at every node's check points over the node's descendant bodies, then the node's
+// equivalent strengths F.mu = (FP64 product with the pseudo-inverse) scaled by the radius.
+static mfs_status ff_upward(mfs_ctx *ctx, mfs_ctx::FarField &F, int variant, const mfs_ctx::FarField::Plan *pl,
+                            const double *strength, int nrhs, cudaStream_t st) {
+    int vc = 0;
+    const PairVariant *vv = pair_variants(&vc);
+    const int D = ctx->D, nodes = F.nodes;
+    if (pair_record_floats(D, nrhs, vv[variant].packed) > F.rec_floats) {
+        ctx->last_error = "far field: record layout larger than its buffer";
+        return MFS_ERR_INVALID_ARG;
+    }
+    CK(pack_sources(D, nrhs, vv[variant].packed, F.src_pos, F.rec_pt, strength, F.nsrc, F.nrec, F.rec, st));
+    PairGeom g = ff_geom(F);
+    g.lst_seg = pl->lst_seg_up;
+    g.lst_cum = pl->lst_cum_up;
     g.tgt = F.chk_pos;
     g.ntargets = nodes * FF_NC;
     const PairWork wu = work_of(pl->up);
@@ -815,8 +818,25 @@ mfs_status ff_pair_apply(mfs_ctx *ctx, mfs_ctx::FarField &F, int variant, const 
     const int Sk = gemm_rm64_chunks(nrhs * nodes, D * FF_NE, D * FF_NC, ctx->sm_count);
     CK(gemm_rm64_splitk(nrhs * nodes, D * FF_NE, D * FF_NC, Sk, F.ucheck, F.PinvT, F.fit_chunks, F.mu, st));
     CK(ff_scale(F.mu, F.re, nodes, D * FF_NE, nrhs, st));
+    ctx->launches += 4;
+    return MFS_OK;
+}
+
+// out = beta * base + scale * (pair sum of strengths) through the treecode: the upward step, the
+// equivalent strengths' records, then the evaluation over the interaction lists (results written
+// back in the caller's target order).
+mfs_status ff_pair_apply(mfs_ctx *ctx, mfs_ctx::FarField &F, int variant, const double *strength, double *out,
+                         const double *base, double beta, double scale, int nrhs, int include_self, cudaStream_t st) {
+    mfs_ctx::FarField::Plan *pl = nullptr;
+    CKS(ff_get_plan(ctx, F, variant, include_self, &pl));
+    int vc = 0;
+    const PairVariant *vv = pair_variants(&vc);
+    const int D = ctx->D, nodes = F.nodes;
+    const int REC = pair_record_floats(D, nrhs, vv[variant].packed);
+    CKS(ff_upward(ctx, F, variant, pl, strength, nrhs, st));
     CK(pack_sources(D, nrhs, vv[variant].packed, F.eq_pos, F.eq_pt, F.mu, nodes * FF_NE, nodes * FF_NE,
                     F.rec + (size_t)F.nrec * REC, st));
+    PairGeom g = ff_geom(F);
     g.lst_seg = pl->lst_seg_ev;
     g.lst_cum = pl->lst_cum_ev;
     g.tgt = F.tgt;
@@ -825,7 +845,54 @@ mfs_status ff_pair_apply(mfs_ctx *ctx, mfs_ctx::FarField &F, int variant, const 
     we.tperm = F.tperm;
     CKS(ff_launch(ctx, variant, g, we, st));
     CK(pair_epilogue(D, nrhs, we, base, beta, scale, out, F.ntgt, st));
-    ctx->launches += 7;
+    ctx->launches += 3;
+    return MFS_OK;
+}
+
+// wt[h][t][c] = (float) v[h][perm[t]][c]: per-target weights in the tree's target order.
+static __global__ void ff_gather_weights_kernel(const double *v, const int *perm, int n, int nrhs, float *wt) {
+    const size_t total = (size_t)nrhs * n * 3;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t h = e / ((size_t)n * 3), r = e % ((size_t)n * 3);
+        const int t = (int)(r / 3), c = (int)(r % 3);
+        wt[e] = (float)v[(h * n + perm[t]) * 3 + c];
+    }
+}
+
+// The adjoint's pair gradient through the treecode, per target of F (scaled, FP64, caller's order):
+//   out_t = scale * sum_h sum_{s not on t's body} grad_r (tw_h(t)^T G(r) sigma_h(s)),  r = x_t - y_s,
+// with sigma the sources' strengths (near bodies directly, far nodes through the equivalent
+// strengths fitted to sigma) and tw the targets' weights.  On the forward tree (targets the
+// collocation points, tw = w, sigma = mu) it is the target side of the centre gradient; on the
+// transposed tree (targets the proxy points, tw = mu, sigma = w) its source side with the sign
+// reversed (G symmetric and even, so its gradient is odd).
+mfs_status ff_grad_apply(mfs_ctx *ctx, mfs_ctx::FarField &F, int gv, const double *sigma, const double *tw, int nrhs,
+                         double *out, cudaStream_t st) {
+    const int fv = fp32_variant(ctx, 3, nrhs);  // the upward sums: the forward pair kernel
+    mfs_ctx::FarField::Plan *pu = nullptr, *pg = nullptr;
+    CKS(ff_get_plan(ctx, F, fv, 1, &pu));
+    CKS(ff_get_plan(ctx, F, gv, 0, &pg));
+    CKS(ff_upward(ctx, F, fv, pu, sigma, nrhs, st));
+    // records of the gradient kernel (plain layout): the sources, then the equivalent points
+    const int REC = pair_record_floats(3, nrhs, 0), nodes = F.nodes;
+    CK(pack_sources(3, nrhs, 0, F.src_pos, F.rec_pt, sigma, F.nsrc, F.nrec, F.rec, st));
+    CK(pack_sources(3, nrhs, 0, F.eq_pos, F.eq_pt, F.mu, nodes * FF_NE, nodes * FF_NE, F.rec + (size_t)F.nrec * REC,
+                    st));
+    if (!F.wt) CK(ctx->alloc(&F.wt, (size_t)ctx->opt.max_rhs * F.ntgt * 3));
+    ff_gather_weights_kernel<<<1024, 256, 0, st>>>(tw, F.tperm, F.ntgt, nrhs, F.wt);
+    CK(cudaGetLastError());
+    PairGeom g = ff_geom(F);
+    g.lst_seg = pg->lst_seg_ev;
+    g.lst_cum = pg->lst_cum_ev;
+    g.tgt = F.tgt;
+    g.ntargets = F.ntgt;
+    g.tgt_w = F.wt;
+    PairWork we = work_of(pg->ev);
+    we.tperm = F.tperm;
+    we.src_grad = nullptr;  // segments are bodies and nodes here: no per-source-body reduction
+    CKS(ff_launch(ctx, gv, g, we, st));
+    CK(pair_epilogue(3, 1, we, nullptr, 0.0, kernel_scale(ctx), out, F.ntgt, st));
+    ctx->launches += 5;
     return MFS_OK;
 }
 
@@ -2573,6 +2640,27 @@ static __global__ void centre_grad_kernel(const double *gradT, const int *tgt_of
     if (threadIdx.x < 3) dc[3 * k + threadIdx.x] = scale * src_grad[3 * k + threadIdx.x] - red[threadIdx.x][0];
 }
 
+// The centre gradient from the two treecode passes: dc_k = -(sum over body k's collocation points of gc)
+// - (sum over its proxy points of gp), both already scaled.
+static __global__ void centre_grad_ff_kernel(const double *gc, const int *tgt_off, const double *gp, const int *src_off,
+                                             double *dc) {
+    const int k = blockIdx.x;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int i = tgt_off[k] + threadIdx.x; i < tgt_off[k + 1]; i += blockDim.x)
+        for (int c = 0; c < 3; ++c) acc[c] += gc[3 * (size_t)i + c];
+    for (int j = src_off[k] + threadIdx.x; j < src_off[k + 1]; j += blockDim.x)
+        for (int c = 0; c < 3; ++c) acc[c] += gp[3 * (size_t)j + c];
+    __shared__ double red[3][128];
+    for (int c = 0; c < 3; ++c) red[c][threadIdx.x] = acc[c];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) dc[3 * k + threadIdx.x] = -red[threadIdx.x][0];
+}
+
 // [dF; dT]_k = G_k^{-1} v_k with G_k = R_2 G_0 R_2^T (v = -K_N^T z, given as its force and torque parts)
 static __global__ void gram_solve_kernel(const double *vf, const double *vt, int P, int nrhs, const double *rot64,
                                          const double *G0inv_shapes, const int *shape_id, double *dF, double *dT) {
@@ -2658,20 +2746,31 @@ mfs_status mfs_mobility_vjp(mfs_ctx *ctx, const double *dU, const double *dOmega
         ctx->last_error = "no gradient kernel for this nrhs";
         return MFS_ERR_INVALID_ARG;
     }
-    to_f32_kernel<<<1024, 256, 0, st>>>(ctx->x_d, ctx->w32_d, nM);
-    CK(pack_sources(3, nrhs, 0, ctx->src_pos_d, ctx->rec_pt_d, ctx->lam_d, ctx->sumN, ctx->nrec, ctx->rec_d, st));
-    CK(cudaMemsetAsync(ctx->src_grad_d, 0, sizeof(double) * 3 * P, st));
-    PairPlan *plan = nullptr;
-    CKS(get_plan(ctx, gv, 0, &plan));
-    PairGeom g = geom_of(ctx);
-    g.tgt_w = ctx->w32_d;
-    PairWork wk = work_of(*plan);
-    wk.src_grad = ctx->src_grad_d;
-    if (wk.total_units > 0) CK(pair_launch(gv, g, wk, ctx->err_d, st));
-    CK(pair_epilogue(3, 1, wk, nullptr, 0.0, kernel_scale(ctx), ctx->gradT_d, ctx->sumM, st));
-    centre_grad_kernel<<<P, 128, 0, st>>>(ctx->gradT_d, ctx->tgt_off_d, ctx->src_grad_d, kernel_scale(ctx), dco.d);
-    CK(cudaGetLastError());
-    ctx->launches += 6;
+    if (ctx->ff.ready && ctx->ffT.ready) {
+        // through the treecodes: the target side on the forward tree (weights w at the collocation
+        // points, sources mu), the source side on the transposed tree (weights mu at the proxy
+        // points, sources w); tmpM_d (free again) takes the proxy-side gradient
+        CKS(ff_grad_apply(ctx, ctx->ff, gv, ctx->lam_d, ctx->x_d, nrhs, ctx->gradT_d, st));
+        CKS(ff_grad_apply(ctx, ctx->ffT, gv, ctx->x_d, ctx->lam_d, nrhs, ctx->tmpM_d, st));
+        centre_grad_ff_kernel<<<P, 128, 0, st>>>(ctx->gradT_d, ctx->tgt_off_d, ctx->tmpM_d, ctx->src_off_d, dco.d);
+        CK(cudaGetLastError());
+        ctx->launches += 1;
+    } else {
+        to_f32_kernel<<<1024, 256, 0, st>>>(ctx->x_d, ctx->w32_d, nM);
+        CK(pack_sources(3, nrhs, 0, ctx->src_pos_d, ctx->rec_pt_d, ctx->lam_d, ctx->sumN, ctx->nrec, ctx->rec_d, st));
+        CK(cudaMemsetAsync(ctx->src_grad_d, 0, sizeof(double) * 3 * P, st));
+        PairPlan *plan = nullptr;
+        CKS(get_plan(ctx, gv, 0, &plan));
+        PairGeom g = geom_of(ctx);
+        g.tgt_w = ctx->w32_d;
+        PairWork wk = work_of(*plan);
+        wk.src_grad = ctx->src_grad_d;
+        if (wk.total_units > 0) CK(pair_launch(gv, g, wk, ctx->err_d, st));
+        CK(pair_epilogue(3, 1, wk, nullptr, 0.0, kernel_scale(ctx), ctx->gradT_d, ctx->sumM, st));
+        centre_grad_kernel<<<P, 128, 0, st>>>(ctx->gradT_d, ctx->tgt_off_d, ctx->src_grad_d, kernel_scale(ctx), dco.d);
+        CK(cudaGetLastError());
+        ctx->launches += 6;
+    }
     // 5. force and torque cotangents
     if (dF) {
         CKS(pair_apply_T(ctx, ctx->x_d, ctx->lam_d, nrhs, 1, st));

@@ -689,6 +689,7 @@ struct GradStokes : PolicyBase {
     }
     // All threads of the CTA call this together (the source-body boundary is CTA-uniform).
     __device__ __forceinline__ void source_side(int body, bool include_self, double *src_grad) {
+        if (!src_grad) return;  // no per-source-body reduction (a kernel argument: CTA-uniform)
         __shared__ float red[NT / 32][3];
         float s[3] = {0.f, 0.f, 0.f};
 #pragma unroll

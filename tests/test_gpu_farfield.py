@@ -175,14 +175,18 @@ def test_farfield_dirichlet_and_adjoint():
     Fb, Tb, ib = tree.solve_resistance(Uin, Win)
     assert ia.converged and ib.converged
     assert _rel(np.concatenate([Fb.numpy(), Tb.numpy()], 2), np.concatenate([Fa.numpy(), Ta.numpy()], 2)) < 1e-5
-    F, T = torch.tensor(wl.F[:1], device="cuda"), torch.tensor(wl.T[:1], device="cuda")
-    grads = []
-    for ctx in (direct, tree):
-        U, W, _ = ctx.solve_mobility(F, T)
-        dc, dF, dT = ctx.mobility_vjp(2.0 * U, 0.6 * W, want_force_grads=True)
-        grads.append(np.concatenate([dc.cpu().numpy().reshape(-1), dF.cpu().numpy().reshape(-1),
-                                     dT.cpu().numpy().reshape(-1)]))
-    assert _rel(grads[1], grads[0]) < 1e-4
+    for nrhs in (1, 2):  # the centre gradient runs on both trees (target and source sides)
+        F, T = torch.tensor(wl.F[:nrhs], device="cuda"), torch.tensor(wl.T[:nrhs], device="cuda")
+        grads = []
+        for ctx in (direct, tree):
+            U, W, _ = ctx.solve_mobility(F, T)
+            dc, dF, dT = ctx.mobility_vjp(2.0 * U, 0.6 * W, want_force_grads=True)
+            grads.append((dc.cpu().numpy(), np.concatenate([dF.cpu().numpy().reshape(-1),
+                                                            dT.cpu().numpy().reshape(-1)])))
+        (dca, fa), (dcb, fb) = grads
+        assert _rel(dcb, dca) < 1e-4, nrhs
+        assert _rel(fb, fa) < 1e-4, nrhs
+        assert np.abs(dcb.sum(axis=0)).max() <= 1e-4 * np.abs(dca).max()  # translation invariance
     direct.close()
     tree.close()
     lw = make_workload("sphere100_elastance", count=40, m=300, n=150)
