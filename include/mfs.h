@@ -115,7 +115,9 @@ typedef struct {
                              transposed sums of mfs_matvec_transposed and mfs_mobility_vjp use a second tree
                              with the roles swapped (collocation points as sources, proxy points as targets,
                              built on first use), and so does the VJP's centre gradient (its target side on
-                             the first tree, its source side on the second); mfs_evaluate* stay direct. */
+                             the first tree, its source side on the second); mfs_evaluate sums over the first
+                             tree with interaction lists built for each call's points (each owner body's
+                             radius that of its farthest point); mfs_evaluate_stress stays direct. */
     double farfield_separation; /* farfield = 1: a target uses a node's equivalent points when it is at least
                                    this many equivalent radii from the node's centre; default 3, allowed
                                    [2.5, 10] (2.5 = the check sphere; smaller is faster and less accurate). */

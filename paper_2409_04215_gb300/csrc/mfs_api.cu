@@ -2922,6 +2922,90 @@ mfs_status last_strengths(mfs_ctx *ctx, int nrhs, double *tmp, cudaStream_t st) 
 }
 }  // namespace
 
+// The representation at owner-grouped evaluation points through the treecode (farfield = 1): the
+// upward step on the strengths in lam_d, the points reordered into the tree's body order, one-off
+// interaction lists for them (each owner's radius is that of its farthest point), and the
+// evaluation launch; results land in sorted_d in the grouped order (out = scale * sums).
+static mfs_status ff_evaluate_points(mfs_ctx *ctx, int variant, const EvalTargets &et, int nrhs, double scale,
+                                     double *sorted_d, cudaStream_t st) {
+    auto &F = ctx->ff;
+    const int P = ctx->P, D = ctx->D, np = (int)et.t4.size(), nodes = F.nodes;
+    int vc = 0;
+    const PairVariant *vv = pair_variants(&vc);
+    mfs_ctx::FarField::Plan *pu = nullptr;
+    CKS(ff_get_plan(ctx, F, variant, 1, &pu));
+    CKS(ff_upward(ctx, F, variant, pu, ctx->lam_d, nrhs, st));
+    const int REC = pair_record_floats(D, nrhs, vv[variant].packed);
+    CK(pack_sources(D, nrhs, vv[variant].packed, F.eq_pos, F.eq_pt, F.mu, nodes * FF_NE, nodes * FF_NE,
+                    F.rec + (size_t)F.nrec * REC, st));
+    // tree order of the points; w = the owner's tree position; tperm: tree index -> grouped index
+    std::vector<float4> tt(np);
+    std::vector<int> tperm(np), toff(P + 1, 0);
+    std::vector<double> rad(P, 0.0);
+    int t = 0;
+    for (int q = 0; q < P; ++q) {
+        const int b = F.tree.order[q];
+        float w;
+        std::memcpy(&w, &q, sizeof(float));
+        for (int j = et.toff[b]; j < et.toff[b + 1]; ++j, ++t) {
+            tt[t] = make_float4(et.t4[j].x, et.t4[j].y, et.t4[j].z, w);
+            tperm[t] = j;
+            const double *x = &et.t64[3 * (size_t)j];
+            rad[b] = std::max(rad[b], std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]));
+        }
+        toff[q + 1] = t;
+    }
+    std::vector<long long> seg_blocks(P + nodes);
+    std::vector<int> seg_recs(P + nodes);
+    for (int sg = 0; sg < P + nodes; ++sg) {
+        seg_recs[sg] = F.seg_rec1_h[sg] - F.seg_rec0_h[sg];
+        seg_blocks[sg] = (seg_recs[sg] + MFS_BS - 1) / MFS_BS;
+    }
+    std::vector<int> cuts(ctx->S + 1), suspension_of(P), tb;
+    for (int sp = 0; sp <= ctx->S; ++sp) cuts[sp] = ctx->body_off[sp];
+    for (int sp = 0; sp < ctx->S; ++sp)
+        for (int b = ctx->body_off[sp]; b < ctx->body_off[sp + 1]; ++b) suspension_of[b] = sp;
+    PairPlan plan;
+    int *lst_seg = nullptr, *perm_d = nullptr;
+    long long *lst_cum = nullptr;
+    float4 *tt_d = nullptr;
+    double pairs = 0.0;
+    mfs_status rc = build_plan_lists(
+        ctx, variant, 1, toff, 0, cuts, seg_blocks, seg_recs,
+        [&](int g0, int g1, std::vector<int> &segs) {
+            tb.clear();
+            for (int q = g0; q <= g1; ++q) tb.push_back(F.tree.order[q]);
+            ff_interaction_list(F.tree, F.tree.roots[suspension_of[tb[0]]], tb, ctx->centres.data(), rad.data(),
+                                ctx->opt.farfield_separation, 0, segs);
+        },
+        plan, &lst_seg, &lst_cum, pairs);
+    if (rc == MFS_OK) {
+        rc = [&]() -> mfs_status {
+            CK(ctx->alloc(&tt_d, np));
+            CK(ctx->alloc(&perm_d, np));
+            CK(cudaMemcpyAsync(tt_d, tt.data(), sizeof(float4) * np, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(perm_d, tperm.data(), sizeof(int) * np, cudaMemcpyHostToDevice, st));
+            PairGeom g = ff_geom(F);
+            g.lst_seg = lst_seg;
+            g.lst_cum = lst_cum;
+            g.tgt = tt_d;
+            g.ntargets = np;
+            PairWork we = work_of(plan);
+            we.tperm = perm_d;
+            CKS(ff_launch(ctx, variant, g, we, st));
+            CK(pair_epilogue(D, nrhs, we, nullptr, 0.0, scale, sorted_d, np, st));
+            return MFS_OK;
+        }();
+    }
+    cudaStreamSynchronize(st);  // the one-off lists and plan are freed below
+    ctx->release(tt_d);
+    ctx->release(perm_d);
+    ctx->release(lst_seg);
+    ctx->release(lst_cum);
+    if (plan.tiles) release_plan(ctx, plan);
+    return rc;
+}
+
 extern "C" {
 
 mfs_status mfs_evaluate(mfs_ctx *ctx, const double *points, const int32_t *owner, int32_t npoints, double *out,
@@ -2981,17 +3065,21 @@ mfs_status mfs_evaluate(mfs_ctx *ctx, const double *points, const int32_t *owner
                 ctx->last_error = "no pair-kernel variant for this nrhs";
                 return MFS_ERR_INVALID_ARG;
             }
-            CKS(build_plan_for(ctx, variant, 1, toff, tbody, ctx->blk_off, np, plan));
-            int vc = 0;
-            const PairVariant *vv = pair_variants(&vc);
-            CK(pack_sources(D, nrhs, vv[variant].packed, ctx->src_pos_d, ctx->rec_pt_d, ctx->lam_d, ctx->sumN,
-                            ctx->nrec, ctx->rec_d, st));
-            PairGeom g = geom_of(ctx);
-            g.tgt = t4_d;
-            g.ntargets = np;
-            const PairWork w = work_of(plan);
-            if (w.total_units > 0) CK(pair_launch(variant, g, w, ctx->err_d, st));
-            CK(pair_epilogue(D, nrhs, w, nullptr, 0.0, scale, sorted_d, np, st));
+            if (ctx->ff.ready) {  // through the treecode
+                CKS(ff_evaluate_points(ctx, variant, et, nrhs, scale, sorted_d, st));
+            } else {
+                CKS(build_plan_for(ctx, variant, 1, toff, tbody, ctx->blk_off, np, plan));
+                int vc = 0;
+                const PairVariant *vv = pair_variants(&vc);
+                CK(pack_sources(D, nrhs, vv[variant].packed, ctx->src_pos_d, ctx->rec_pt_d, ctx->lam_d, ctx->sumN,
+                                ctx->nrec, ctx->rec_d, st));
+                PairGeom g = geom_of(ctx);
+                g.tgt = t4_d;
+                g.ntargets = np;
+                const PairWork w = work_of(plan);
+                if (w.total_units > 0) CK(pair_launch(variant, g, w, ctx->err_d, st));
+                CK(pair_epilogue(D, nrhs, w, nullptr, 0.0, scale, sorted_d, np, st));
+            }
         }
         const size_t n = (size_t)nrhs * np * D;
         unsort_kernel<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, st>>>(sorted_d, order_d, np, D,

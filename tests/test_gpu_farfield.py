@@ -228,3 +228,37 @@ def test_farfield_transposed_sums():
             assert e_tree <= 1.5 * e_dir + 1e-6, (step, e_tree, e_dir)
     for ctx in (tree, direct, ref):
         ctx.close()
+
+
+def test_farfield_evaluate_points():
+    """mfs_evaluate through the treecode (the points reordered into the tree's body order, one-off
+    interaction lists with each owner's farthest point as its radius) against the direct evaluation:
+    points near the bodies' surfaces and points between them, owners given or found, mobility with two
+    right-hand sides and elastance."""
+    rng = np.random.default_rng(32)
+    for name in ("sphere100_mobility", "sphere100_elastance"):
+        wl = make_workload(name, count=40, m=300, n=150, seed=31) if name.endswith("mobility") else \
+            make_workload(name, count=40, m=300, n=150)
+        tree, direct = _ctx(wl, farfield=1), _ctx(wl)
+        nrhs = 2 if name.endswith("mobility") else 1
+        FT = rng.standard_normal((2, nrhs, wl.num_bodies, 3))
+        for ctx in (tree, direct):
+            if name.endswith("mobility"):
+                ctx.solve_mobility(torch.tensor(FT[0], device="cuda"), torch.tensor(FT[1], device="cuda"))
+            else:
+                ctx.solve_elastance(torch.tensor(wl.Q[None], device="cuda"))
+        k = rng.integers(0, wl.num_bodies, 3000)
+        d = rng.standard_normal((3000, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        near = wl.centres[k] + rng.uniform(1.02, 1.5, 3000)[:, None] * d
+        box = rng.uniform(wl.centres.min(0), wl.centres.max(0), (4000, 3))
+        dist = np.linalg.norm(box[:, None, :] - wl.centres[None], axis=2)
+        box = box[dist.min(1) > 1.05][:800]
+        pts = np.concatenate([near, box])
+        owner = np.linalg.norm(pts[:, None, :] - wl.centres[None], axis=2).argmin(1).astype(np.int32)
+        for own in (owner, None):
+            a = direct.evaluate(pts, owner=own, nrhs=nrhs).numpy()
+            b = tree.evaluate(pts, owner=own, nrhs=nrhs).numpy()
+            assert _rel(b, a) < 1e-6, (name, own is None)
+        tree.close()
+        direct.close()
