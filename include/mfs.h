@@ -117,7 +117,8 @@ typedef struct {
                              built on first use), and so does the VJP's centre gradient (its target side on
                              the first tree, its source side on the second); mfs_evaluate sums over the first
                              tree with interaction lists built for each call's points (each owner body's
-                             radius that of its farthest point); mfs_evaluate_stress stays direct. */
+                             radius that of its farthest point), and mfs_evaluate_stress likewise (the
+                             pressure and traction of the equivalent Stokeslets in the far field). */
     double farfield_separation; /* farfield = 1: a target uses a node's equivalent points when it is at least
                                    this many equivalent radii from the node's centre; default 3, allowed
                                    [2.5, 10] (2.5 = the check sphere; smaller is faster and less accurate). */

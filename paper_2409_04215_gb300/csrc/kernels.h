@@ -139,6 +139,11 @@ cudaError_t dirichlet_rhs_laplace(const double *phi, int nrhs, int P, const int 
 cudaError_t stress_f32(int nrhs, const float4 *tgt, const float *nrm, int np, const float *rec, int rec_floats,
                        const int *rec_off, const int *sb0, const int *sb1, const double *centres, double *p_out,
                        double *t_out, cudaStream_t st);
+// The same over per-owner interaction lists (far-field treecode): tree-ordered targets (w = owner's tree
+// position), segments with record ranges and centres, results at index perm[t].
+cudaError_t stress_list_f32(int nrhs, const float4 *tgt, const float *nrm, int np, const float *rec, int rec_floats,
+                            const int *lst_off, const int *lst_seg, const int *seg_rec0, const int *seg_rec1,
+                            const double *centres, const int *perm, double *p_out, double *t_out, cudaStream_t st);
 cudaError_t stress_f64(int nrhs, const double *tgt_local, const int *tbody, const double *nrm, int np,
                        const double *src_local, const int *src_off, int sum_N, const double *lam, const int *sb0,
                        const int *sb1, const double *centres, double *p_out, double *t_out, cudaStream_t st);

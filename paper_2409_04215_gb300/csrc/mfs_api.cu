@@ -3006,6 +3006,81 @@ static mfs_status ff_evaluate_points(mfs_ctx *ctx, int variant, const EvalTarget
     return rc;
 }
 
+// Pressure and traction (Eq. traction) at owner-grouped points through the treecode: the upward step
+// on the strengths in lam_d, the proxy and equivalent records in the plain layout, the points in the
+// tree's body order and each owner's interaction list; results in the grouped order (ps_d, ts_d).
+static mfs_status ff_stress_points(mfs_ctx *ctx, const EvalTargets &et, bool traction, int nrhs, double *ps_d,
+                                   double *ts_d, cudaStream_t st) {
+    auto &F = ctx->ff;
+    const int P = ctx->P, np = (int)et.t4.size(), nodes = F.nodes;
+    const int fv = fp32_variant(ctx, 3, nrhs);
+    mfs_ctx::FarField::Plan *pu = nullptr;
+    CKS(ff_get_plan(ctx, F, fv, 1, &pu));
+    CKS(ff_upward(ctx, F, fv, pu, ctx->lam_d, nrhs, st));
+    const int REC = pair_record_floats(3, nrhs, 0);
+    CK(pack_sources(3, nrhs, 0, F.src_pos, F.rec_pt, ctx->lam_d, F.nsrc, F.nrec, F.rec, st));
+    CK(pack_sources(3, nrhs, 0, F.eq_pos, F.eq_pt, F.mu, nodes * FF_NE, nodes * FF_NE, F.rec + (size_t)F.nrec * REC,
+                    st));
+    std::vector<float4> tt(np);
+    std::vector<float> nn(traction ? 3 * (size_t)np : 0);
+    std::vector<int> tperm(np), lst_off(P + 1, 0), lst, segs;
+    std::vector<double> rad(P, 0.0);
+    for (int b = 0; b < P; ++b)
+        for (int j = et.toff[b]; j < et.toff[b + 1]; ++j) {
+            const double *x = &et.t64[3 * (size_t)j];
+            rad[b] = std::max(rad[b], std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]));
+        }
+    std::vector<int> root_of(P);
+    for (int sp = 0; sp < ctx->S; ++sp)
+        for (int b = ctx->body_off[sp]; b < ctx->body_off[sp + 1]; ++b) root_of[b] = F.tree.roots[sp];
+    int t = 0;
+    for (int q = 0; q < P; ++q) {
+        const int b = F.tree.order[q];
+        float w;
+        std::memcpy(&w, &q, sizeof(float));
+        for (int j = et.toff[b]; j < et.toff[b + 1]; ++j, ++t) {
+            tt[t] = make_float4(et.t4[j].x, et.t4[j].y, et.t4[j].z, w);
+            if (traction)
+                for (int a = 0; a < 3; ++a) nn[3 * (size_t)t + a] = et.nrm32[3 * (size_t)j + a];
+            tperm[t] = j;
+        }
+        segs.clear();
+        if (et.toff[b + 1] > et.toff[b])
+            ff_interaction_list(F.tree, root_of[b], std::vector<int>{b}, ctx->centres.data(), rad.data(),
+                                ctx->opt.farfield_separation, 0, segs);
+        lst.insert(lst.end(), segs.begin(), segs.end());
+        lst_off[q + 1] = (int)lst.size();
+    }
+    float4 *tt_d = nullptr;
+    float *nn_d = nullptr;
+    int *perm_d = nullptr, *off_d = nullptr, *lst_d = nullptr;
+    mfs_status rc = [&]() -> mfs_status {
+        CK(ctx->alloc(&tt_d, np));
+        CK(ctx->alloc(&perm_d, np));
+        CK(ctx->alloc(&off_d, P + 1));
+        CK(ctx->alloc(&lst_d, std::max<size_t>(lst.size(), 1)));
+        CK(cudaMemcpyAsync(tt_d, tt.data(), sizeof(float4) * np, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(perm_d, tperm.data(), sizeof(int) * np, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(off_d, lst_off.data(), sizeof(int) * (P + 1), cudaMemcpyHostToDevice, st));
+        if (!lst.empty()) CK(cudaMemcpyAsync(lst_d, lst.data(), sizeof(int) * lst.size(), cudaMemcpyHostToDevice, st));
+        if (traction) {
+            CK(ctx->alloc(&nn_d, nn.size()));
+            CK(cudaMemcpyAsync(nn_d, nn.data(), sizeof(float) * nn.size(), cudaMemcpyHostToDevice, st));
+        }
+        CK(stress_list_f32(nrhs, tt_d, nn_d, np, F.rec, REC, off_d, lst_d, F.seg_rec0, F.seg_rec1, F.centres, perm_d,
+                           ps_d, ts_d, st));
+        ctx->launches += 1;
+        return MFS_OK;
+    }();
+    cudaStreamSynchronize(st);  // the one-off lists are freed below
+    ctx->release(tt_d);
+    ctx->release(nn_d);
+    ctx->release(perm_d);
+    ctx->release(off_d);
+    ctx->release(lst_d);
+    return rc;
+}
+
 extern "C" {
 
 mfs_status mfs_evaluate(mfs_ctx *ctx, const double *points, const int32_t *owner, int32_t npoints, double *out,
@@ -3166,11 +3241,15 @@ mfs_status mfs_evaluate_stress(mfs_ctx *ctx, const double *points, const double 
                 CK(cudaMemcpyAsync(n32_d, et.nrm32.data(), sizeof(float) * et.nrm32.size(), cudaMemcpyHostToDevice,
                                    st));
             }
-            // scalar-format records: position then the strengths of every rhs
-            CK(pack_sources(3, nrhs, 0, ctx->src_pos_d, ctx->rec_pt_d, ctx->lam_d, ctx->sumN, ctx->nrec, ctx->rec_d,
-                            st));
-            CK(stress_f32(nrhs, t4_d, n32_d, np, ctx->rec_d, pair_record_floats(3, nrhs, 0), ctx->rec_off_d, sb0_d,
-                          sb1_d, ctx->centres_d, ps_d, ts_d, st));
+            if (ctx->ff.ready) {  // through the treecode
+                CKS(ff_stress_points(ctx, et, traction != nullptr, nrhs, ps_d, ts_d, st));
+            } else {
+                // scalar-format records: position then the strengths of every rhs
+                CK(pack_sources(3, nrhs, 0, ctx->src_pos_d, ctx->rec_pt_d, ctx->lam_d, ctx->sumN, ctx->nrec,
+                                ctx->rec_d, st));
+                CK(stress_f32(nrhs, t4_d, n32_d, np, ctx->rec_d, pair_record_floats(3, nrhs, 0), ctx->rec_off_d,
+                              sb0_d, sb1_d, ctx->centres_d, ps_d, ts_d, st));
+            }
         }
         if (pressure) {
             const size_t n = (size_t)nrhs * np;

@@ -262,3 +262,32 @@ def test_farfield_evaluate_points():
             assert _rel(b, a) < 1e-6, (name, own is None)
         tree.close()
         direct.close()
+
+
+def test_farfield_pressure_and_traction():
+    """mfs_evaluate_stress through the treecode (per-owner interaction lists of bodies and tree nodes,
+    the pressure and traction of the equivalent Stokeslets in the far field) against the direct sums,
+    after a mobility solve with two right-hand sides and after a resistance solve."""
+    rng = np.random.default_rng(33)
+    wl = make_workload("sphere100_mobility", count=40, m=300, n=150, seed=34)
+    tree, direct = _ctx(wl, farfield=1), _ctx(wl)
+    k = rng.integers(0, wl.num_bodies, 3000)
+    d = rng.standard_normal((3000, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    pts = wl.centres[k] + rng.uniform(1.0, 1.4, 3000)[:, None] * d
+    nrm = rng.standard_normal((3000, 3))
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    for solve in ("mobility", "resistance"):
+        FT = rng.standard_normal((2, 2, wl.num_bodies, 3))
+        for ctx in (tree, direct):
+            if solve == "mobility":
+                ctx.solve_mobility(torch.tensor(FT[0], device="cuda"), torch.tensor(FT[1], device="cuda"))
+            else:
+                ctx.solve_resistance(FT[0], FT[1])
+        for own in (k.astype(np.int32), None):
+            pa, ta = direct.evaluate_stress(pts, normals=nrm, owner=own, nrhs=2)
+            pb, tb = tree.evaluate_stress(pts, normals=nrm, owner=own, nrhs=2)
+            assert _rel(pb.numpy(), pa.numpy()) < 1e-6, (solve, "pressure")
+            assert _rel(tb.numpy(), ta.numpy()) < 1e-6, (solve, "traction")
+    tree.close()
+    direct.close()
