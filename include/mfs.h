@@ -118,7 +118,9 @@ typedef struct {
                              the first tree, its source side on the second); mfs_evaluate sums over the first
                              tree with interaction lists built for each call's points (each owner body's
                              radius that of its farthest point), and mfs_evaluate_stress likewise (the
-                             pressure and traction of the equivalent Stokeslets in the far field). */
+                             pressure and traction of the equivalent Stokeslets in the far field; these are
+                             derivatives of the field, matched to about 1e-5 relative at separation 3 where
+                             velocities are matched to about 1e-7; a larger separation tightens both). */
     double farfield_separation; /* farfield = 1: a target uses a node's equivalent points when it is at least
                                    this many equivalent radii from the node's centre; default 3, allowed
                                    [2.5, 10] (2.5 = the check sphere; smaller is faster and less accurate). */
