@@ -71,6 +71,7 @@ struct PairWork {
     int include_self;          // 1: self pairs included (right-hand side u_0)
     double *src_grad = nullptr;  // gradient kernel only: per source body sums, FP64 [P][3] (atomic adds)
     const int *tperm = nullptr;  // epilogue: target t's value goes to (and its base is read at) tperm[t]
+    int max_share = 1;           // epilogue: the most CTAs that share one tile
 };
 
 // ---------------------------------------------------------------------------

@@ -38,6 +38,7 @@ struct PairPlan {
     double *partial = nullptr;
     double *direct = nullptr;
     size_t partial_bytes = 0, direct_bytes = 0;
+    int max_share = 1;  // the most CTAs that share one tile (sizes the epilogue)
 };
 
 // The one-body apply factors of one formulation for one shape, FP32 / FP64 and as tensor-core pieces.
@@ -462,6 +463,7 @@ mfs_status build_plan_for(mfs_ctx *ctx, int variant, int include_self, const std
     long long G = (long long)occ * ctx->sm_count;
     if (G > units) G = std::max<long long>(units, 1);
     const long long W = units;
+    int max_share = 1;
     for (auto &tl : tiles) {
         if (tl.u1 == tl.u0) {
             tl.gA = tl.gB = -1;
@@ -470,12 +472,14 @@ mfs_status build_plan_for(mfs_ctx *ctx, int variant, int include_self, const std
         auto owner = [&](long long u) { return (int)(((u + 1) * G - 1) / W); };
         tl.gA = owner(tl.u0);
         tl.gB = owner(tl.u1 - 1);
+        max_share = std::max(max_share, tl.gB - tl.gA + 1);
     }
     plan.variant = variant;
     plan.include_self = include_self;
     plan.tile_targets = TT;
     plan.G = (int)G;
     plan.ntiles = (int)tiles.size();
+    plan.max_share = max_share;
     plan.total_units = units;
     CK(ctx->alloc(&plan.tiles, tiles.size()));
     CK(cudaMemcpy(plan.tiles, tiles.data(), sizeof(PairTile) * tiles.size(), cudaMemcpyHostToDevice));
@@ -521,6 +525,7 @@ PairWork work_of(const PairPlan &p) {
     w.direct = p.direct;
     w.tile_targets = p.tile_targets;
     w.include_self = p.include_self;
+    w.max_share = p.max_share;
     return w;
 }
 
@@ -678,6 +683,7 @@ mfs_status build_plan_lists(mfs_ctx *ctx, int variant, int include_self, const s
     long long G = (long long)occ * ctx->sm_count;
     if (G > units) G = std::max<long long>(units, 1);
     const long long W = std::max<long long>(units, 1);
+    int max_share = 1;
     for (auto &tl : tiles) {
         if (tl.u1 == tl.u0) {
             tl.gA = tl.gB = -1;
@@ -686,12 +692,14 @@ mfs_status build_plan_lists(mfs_ctx *ctx, int variant, int include_self, const s
         auto owner = [&](long long u) { return (int)(((u + 1) * G - 1) / W); };
         tl.gA = owner(tl.u0);
         tl.gB = owner(tl.u1 - 1);
+        max_share = std::max(max_share, tl.gB - tl.gA + 1);
     }
     plan.variant = variant;
     plan.include_self = include_self;
     plan.tile_targets = TT;
     plan.G = (int)G;
     plan.ntiles = (int)tiles.size();
+    plan.max_share = max_share;
     plan.total_units = units;
     CK(ctx->alloc(&plan.tiles, std::max<size_t>(tiles.size(), 1)));
     CK(cudaMemcpy(plan.tiles, tiles.data(), sizeof(PairTile) * tiles.size(), cudaMemcpyHostToDevice));

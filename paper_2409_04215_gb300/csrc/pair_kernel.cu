@@ -1076,12 +1076,16 @@ __global__ void __launch_bounds__(NT, MINB) pair_sum_kernel(PairGeom geo, PairWo
 }
 
 // Epilogue: out[r][t][d] = beta * base[r][t][d] + scale * (sum of the CTA shares of target t).
-// One block per tile; the CTAs that share the tile and the slot each wrote (0: the tile is where the
-// CTA's range starts, 1: where it ends) are found once per block, and the threads then run over the
-// tile's (target, component) entries, which are contiguous in every array for one right-hand side.
+// Blocks (tile, y): the CTAs that share the tile and the slot each wrote (0: the tile is where the
+// CTA's range starts, 1: where it ends) are found once per block; the tile's (target, component)
+// entries, contiguous in every array for one right-hand side, are spread over the gridDim.y blocks,
+// and S consecutive lanes share an entry: lane k adds shares k, k + S, ... in that order (eight loads
+// in flight), then the S partial sums meet in a fixed xor-shuffle tree.  The order is fixed, so the
+// result is deterministic; with S = 1 it is the plain sum in CTA order.  Tiles shared by many CTAs
+// (the far-field upward sums of the top nodes) are why S and the y blocks exist.
 template <int D, int NRHS>
 __global__ void __launch_bounds__(1024) pair_epilogue_kernel(PairWork work, const double *base, double beta, double scale, double *out,
-                                     int ntargets) {
+                                     int ntargets, int S) {
     constexpr int C = D * NRHS;
     constexpr int MAXS = 256;
     __shared__ signed char slot_of[MAXS];  // per CTA gA + i: slot 0 / 1, -1 for an empty range
@@ -1094,16 +1098,19 @@ __global__ void __launch_bounds__(1024) pair_epilogue_kernel(PairWork work, cons
         slot_of[i] = b0 >= b1 ? -1 : (b0 >= tl.u0 ? 0 : 1);
     }
     __syncthreads();
-    const int nt = tl.t1 - tl.t0;
-    for (int q = threadIdx.x; q < nt * C; q += blockDim.x) {
-        const int t = tl.t0 + q / C, c = q % C;
+    const int E = (tl.t1 - tl.t0) * C;
+    const int per_block = blockDim.x / S, sub = threadIdx.x % S;
+    const size_t per_slot = (size_t)work.tile_targets * C;
+    // the round count depends on the block only, so every lane of a warp reaches the shuffles
+    for (int q0 = blockIdx.y * per_block; q0 < E; q0 += gridDim.y * per_block) {
+        const int q = q0 + (int)threadIdx.x / S;
         double v = 0.0;
-        if (tl.gA >= 0) {
+        if (q < E && tl.gA >= 0) {
+            const int t = tl.t0 + q / C, c = q % C;
             if (tl.gA == tl.gB) {
-                v = work.direct[(size_t)t * C + c];
+                if (sub == 0) v = work.direct[(size_t)t * C + c];
             } else {
-                // shares of CTAs gA, gA + 1, ... added in that order; four loads issued before the adds
-                const size_t within = (size_t)(t - tl.t0) * C + c, per_slot = (size_t)work.tile_targets * C;
+                const size_t within = (size_t)(t - tl.t0) * C + c;
                 auto share = [&](int i) -> double {
                     int slot;
                     if (i < MAXS) {
@@ -1115,21 +1122,25 @@ __global__ void __launch_bounds__(1024) pair_epilogue_kernel(PairWork work, cons
                     }
                     return slot < 0 ? 0.0 : work.partial[(size_t)((tl.gA + i) * 2 + slot) * per_slot + within];
                 };
-                int i = 0;
-                for (; i + 4 <= ns; i += 4) {
-                    const double p0 = share(i), p1 = share(i + 1), p2 = share(i + 2), p3 = share(i + 3);
-                    v += p0;
-                    v += p1;
-                    v += p2;
-                    v += p3;
+                int i = sub;
+                for (; i + 7 * S < ns; i += 8 * S) {
+                    double p[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) p[u] = share(i + u * S);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) v += p[u];
                 }
-                for (; i < ns; ++i) v += share(i);
+                for (; i < ns; i += S) v += share(i);
             }
         }
-        const int h = c / D, d = c % D;
-        const size_t o = ((size_t)h * ntargets + (work.tperm ? work.tperm[t] : t)) * D + d;
-        const double b = base ? beta * base[o] : 0.0;
-        out[o] = b + scale * v;
+        for (int o = S / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (q < E && sub == 0) {
+            const int t = tl.t0 + q / C, c = q % C;
+            const int h = c / D, d = c % D;
+            const size_t o = ((size_t)h * ntargets + (work.tperm ? work.tperm[t] : t)) * D + d;
+            const double b = base ? beta * base[o] : 0.0;
+            out[o] = b + scale * v;
+        }
     }
 }
 
@@ -1391,11 +1402,17 @@ cudaError_t pair_launch(int vi, const PairGeom &geo, const PairWork &work, int *
 
 cudaError_t pair_epilogue(int D, int nrhs, const PairWork &work, const double *base, double beta, double scale,
                           double *out, int ntargets, cudaStream_t st) {
-    const int threads = 1024;  // one block per tile: a few hundred blocks at most, so wide blocks
+    const int threads = 1024;
     if (work.ntiles == 0) return cudaSuccess;
+    // lanes per entry from the most CTAs on one tile; blocks per tile so that a tile's entries times
+    // lanes fill about one 1024-thread block each (at most 16)
+    const int S = work.max_share >= 64 ? 8 : (work.max_share >= 16 ? 4 : 1);
+    const long long lanes = (long long)work.tile_targets * D * nrhs * S;
+    const int Y = (int)std::min<long long>(16, std::max<long long>(1, (lanes + threads - 1) / threads));
+    const dim3 grid((unsigned)work.ntiles, (unsigned)Y);
 #define E(D_, R_)                                                                                      \
     if (D == D_ && nrhs == R_) {                                                                       \
-        pair_epilogue_kernel<D_, R_><<<work.ntiles, threads, 0, st>>>(work, base, beta, scale, out, ntargets); \
+        pair_epilogue_kernel<D_, R_><<<grid, threads, 0, st>>>(work, base, beta, scale, out, ntargets, S); \
         return cudaGetLastError();                                                                     \
     }
     E(3, 1) E(3, 2) E(3, 3) E(3, 4) E(1, 1) E(1, 2) E(1, 3) E(1, 4)
@@ -1629,7 +1646,7 @@ extern "C" mfs_status mfs_stokeslet_sum_noalloc(const double *targets, int32_t n
     work.include_self = 1;
     if (launch_variant<Pol, NT>(geo, work, &meta->err, st) != cudaSuccess) return MFS_ERR_CUDA;
     pair_epilogue_kernel<3, 1><<<ntiles, 1024, 0, st>>>(work, nullptr, 0.0, 1.0 / (8.0 * MFS_PI * mu), u,
-                                                       num_targets);
+                                                       num_targets, 1);
     poison_on_timeout_kernel<<<sms, 256, 0, st>>>(&meta->err, u, 3 * (size_t)num_targets);
     return cudaGetLastError() == cudaSuccess ? MFS_OK : MFS_ERR_CUDA;
 }
