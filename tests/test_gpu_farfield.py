@@ -291,3 +291,29 @@ def test_farfield_pressure_and_traction():
             assert _rel(tb.numpy(), ta.numpy()) < 1e-6, (solve, "traction")
     tree.close()
     direct.close()
+
+
+@pytest.mark.parametrize("kind", ["stokes", "laplace"])
+def test_farfield_small_and_many_rhs(kind):
+    """Degenerate trees and every right-hand-side count: one body (no pairs at all off the body), two
+    bodies, and several suspensions of uneven size, 1-4 right-hand sides, both kernels, against the
+    direct GPU sums."""
+    name = "batched256_mobility"
+    for count, kw in ((1, dict(num_suspensions=1, p_lo=1, p_hi=1)), (2, dict(num_suspensions=1, p_lo=2, p_hi=2)),
+                      (None, dict(num_suspensions=5, p_lo=1, p_hi=30))):
+        wl = make_workload(name, m=120, n=60, seed=41, **kw)
+        if kind == "laplace":
+            wl.kind = "laplace"
+        direct, tree = _ctx(wl), _ctx(wl, farfield=1)
+        d = 3 if kind == "stokes" else 1
+        for nrhs in (1, 2, 3, 4):
+            s = torch.tensor(np.random.default_rng(nrhs).standard_normal((nrhs, direct.sum_N, d)), device="cuda")
+            for include_self in (False, True):
+                a = direct.pair_sum(s, include_self=include_self).cpu().numpy()
+                b = tree.pair_sum(s, include_self=include_self).cpu().numpy()
+                if not np.any(a):  # one body, self pairs left out: nothing to sum
+                    assert not np.any(b)
+                    continue
+                assert _rel(b.reshape(-1), a.reshape(-1)) < 1e-6, (count, nrhs, include_self)
+        direct.close()
+        tree.close()
