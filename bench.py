@@ -427,6 +427,15 @@ def secondary(args):
                                   "pairs_per_s": ref_rate,
                                   "rel_diff_fp32_vs_fp64": float(np.linalg.norm(got - refv) / np.linalg.norm(refv)),
                                   "speedup_fp32_path_pairs_per_s": line["value"] / ref_rate}
+        if name == "sphere200_adjoint":
+            # the adjoint against the all-FP64 GPU adjoint (FP64 transposed sums, transposed one-body
+            # apply and centre gradient) of the same solve: centre gradients of the loss sum |U|^2
+            dc32 = ctx.mobility_vjp(2.0 * out[0], torch.zeros_like(out[1]))[0].cpu().numpy()
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            dc64 = ref.mobility_vjp(2.0 * refs[0], torch.zeros_like(refs[1]))[0].cpu().numpy()
+            line["fp64_gpu_vjp"] = {"wall_s": time.perf_counter() - t2,
+                                    "rel_diff_fp32_vs_fp64": float(np.linalg.norm(dc32 - dc64) / np.linalg.norm(dc64))}
     print(json.dumps(line), flush=True)
 
 

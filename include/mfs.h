@@ -76,7 +76,8 @@ typedef struct {
     int32_t restart;   /* Krylov basis size before a restart; default 200 (no restart) */
     double eps_trunc;  /* singular values <= sigma_1 * eps_trunc are dropped (Eq. pseudo); default 0 */
     int32_t precision; /* 0: FP32 pair sums with compensated accumulation and FP32 one-body apply (default);
-                          1: FP64 pair sums and FP64 one-body apply (reference GPU path);
+                          1: FP64 pair sums and FP64 one-body apply (reference GPU path), the adjoint
+                             included (transposed sums, transposed apply and centre gradient in FP64);
                           2: FP32 pair sums, FP64 one-body apply;
                           3: compensated double-FP32 pair sums (every pair term carried as hi + lo
                              to about 2^-28 of its size, TwoSum accumulation) and FP64 one-body
@@ -182,8 +183,8 @@ mfs_status mfs_matvec(mfs_ctx *ctx, const double *gamma, double *y, int32_t nrhs
  * proxy points of body k' as targets (the Stokeslet is symmetric and even in r), and the transposed
  * one-body apply is R_M U W^T R_N^T (Eq. pseudo transposed).  Stokes contexts only (else
  * MFS_ERR_INVALID_ARG).  w, y: [nrhs][sum_M][3], host or device, 1 <= nrhs <= max_rhs.  FP32 pair
- * sums and an FP32-level one-body apply in every precision mode (on the tensor cores when
- * tensor_cores != 0 and precision = 0, else the CUDA-core split-K GEMM).  The first call builds the
+ * sums and an FP32-level one-body apply (on the tensor cores when tensor_cores != 0 and
+ * precision = 0, else the CUDA-core split-K GEMM); with precision = 1 both in FP64.  The first call builds the
  * transposed-apply data (a one-off setup cost, synchronising).
  */
 mfs_status mfs_matvec_transposed(mfs_ctx *ctx, const double *w, double *y, int32_t nrhs, void *stream);

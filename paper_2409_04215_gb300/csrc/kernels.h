@@ -29,6 +29,13 @@ cudaError_t pack_sources(int D, int nrhs, int packed, const float4 *src_pos, con
 cudaError_t pack_sources_comp(int D, int nrhs, const double *src_local64, const int *src_pt_of_rec,
                               const double *strength, int nsrc, int nrec, float *records, cudaStream_t st);
 
+// FP64 reference of the adjoint's pair gradient (precision = 1), per target: sum over the other
+// bodies' sources of grad_r (tw^T G(r) strength), raw (no 1/(8 pi mu)); tw [nrhs][ntargets][3], out
+// [ntargets][3]; the other arguments as pair_sum_fp64.
+cudaError_t grad_pair_fp64(int nrhs, const double *tgt_local, const int *tgt_body, int ntargets, const double *tw,
+                           const double *src_local4, int nsrc, const int *susp_src_begin, const int *susp_src_end,
+                           const int *body_src_off, const double *centres, const double *strength, double *out,
+                           cudaStream_t st);
 // FP64 reference pair sum (precision = 1): one thread per target, direct loops; raw sums (no 1/(4pi) factor).
 cudaError_t pair_sum_fp64(int D, int nrhs, const double *tgt_local, const int *tgt_body, int ntargets,
                           const double *src_local4, int nsrc, const int *susp_src_begin, const int *susp_src_end,
@@ -42,6 +49,7 @@ struct ShapeDev {
     float *Wp;            // [r][dN]  ((I - L0) V Sigma^+)^T (projected apply, matvec)
     float *Wr;            // [r][dN]  (V Sigma^+)^T (recovery apply)
     double *U64, *Wp64, *Wr64;  // FP64 copies (precision = 1)
+    double *UT64 = nullptr, *WpT64 = nullptr, *WrT64 = nullptr;  // their transposes (the FP64 adjoint)
     double sigma1, sigma_min;   // largest / smallest kept singular value
 };
 

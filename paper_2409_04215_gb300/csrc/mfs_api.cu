@@ -155,6 +155,10 @@ struct mfs_ctx {
     std::vector<long long> blkT_off;
     int nrecT = 0;
     float4 *tgtT_pos_d = nullptr;
+    // the FP64 transposed sums (precision = 1): proxy -> body, collocation points [sum_M][4] (body-local
+    // x, y, z and the body id), each body's suspension as a collocation range
+    int *src_body_d = nullptr, *colT_begin_d = nullptr, *colT_end_d = nullptr;
+    double *colloc4_d = nullptr;
     float *recT_d = nullptr;
     int *recT_off_d = nullptr, *rec_ptT_d = nullptr;
     long long *blkT_off_d = nullptr;
@@ -1058,6 +1062,13 @@ mfs_status ensure_gmres(mfs_ctx *ctx, int nrhs) {
 // ---------------------------------------------------------------------------
 // Adjoint (transposed) operators
 // ---------------------------------------------------------------------------
+// dst[c][r] = src[r][c], FP64 (setup of the FP64 adjoint's factor transposes).
+static __global__ void transpose64_kernel(const double *src, int rows, int cols, double *dst) {
+    const size_t n = (size_t)rows * cols;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[(i % cols) * rows + i / cols] = src[i];
+}
+
 // The transposed geometry: proxy points as targets (float4 with body bits), collocation points
 // as sources packed into records with their own padded offsets; plus adjoint scratch; with
 // farfield = 1 the treecode of the transposed sums (collocation sources, proxy targets).
@@ -1153,6 +1164,40 @@ mfs_status ensure_transposed(mfs_ctx *ctx) {
             fx.tcT_ready = true;
         }
     }
+    if (ctx->opt.precision == 1) {  // the FP64 transposed sums and one-body apply
+        std::vector<double> tl(3 * (size_t)ctx->sumM), c4(4 * (size_t)ctx->sumM);
+        CK(cudaMemcpy(tl.data(), ctx->tgt_local64_d, sizeof(double) * tl.size(), cudaMemcpyDeviceToHost));
+        for (int i = 0; i < ctx->sumM; ++i) {
+            for (int a = 0; a < 3; ++a) c4[4 * (size_t)i + a] = tl[3 * (size_t)i + a];
+            c4[4 * (size_t)i + 3] = (double)ctx->tgt_body[i];
+        }
+        std::vector<int> cb(P), ce(P);
+        for (int sp = 0; sp < ctx->S; ++sp)
+            for (int k = ctx->body_off[sp]; k < ctx->body_off[sp + 1]; ++k) {
+                cb[k] = ctx->tgt_off[ctx->body_off[sp]];
+                ce[k] = ctx->tgt_off[ctx->body_off[sp + 1]];
+            }
+        CK(ctx->alloc(&ctx->src_body_d, ctx->sumN));
+        CK(ctx->alloc(&ctx->colloc4_d, c4.size()));
+        CK(ctx->alloc(&ctx->colT_begin_d, P));
+        CK(ctx->alloc(&ctx->colT_end_d, P));
+        CK(cudaMemcpy(ctx->src_body_d, ctx->src_body.data(), sizeof(int) * ctx->sumN, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->colloc4_d, c4.data(), sizeof(double) * c4.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->colT_begin_d, cb.data(), sizeof(int) * P, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->colT_end_d, ce.data(), sizeof(int) * P, cudaMemcpyHostToDevice));
+        for (auto &sh : ctx->shapes) {
+            if (sh.bodies.empty()) continue;
+            ShapeDev &sd = sh.fs[0].dev;
+            CK(ctx->alloc(&sd.UT64, (size_t)sd.dM * sd.r));
+            CK(ctx->alloc(&sd.WpT64, (size_t)sd.r * sd.dN));
+            CK(ctx->alloc(&sd.WrT64, (size_t)sd.r * sd.dN));
+            transpose64_kernel<<<1024, 256>>>(sd.U64, sd.dM, sd.r, sd.UT64);
+            transpose64_kernel<<<1024, 256>>>(sd.Wp64, sd.r, sd.dN, sd.WpT64);
+            transpose64_kernel<<<1024, 256>>>(sd.Wr64, sd.r, sd.dN, sd.WrT64);
+            CK(cudaGetLastError());
+        }
+        CK(cudaDeviceSynchronize());
+    }
     if (ctx->opt.farfield) {
         auto &F = ctx->ffT;
         F.src_colloc = true;
@@ -1173,6 +1218,17 @@ mfs_status ensure_transposed(mfs_ctx *ctx) {
 // z^(k') = sum_k S^(kk')^T w^(k) at the proxy points (the Stokeslet is symmetric and even in r),
 // self pairs included or not.  w: [nrhs][sum_M][3], z: [nrhs][sum_N][3], both FP64 on the device.
 mfs_status pair_apply_T(mfs_ctx *ctx, const double *w, double *z, int nrhs, int include_self, cudaStream_t st) {
+    if (ctx->opt.precision == 1) {  // FP64 reference: the plain FP64 loops with the roles swapped
+        CK(pair_sum_fp64(3, nrhs, ctx->src_local64_d, ctx->src_body_d, ctx->sumN, ctx->colloc4_d, ctx->sumM,
+                         ctx->colT_begin_d, ctx->colT_end_d, ctx->tgt_off_d, ctx->centres_d, w, include_self,
+                         ctx->raw_d, st));
+        const size_t n = (size_t)nrhs * ctx->sumN * 3;
+        combine_raw_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ctx->raw_d, nullptr, 0.0, kernel_scale(ctx), z,
+                                                                        n);
+        CK(cudaGetLastError());
+        ctx->launches += 2;
+        return MFS_OK;
+    }
     const int variant = fp32_variant(ctx, 3, nrhs);
     if (ctx->ffT.ready)
         return ff_pair_apply(ctx, ctx->ffT, variant, w, z, nullptr, 0.0, kernel_scale(ctx), nrhs, include_self, st);
@@ -1212,6 +1268,17 @@ mfs_status precondT_dev(mfs_ctx *ctx, const double *z, double *out, int project,
         const int ncols = nb * nrhs;
         const FactorSet &fx = sh.fs[0];
         const ShapeDev &sd = fx.dev;
+        if (ctx->opt.precision == 1) {
+            // FP64 reference: out = R_M U (W (R_N^T z)) with the transposed FP64 factors
+            CK(gather_rotate(3, z, ctx->sumN * 3, sh.col_body, sh.col_rhs, ctx->src_off_d, ctx->rot64_d, ncols, sd.dN,
+                             sh.A, sh.A64, st));
+            CK(gemm_rm64(ncols, sd.r, sd.dN, sh.A64, project ? sd.WpT64 : sd.WrT64, sh.T64, st));
+            CK(gemm_rm64(ncols, sd.dM, sd.r, sh.T64, sd.UT64, sh.O64, st));
+            CK(scatter_rotate(3, nullptr, sh.O64, sh.col_body, sh.col_rhs, ctx->tgt_off_d, ctx->rot_d, ctx->rot64_d,
+                              ncols, sd.dM, ctx->sumM, out, st));
+            ctx->launches += 4;
+            continue;
+        }
         if (fx.tcT_ready && ctx->opt.precision == 0) {
             // tensor cores, as the forward apply: x = W^T (R_N^T z) with the K = dN column pieces in Tp,
             // x cut back into pieces (same layout, Tp reused), out = R_M U x kept in FP64
@@ -2763,6 +2830,24 @@ mfs_status mfs_mobility_vjp(mfs_ctx *ctx, const double *dU, const double *dOmega
         centre_grad_ff_kernel<<<P, 128, 0, st>>>(ctx->gradT_d, ctx->tgt_off_d, ctx->tmpM_d, ctx->src_off_d, dco.d);
         CK(cudaGetLastError());
         ctx->launches += 1;
+    } else if (ctx->opt.precision == 1) {
+        // FP64 reference, the same two sides as the treecode's: weights w at the collocation points
+        // against mu, weights mu at the proxy points against w (roles swapped, sign folded into dc)
+        CK(grad_pair_fp64(nrhs, ctx->tgt_local64_d, ctx->tgt_body_d, ctx->sumM, ctx->x_d, ctx->src_local4_d,
+                          ctx->sumN, ctx->susp_src_begin_d, ctx->susp_src_end_d, ctx->src_off_d, ctx->centres_d,
+                          ctx->lam_d, ctx->gradT_d, st));
+        CK(grad_pair_fp64(nrhs, ctx->src_local64_d, ctx->src_body_d, ctx->sumN, ctx->lam_d, ctx->colloc4_d,
+                          ctx->sumM, ctx->colT_begin_d, ctx->colT_end_d, ctx->tgt_off_d, ctx->centres_d, ctx->x_d,
+                          ctx->tmpM_d, st));
+        const double scale = kernel_scale(ctx);
+        const size_t nc = (size_t)ctx->sumM * 3, np3 = (size_t)ctx->sumN * 3;
+        combine_raw_kernel<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(ctx->gradT_d, nullptr, 0.0, scale,
+                                                                         ctx->gradT_d, nc);
+        combine_raw_kernel<<<(unsigned)((np3 + 255) / 256), 256, 0, st>>>(ctx->tmpM_d, nullptr, 0.0, scale,
+                                                                          ctx->tmpM_d, np3);
+        centre_grad_ff_kernel<<<P, 128, 0, st>>>(ctx->gradT_d, ctx->tgt_off_d, ctx->tmpM_d, ctx->src_off_d, dco.d);
+        CK(cudaGetLastError());
+        ctx->launches += 5;
     } else {
         to_f32_kernel<<<1024, 256, 0, st>>>(ctx->x_d, ctx->w32_d, nM);
         CK(pack_sources(3, nrhs, 0, ctx->src_pos_d, ctx->rec_pt_d, ctx->lam_d, ctx->sumN, ctx->nrec, ctx->rec_d, st));

@@ -716,6 +716,56 @@ __global__ void pair_sum_fp64_kernel(int D, int nrhs, const double *tgt_local, c
         for (int a = 0; a < D; ++a) out[((size_t)h * nt + t) * D + a] = acc[D * h + a];
 }
 
+// FP64 reference of the adjoint's pair gradient (precision = 1): one thread per target,
+//   out_t = sum_h sum_{s in t's suspension, not on t's body} grad_r (tw_h(t)^T G(r) sigma_h(s)),  r = x_t - y_s,
+// G = I / r + r r^T / r^3 (raw, without 1 / (8 pi mu)), so grad_r = [w (r.m) + m (w.r) - (w.m) r
+// - 3 (w.r)(r.m) r / r^2] / r^3 with w = tw_h(t), m = sigma_h(s).  Layouts as pair_sum_fp64; tw is
+// [nrhs][nt][3], out [nt][3].
+__global__ void grad_pair_fp64_kernel(int nrhs, const double *tgt_local, const int *tgt_body, int nt, const double *tw,
+                                      const double *src_local4, int nsrc, const int *susp_src_begin,
+                                      const int *susp_src_end, const int *body_src_off, const double *centres,
+                                      const double *strength, double *out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    const int kt = tgt_body[t];
+    const double x[3] = {centres[3 * kt] + tgt_local[3 * t], centres[3 * kt + 1] + tgt_local[3 * t + 1],
+                         centres[3 * kt + 2] + tgt_local[3 * t + 2]};
+    double acc[3] = {0.0, 0.0, 0.0};
+    const int self0 = body_src_off[kt], self1 = body_src_off[kt + 1];
+    for (int s = susp_src_begin[kt]; s < susp_src_end[kt]; ++s) {
+        if (s >= self0 && s < self1) continue;
+        const double *yl = src_local4 + 4 * (size_t)s;
+        const int kb = (int)yl[3];
+        const double r[3] = {x[0] - (centres[3 * kb] + yl[0]), x[1] - (centres[3 * kb + 1] + yl[1]),
+                             x[2] - (centres[3 * kb + 2] + yl[2])};
+        const double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        const double ri = 1.0 / sqrt(r2);
+        const double ri3 = ri * ri * ri;
+        for (int h = 0; h < nrhs; ++h) {
+            const double *w = tw + ((size_t)h * nt + t) * 3;
+            const double *m = strength + ((size_t)h * nsrc + s) * 3;
+            const double wm = w[0] * m[0] + w[1] * m[1] + w[2] * m[2];
+            const double wr = w[0] * r[0] + w[1] * r[1] + w[2] * r[2];
+            const double rm = r[0] * m[0] + r[1] * m[1] + r[2] * m[2];
+            const double q = -(wm + 3.0 * wr * rm / r2);
+            for (int a = 0; a < 3; ++a) acc[a] += (r[a] * q + w[a] * rm + m[a] * wr) * ri3;
+        }
+    }
+    for (int a = 0; a < 3; ++a) out[3 * (size_t)t + a] = acc[a];
+}
+
+cudaError_t grad_pair_fp64(int nrhs, const double *tgt_local, const int *tgt_body, int ntargets, const double *tw,
+                           const double *src_local4, int nsrc, const int *susp_src_begin, const int *susp_src_end,
+                           const int *body_src_off, const double *centres, const double *strength, double *out,
+                           cudaStream_t st) {
+    const int threads = 128;
+    if (ntargets == 0) return cudaSuccess;
+    grad_pair_fp64_kernel<<<(ntargets + threads - 1) / threads, threads, 0, st>>>(
+        nrhs, tgt_local, tgt_body, ntargets, tw, src_local4, nsrc, susp_src_begin, susp_src_end, body_src_off, centres,
+        strength, out);
+    return cudaGetLastError();
+}
+
 cudaError_t pair_sum_fp64(int D, int nrhs, const double *tgt_local, const int *tgt_body, int ntargets,
                           const double *src_local4, int nsrc, const int *susp_src_begin, const int *susp_src_end,
                           const int *body_src_off, const double *centres, const double *strength, int include_self,

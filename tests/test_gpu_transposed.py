@@ -61,3 +61,19 @@ def test_transposed_matvec_rejects_laplace():
     with pytest.raises(MFSError):
         ctx.matvec_transposed(np.zeros((1, ctx.sum_M, 1)))
     ctx.close()
+
+
+def test_transposed_matvec_fp64_path():
+    """precision = 1: the transposed pair sums in plain FP64 loops and the FP64 transposed one-body
+    apply hold A^T w to the oracle's FP64 transposed matvec at the FP64 path's matvec bar (1e-11)."""
+    wl = _mixed("stokes", nsusp=2)
+    ctx = _ctx(wl, precision=1, autotune=0)
+    pr = Problem(wl)
+    w = np.random.default_rng(24).standard_normal((2, ctx.sum_M, 3))
+    y = ctx.matvec_transposed(torch.tensor(w, device="cuda")).cpu().numpy()
+    for h in range(2):
+        ref = np.concatenate([pr.matvec_T(list(pr.suspension_bodies(s)),
+                                          w[h].reshape(-1)[_seg(pr, list(pr.suspension_bodies(s)), "colloc")])
+                              for s in range(wl.num_suspensions)])
+        assert _rel(y[h].reshape(-1), ref) < 1e-11
+    ctx.close()
