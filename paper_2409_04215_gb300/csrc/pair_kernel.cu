@@ -268,8 +268,8 @@ struct Scalar : PolicyBase {
     }
 };
 
-template <int NRHS, int TP, int NT>
-struct PackedStokes : PolicyBase {
+template <int NRHS, int TP, int NT, bool OA = false>
+struct PackedStokesT : PolicyBase {
     static constexpr int D = 3;
     static constexpr int C = 3 * NRHS;
     static constexpr int REC = rec_floats(3, NRHS, true);
@@ -347,11 +347,20 @@ struct PackedStokes : PolicyBase {
 #pragma unroll
                         for (int h = 0; h < NRHS; ++h) {
                             const u64 lx = rec[3 + 3 * h], ly = rec[4 + 3 * h], lz = rec[5 + 3 * h];
-                            const u64 dot = f2_fma(dx, lx, f2_fma(dy, ly, f2_mul(dz, lz)));
-                            const u64 sc = f2_mul(dot, ri2);
-                            blk[p][3 * h + 0] = f2_fma(f2_fma(dx, sc, lx), ri, blk[p][3 * h + 0]);
-                            blk[p][3 * h + 1] = f2_fma(f2_fma(dy, sc, ly), ri, blk[p][3 * h + 1]);
-                            blk[p][3 * h + 2] = f2_fma(f2_fma(dz, sc, lz), ri, blk[p][3 * h + 2]);
+                            u64 dot, sc;
+                            if constexpr (OA) {  // the operand shared by consecutive FMAs in slot A
+                                dot = f2_fma(lx, dx, f2_fma(ly, dy, f2_mul(lz, dz)));
+                                sc = f2_mul(ri2, dot);
+                                blk[p][3 * h + 0] = f2_fma(ri, f2_fma(sc, dx, lx), blk[p][3 * h + 0]);
+                                blk[p][3 * h + 1] = f2_fma(ri, f2_fma(sc, dy, ly), blk[p][3 * h + 1]);
+                                blk[p][3 * h + 2] = f2_fma(ri, f2_fma(sc, dz, lz), blk[p][3 * h + 2]);
+                            } else {
+                                dot = f2_fma(dx, lx, f2_fma(dy, ly, f2_mul(dz, lz)));
+                                sc = f2_mul(dot, ri2);
+                                blk[p][3 * h + 0] = f2_fma(f2_fma(dx, sc, lx), ri, blk[p][3 * h + 0]);
+                                blk[p][3 * h + 1] = f2_fma(f2_fma(dy, sc, ly), ri, blk[p][3 * h + 1]);
+                                blk[p][3 * h + 2] = f2_fma(f2_fma(dz, sc, lz), ri, blk[p][3 * h + 2]);
+                            }
                         }
                     }
                 }
@@ -387,6 +396,10 @@ struct PackedStokes : PolicyBase {
         return at(4 + c, j);
     }
 };
+template <int NRHS, int TP, int NT>
+using PackedStokes = PackedStokesT<NRHS, TP, NT, false>;
+template <int NRHS, int TP, int NT>
+using PackedStokesOA = PackedStokesT<NRHS, TP, NT, true>;
 
 // The same packed Stokeslet arithmetic with all per-target state in registers (more registers,
 // more freedom for the compiler to interleave sources; the autotuner picks per geometry).
@@ -1318,6 +1331,9 @@ static int occupancy_variant() {
     P(PackedStokes, 1, 5, 64)     \
     P(PackedStokes, 1, 5, 128)    \
     P(PackedStokes, 1, 6, 64)     \
+    P(PackedStokesOA, 1, 4, 64)   \
+    P(PackedStokesOA, 1, 6, 64)   \
+    P(PackedStokesOA, 1, 5, 64)   \
     P(PackedLaplaceReg, 1, 2, 128) \
     P(PackedLaplaceReg, 1, 4, 128) \
     P(PackedLaplaceReg, 1, 2, 256) \
