@@ -53,7 +53,9 @@ THROTTLE_BITS = {
 # the first of a timed solve (cold L2 after the flush), by variant, for the kernel source as captured;
 # a variant not listed reports null.
 PAIR_DRAM_BYTES = {"PackedStokes<1,3,128>": 4845312, "PackedStokes<1,4,128>": 4848640, "PackedStokes<1,4,64>": 4855296,
-                   "PackedStokes<1,5,64>": 4860416, "PackedStokes<1,6,64>": 4991744}
+                   "PackedStokes<1,5,64>": 4860416, "PackedStokes<1,6,64>": 4991744,
+                   "PackedStokesOA<1,4,64>": 4860416, "PackedStokesOA<1,5,64>": 4863488,
+                   "PackedStokesOA<1,6,64>": 4908544}
 
 
 def _args():
