@@ -291,3 +291,36 @@ def test_not_converged_is_reported():
     U, W, info = ctx.solve_mobility(wl.F[:1], wl.T[:1], allow_not_converged=True)
     assert info.status == 4 and not info.converged and info.iters == 2
     assert np.all(np.isfinite(U.numpy()))
+
+
+@pytest.mark.parametrize("kind", ["stokes", "laplace"])
+def test_update_centers_matches_fresh_context(kind):
+    """mfs_update_centers moves the bodies and keeps the one-body factors (Remark congruent): a context
+    moved to new centres (the bodies shuffled over the lattice and shifted) solves exactly as a context
+    set up there (same pair-kernel policy, bit for bit), twice in a row, and within the bar of the
+    oracle's solve at the new positions."""
+    import copy
+
+    wl = _mixed(kind, P=8, nsusp=1, seed=44)
+    ctx = _ctx(wl, autotune=0)
+    rng = np.random.default_rng(45)
+    for step in range(2):
+        moved = copy.copy(wl)
+        moved.centres = wl.centres[rng.permutation(wl.num_bodies)] + rng.standard_normal(3)
+        ctx.update_centers(moved.centres)
+        fresh = _ctx(moved, autotune=0)
+        if kind == "stokes":
+            F, T = torch.tensor(wl.F[:1], device="cuda"), torch.tensor(wl.T[:1], device="cuda")
+            a = torch.cat(ctx.solve_mobility(F, T)[:2], -1).cpu().numpy()
+            b = torch.cat(fresh.solve_mobility(F, T)[:2], -1).cpu().numpy()
+            Ur, Wr, _ = Problem(moved).solve_mobility(wl.F[0], wl.T[0], tol=1e-12)
+            ref = np.concatenate([Ur, Wr], axis=1)
+        else:
+            Q = torch.tensor(wl.Q[None], device="cuda")
+            a = ctx.solve_elastance(Q)[0].cpu().numpy()
+            b = fresh.solve_elastance(Q)[0].cpu().numpy()
+            ref = Problem(moved).solve_elastance(wl.Q, tol=1e-12)[0]
+        assert np.array_equal(a, b), step
+        assert _rel(a.reshape(ref.shape), ref) < 1e-5, step
+        fresh.close()
+    ctx.close()
