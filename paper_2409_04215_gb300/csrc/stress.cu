@@ -29,9 +29,20 @@ __device__ __forceinline__ void stress_segment(float xr, float yr, float zr, flo
         bp[h] = 0.f;
         bt[h][0] = bt[h][1] = bt[h][2] = 0.f;
     }
+    constexpr int RV = (3 + 3 * NRHS + 3) / 4;  // float4 loads per record (plain layout, padded to 4 floats)
     for (int j = j0; j < j1; ++j) {
-        const float *s = rec + (size_t)j * rec_floats;
-        const float rx = xr - __ldg(s), ry = yr - __ldg(s + 1), rz = zr - __ldg(s + 2);
+        // the record in 16-byte loads: rec_floats is a multiple of 4 and the buffer 256-byte aligned
+        const float4 *s4 = reinterpret_cast<const float4 *>(rec + (size_t)j * rec_floats);
+        float s[4 * RV];
+#pragma unroll
+        for (int v = 0; v < RV; ++v) {
+            const float4 f = __ldg(s4 + v);
+            s[4 * v] = f.x;
+            s[4 * v + 1] = f.y;
+            s[4 * v + 2] = f.z;
+            s[4 * v + 3] = f.w;
+        }
+        const float rx = xr - s[0], ry = yr - s[1], rz = zr - s[2];
         const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
         const float ir = rsqrtf(r2);
         const float ir3 = ir * ir * ir;
@@ -39,7 +50,7 @@ __device__ __forceinline__ void stress_segment(float xr, float yr, float zr, flo
         const float q5 = rn * ir3 * ir * ir;
 #pragma unroll
         for (int h = 0; h < NRHS; ++h) {
-            const float lx = __ldg(s + 3 + 3 * h), ly = __ldg(s + 4 + 3 * h), lz = __ldg(s + 5 + 3 * h);
+            const float lx = s[3 + 3 * h], ly = s[4 + 3 * h], lz = s[5 + 3 * h];
             const float rl = fmaf(rx, lx, fmaf(ry, ly, rz * lz));
             bp[h] = fmaf(rl, ir3, bp[h]);
             const float q = rl * q5;
