@@ -336,8 +336,10 @@ mfs_status mfs_evaluate_stress(mfs_ctx *ctx, const double *points, const double 
 const char *mfs_pair_variant(const mfs_ctx *ctx, int32_t nrhs);
 
 /* Entry `index` of the pair-kernel table: its name (as mfs_pair_variant reports it), dimension d (1 or
- * 3), right-hand sides and whether it is the adjoint's centre-gradient kernel (grad = 1, not a pair
- * sum).  NULL past the end of the table; the out-pointers may be NULL.  Static storage. */
+ * 3; 4 for the stress entries), right-hand sides and whether it is a kernel other than a pair sum
+ * (grad = 1: the adjoint's centre gradient; grad = 2: the pressure and traction of mfs_evaluate_stress,
+ * four outputs per right-hand side).  NULL past the end of the table; the out-pointers may be NULL.
+ * Static storage. */
 const char *mfs_pair_variant_info(int32_t index, int32_t *d, int32_t *nrhs, int32_t *grad);
 
 /*

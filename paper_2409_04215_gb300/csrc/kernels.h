@@ -13,7 +13,7 @@ namespace mfs {
 struct PairVariant {
     int D, nrhs, T, NT, tile_targets;
     int packed;  // 1: f32x2 Stokes policy with duplicated source records
-    int grad;    // 1: centre-gradient kernel of the adjoint (not a pair sum)
+    int grad;    // not a pair sum: 1 the adjoint's centre-gradient kernel, 2 pressure and traction (D = 4 outputs)
     int comp;    // 1: compensated double-FP32 arithmetic (precision = 3), records from pack_sources_comp
     const char *name;  // policy and template arguments, e.g. "PackedStokes<1,3,128>"
 };
@@ -140,18 +140,11 @@ cudaError_t dirichlet_rhs_stokes(const double *U, const double *Om, int nrhs, in
 cudaError_t dirichlet_rhs_laplace(const double *phi, int nrhs, int P, const int *body_tgt_off, int sum_M, double *b,
                                   cudaStream_t st);
 
-// ---- pressure and traction at evaluation points (stress.cu, Eq. traction) ----
-// FP32: points tgt (owner-relative float4 with owner bits), unit normals nrm [np][3] or null (no
-// traction), scalar-format source records, per-body record offsets, per-body suspension body range
-// [sb0, sb1); outputs p [nrhs][np], traction [nrhs][np][3] (either may be null).
-cudaError_t stress_f32(int nrhs, const float4 *tgt, const float *nrm, int np, const float *rec, int rec_floats,
-                       const int *rec_off, const int *sb0, const int *sb1, const double *centres, double *p_out,
-                       double *t_out, cudaStream_t st);
-// The same over per-owner interaction lists (far-field treecode): tree-ordered targets (w = owner's tree
-// position), segments with record ranges and centres, results at index perm[t].
-cudaError_t stress_list_f32(int nrhs, const float4 *tgt, const float *nrm, int np, const float *rec, int rec_floats,
-                            const int *lst_off, const int *lst_seg, const int *seg_rec0, const int *seg_rec1,
-                            const double *centres, const int *perm, double *p_out, double *t_out, cudaStream_t st);
+// ---- pressure and traction at evaluation points (stress.cu, Eq. traction), FP64 reference ----
+// Points tgt_local (owner-relative) with owners tbody, unit normals nrm [np][3] or null (no traction),
+// FP64 body-local sources and strengths, per-body suspension body range [sb0, sb1); outputs p
+// [nrhs][np], traction [nrhs][np][3] (either may be null).  The FP32 path is the pair kernel's stress
+// entry (StressStokes).
 cudaError_t stress_f64(int nrhs, const double *tgt_local, const int *tbody, const double *nrm, int np,
                        const double *src_local, const int *src_off, int sum_N, const double *lam, const int *sb0,
                        const int *sb1, const double *centres, double *p_out, double *t_out, cudaStream_t st);

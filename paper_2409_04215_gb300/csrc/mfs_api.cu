@@ -425,7 +425,7 @@ mfs_status build_plan_for(mfs_ctx *ctx, int variant, int include_self, const std
     const PairVariant *vv = pair_variants(&count);
     const PairVariant &v = vv[variant];
     const int TT = v.tile_targets;
-    const int C = v.grad ? 3 : v.D * v.nrhs;
+    const int C = v.grad == 1 ? 3 : v.D * v.nrhs;  // the gradient kernel: one 3-vector per target
     std::vector<PairTile> tiles;
     long long units = 0;
     for (int s = 0; s < ctx->S; ++s) {
@@ -632,7 +632,7 @@ mfs_status build_plan_lists(mfs_ctx *ctx, int variant, int include_self, const s
     const PairVariant *vv = pair_variants(&count);
     const PairVariant &v = vv[variant];
     const int TT = v.tile_targets;
-    const int C = v.D * v.nrhs;
+    const int C = v.grad == 1 ? 3 : v.D * v.nrhs;  // the gradient kernel: one 3-vector per target
     std::vector<PairTile> tiles;
     std::vector<int> lst;
     std::vector<long long> cum{0};
@@ -2816,7 +2816,7 @@ mfs_status mfs_mobility_vjp(mfs_ctx *ctx, const double *dU, const double *dOmega
     int vc = 0, gv = -1;
     const PairVariant *vv = pair_variants(&vc);
     for (int i = 0; i < vc; ++i)
-        if (vv[i].grad && vv[i].nrhs == nrhs) gv = i;
+        if (vv[i].grad == 1 && vv[i].nrhs == nrhs) gv = i;  // the centre-gradient entry (not the stress one)
     if (gv < 0) {
         ctx->last_error = "no gradient kernel for this nrhs";
         return MFS_ERR_INVALID_ARG;
@@ -2889,6 +2889,24 @@ mfs_status mfs_mobility_vjp(mfs_ctx *ctx, const double *dU, const double *dOmega
 static __global__ void add_kernel(double *a, const double *b, size_t n) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         a[i] += b[i];
+}
+
+// (p, T_x, T_y, T_z) per point and rhs -> pressure [n] and traction [n][3] (the -3 of Eq. traction).
+static __global__ void split_stress_kernel(const double *o4, size_t n, double *p, double *t) {
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        if (p) p[e] = o4[4 * e];
+        if (t)
+            for (int c = 0; c < 3; ++c) t[3 * e + c] = -3.0 * o4[4 * e + 1 + c];
+    }
+}
+
+// The stress entry of the pair-kernel table for nrhs (grad = 2), -1 if none.
+static int stress_variant(int nrhs) {
+    int count = 0;
+    const PairVariant *vv = pair_variants(&count);
+    for (int i = 0; i < count; ++i)
+        if (vv[i].grad == 2 && vv[i].nrhs == nrhs) return i;
+    return -1;
 }
 
 // out[h][order[i]][c] = in[h][i][c]: back from owner-sorted to the caller's point order.
@@ -3015,24 +3033,34 @@ mfs_status last_strengths(mfs_ctx *ctx, int nrhs, double *tmp, cudaStream_t st) 
 }
 }  // namespace
 
-// The representation at owner-grouped evaluation points through the treecode (farfield = 1): the
-// upward step on the strengths in lam_d, the points reordered into the tree's body order, one-off
-// interaction lists for them (each owner's radius is that of its farthest point), and the
-// evaluation launch; results land in sorted_d in the grouped order (out = scale * sums).
-static mfs_status ff_evaluate_points(mfs_ctx *ctx, int variant, const EvalTargets &et, int nrhs, double scale,
-                                     double *sorted_d, cudaStream_t st) {
+// Sums at owner-grouped evaluation points through the treecode (farfield = 1): the upward step on the
+// strengths in lam_d (a forward pair-sum entry), the proxy and equivalent records in the layout of
+// `variant` (a pair sum for mfs_evaluate, the stress entry for mfs_evaluate_stress), the points
+// reordered into the tree's body order, one-off interaction lists for them (each owner's radius that
+// of its farthest point), and the launch of `variant` with per-point weights `tw_grouped` (the normals
+// for the stress; may be null); results land in out_grouped [nrhs][np][dout] in the grouped order,
+// scaled by `scale`.
+static mfs_status ff_points(mfs_ctx *ctx, int variant, const EvalTargets &et, const float *tw_grouped, int nrhs,
+                            int dout, double scale, double *out_grouped, cudaStream_t st) {
     auto &F = ctx->ff;
     const int P = ctx->P, D = ctx->D, np = (int)et.t4.size(), nodes = F.nodes;
     int vc = 0;
     const PairVariant *vv = pair_variants(&vc);
+    const int fv = fp32_variant(ctx, D, nrhs);
     mfs_ctx::FarField::Plan *pu = nullptr;
-    CKS(ff_get_plan(ctx, F, variant, 1, &pu));
-    CKS(ff_upward(ctx, F, variant, pu, ctx->lam_d, nrhs, st));
-    const int REC = pair_record_floats(D, nrhs, vv[variant].packed);
-    CK(pack_sources(D, nrhs, vv[variant].packed, F.eq_pos, F.eq_pt, F.mu, nodes * FF_NE, nodes * FF_NE,
+    CKS(ff_get_plan(ctx, F, fv, 1, &pu));
+    CKS(ff_upward(ctx, F, fv, pu, ctx->lam_d, nrhs, st));
+    const int layout = vv[variant].packed, REC = pair_record_floats(D, nrhs, layout);
+    if (REC > F.rec_floats) {
+        ctx->last_error = "far field: record layout larger than its buffer";
+        return MFS_ERR_INVALID_ARG;
+    }
+    CK(pack_sources(D, nrhs, layout, F.src_pos, F.rec_pt, ctx->lam_d, F.nsrc, F.nrec, F.rec, st));
+    CK(pack_sources(D, nrhs, layout, F.eq_pos, F.eq_pt, F.mu, nodes * FF_NE, nodes * FF_NE,
                     F.rec + (size_t)F.nrec * REC, st));
     // tree order of the points; w = the owner's tree position; tperm: tree index -> grouped index
     std::vector<float4> tt(np);
+    std::vector<float> tw(tw_grouped ? 3 * (size_t)np : 0);
     std::vector<int> tperm(np), toff(P + 1, 0);
     std::vector<double> rad(P, 0.0);
     int t = 0;
@@ -3042,6 +3070,8 @@ static mfs_status ff_evaluate_points(mfs_ctx *ctx, int variant, const EvalTarget
         std::memcpy(&w, &q, sizeof(float));
         for (int j = et.toff[b]; j < et.toff[b + 1]; ++j, ++t) {
             tt[t] = make_float4(et.t4[j].x, et.t4[j].y, et.t4[j].z, w);
+            if (tw_grouped)
+                for (int a = 0; a < 3; ++a) tw[3 * (size_t)t + a] = tw_grouped[3 * (size_t)j + a];
             tperm[t] = j;
             const double *x = &et.t64[3 * (size_t)j];
             rad[b] = std::max(rad[b], std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]));
@@ -3062,6 +3092,7 @@ static mfs_status ff_evaluate_points(mfs_ctx *ctx, int variant, const EvalTarget
     int *lst_seg = nullptr, *perm_d = nullptr;
     long long *lst_cum = nullptr;
     float4 *tt_d = nullptr;
+    float *tw_d = nullptr;
     double pairs = 0.0;
     mfs_status rc = build_plan_lists(
         ctx, variant, 1, toff, 0, cuts, seg_blocks, seg_recs,
@@ -3078,99 +3109,30 @@ static mfs_status ff_evaluate_points(mfs_ctx *ctx, int variant, const EvalTarget
             CK(ctx->alloc(&perm_d, np));
             CK(cudaMemcpyAsync(tt_d, tt.data(), sizeof(float4) * np, cudaMemcpyHostToDevice, st));
             CK(cudaMemcpyAsync(perm_d, tperm.data(), sizeof(int) * np, cudaMemcpyHostToDevice, st));
+            if (tw_grouped) {
+                CK(ctx->alloc(&tw_d, tw.size()));
+                CK(cudaMemcpyAsync(tw_d, tw.data(), sizeof(float) * tw.size(), cudaMemcpyHostToDevice, st));
+            }
             PairGeom g = ff_geom(F);
             g.lst_seg = lst_seg;
             g.lst_cum = lst_cum;
             g.tgt = tt_d;
             g.ntargets = np;
+            g.tgt_w = tw_d;
             PairWork we = work_of(plan);
             we.tperm = perm_d;
             CKS(ff_launch(ctx, variant, g, we, st));
-            CK(pair_epilogue(D, nrhs, we, nullptr, 0.0, scale, sorted_d, np, st));
+            CK(pair_epilogue(dout, nrhs, we, nullptr, 0.0, scale, out_grouped, np, st));
             return MFS_OK;
         }();
     }
     cudaStreamSynchronize(st);  // the one-off lists and plan are freed below
     ctx->release(tt_d);
+    ctx->release(tw_d);
     ctx->release(perm_d);
     ctx->release(lst_seg);
     ctx->release(lst_cum);
     if (plan.tiles) release_plan(ctx, plan);
-    return rc;
-}
-
-// Pressure and traction (Eq. traction) at owner-grouped points through the treecode: the upward step
-// on the strengths in lam_d, the proxy and equivalent records in the plain layout, the points in the
-// tree's body order and each owner's interaction list; results in the grouped order (ps_d, ts_d).
-static mfs_status ff_stress_points(mfs_ctx *ctx, const EvalTargets &et, bool traction, int nrhs, double *ps_d,
-                                   double *ts_d, cudaStream_t st) {
-    auto &F = ctx->ff;
-    const int P = ctx->P, np = (int)et.t4.size(), nodes = F.nodes;
-    const int fv = fp32_variant(ctx, 3, nrhs);
-    mfs_ctx::FarField::Plan *pu = nullptr;
-    CKS(ff_get_plan(ctx, F, fv, 1, &pu));
-    CKS(ff_upward(ctx, F, fv, pu, ctx->lam_d, nrhs, st));
-    const int REC = pair_record_floats(3, nrhs, 0);
-    CK(pack_sources(3, nrhs, 0, F.src_pos, F.rec_pt, ctx->lam_d, F.nsrc, F.nrec, F.rec, st));
-    CK(pack_sources(3, nrhs, 0, F.eq_pos, F.eq_pt, F.mu, nodes * FF_NE, nodes * FF_NE, F.rec + (size_t)F.nrec * REC,
-                    st));
-    std::vector<float4> tt(np);
-    std::vector<float> nn(traction ? 3 * (size_t)np : 0);
-    std::vector<int> tperm(np), lst_off(P + 1, 0), lst, segs;
-    std::vector<double> rad(P, 0.0);
-    for (int b = 0; b < P; ++b)
-        for (int j = et.toff[b]; j < et.toff[b + 1]; ++j) {
-            const double *x = &et.t64[3 * (size_t)j];
-            rad[b] = std::max(rad[b], std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]));
-        }
-    std::vector<int> root_of(P);
-    for (int sp = 0; sp < ctx->S; ++sp)
-        for (int b = ctx->body_off[sp]; b < ctx->body_off[sp + 1]; ++b) root_of[b] = F.tree.roots[sp];
-    int t = 0;
-    for (int q = 0; q < P; ++q) {
-        const int b = F.tree.order[q];
-        float w;
-        std::memcpy(&w, &q, sizeof(float));
-        for (int j = et.toff[b]; j < et.toff[b + 1]; ++j, ++t) {
-            tt[t] = make_float4(et.t4[j].x, et.t4[j].y, et.t4[j].z, w);
-            if (traction)
-                for (int a = 0; a < 3; ++a) nn[3 * (size_t)t + a] = et.nrm32[3 * (size_t)j + a];
-            tperm[t] = j;
-        }
-        segs.clear();
-        if (et.toff[b + 1] > et.toff[b])
-            ff_interaction_list(F.tree, root_of[b], std::vector<int>{b}, ctx->centres.data(), rad.data(),
-                                ctx->opt.farfield_separation, 0, segs);
-        lst.insert(lst.end(), segs.begin(), segs.end());
-        lst_off[q + 1] = (int)lst.size();
-    }
-    float4 *tt_d = nullptr;
-    float *nn_d = nullptr;
-    int *perm_d = nullptr, *off_d = nullptr, *lst_d = nullptr;
-    mfs_status rc = [&]() -> mfs_status {
-        CK(ctx->alloc(&tt_d, np));
-        CK(ctx->alloc(&perm_d, np));
-        CK(ctx->alloc(&off_d, P + 1));
-        CK(ctx->alloc(&lst_d, std::max<size_t>(lst.size(), 1)));
-        CK(cudaMemcpyAsync(tt_d, tt.data(), sizeof(float4) * np, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(perm_d, tperm.data(), sizeof(int) * np, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(off_d, lst_off.data(), sizeof(int) * (P + 1), cudaMemcpyHostToDevice, st));
-        if (!lst.empty()) CK(cudaMemcpyAsync(lst_d, lst.data(), sizeof(int) * lst.size(), cudaMemcpyHostToDevice, st));
-        if (traction) {
-            CK(ctx->alloc(&nn_d, nn.size()));
-            CK(cudaMemcpyAsync(nn_d, nn.data(), sizeof(float) * nn.size(), cudaMemcpyHostToDevice, st));
-        }
-        CK(stress_list_f32(nrhs, tt_d, nn_d, np, F.rec, REC, off_d, lst_d, F.seg_rec0, F.seg_rec1, F.centres, perm_d,
-                           ps_d, ts_d, st));
-        ctx->launches += 1;
-        return MFS_OK;
-    }();
-    cudaStreamSynchronize(st);  // the one-off lists are freed below
-    ctx->release(tt_d);
-    ctx->release(nn_d);
-    ctx->release(perm_d);
-    ctx->release(off_d);
-    ctx->release(lst_d);
     return rc;
 }
 
@@ -3234,7 +3196,7 @@ mfs_status mfs_evaluate(mfs_ctx *ctx, const double *points, const int32_t *owner
                 return MFS_ERR_INVALID_ARG;
             }
             if (ctx->ff.ready) {  // through the treecode
-                CKS(ff_evaluate_points(ctx, variant, et, nrhs, scale, sorted_d, st));
+                CKS(ff_points(ctx, variant, et, nullptr, nrhs, D, scale, sorted_d, st));
             } else {
                 CKS(build_plan_for(ctx, variant, 1, toff, tbody, ctx->blk_off, np, plan));
                 int vc = 0;
@@ -3297,11 +3259,13 @@ mfs_status mfs_evaluate_stress(mfs_ctx *ctx, const double *points, const double 
     float4 *t4_d = nullptr;
     float *n32_d = nullptr;
     int *order_d = nullptr, *tbody_d = nullptr, *sb0_d = nullptr, *sb1_d = nullptr;
-    double *t64_d = nullptr, *n64_d = nullptr, *ps_d = nullptr, *ts_d = nullptr, *tmp_d = nullptr;
+    double *t64_d = nullptr, *n64_d = nullptr, *ps_d = nullptr, *ts_d = nullptr, *tmp_d = nullptr, *o4_d = nullptr;
+    PairPlan splan;
     auto cleanup = [&]() {
         cudaStreamSynchronize(st);
-        void *ps[] = {t4_d, n32_d, order_d, tbody_d, sb0_d, sb1_d, t64_d, n64_d, ps_d, ts_d, tmp_d};
+        void *ps[] = {t4_d, n32_d, order_d, tbody_d, sb0_d, sb1_d, t64_d, n64_d, ps_d, ts_d, tmp_d, o4_d};
         for (void *p : ps) ctx->release(p);
+        if (splan.tiles) release_plan(ctx, splan);
     };
     mfs_status rc = [&]() -> mfs_status {
         CK(ctx->alloc(&order_d, np));
@@ -3326,23 +3290,39 @@ mfs_status mfs_evaluate_stress(mfs_ctx *ctx, const double *points, const double 
             }
             CK(stress_f64(nrhs, t64_d, tbody_d, n64_d, np, ctx->src_local64_d, ctx->src_off_d, ctx->sumN, ctx->lam_d,
                           sb0_d, sb1_d, ctx->centres_d, ps_d, ts_d, st));
-        } else {
-            CK(ctx->alloc(&t4_d, np));
-            CK(cudaMemcpyAsync(t4_d, et.t4.data(), sizeof(float4) * np, cudaMemcpyHostToDevice, st));
-            if (traction) {
-                CK(ctx->alloc(&n32_d, 3 * (size_t)np));
-                CK(cudaMemcpyAsync(n32_d, et.nrm32.data(), sizeof(float) * et.nrm32.size(), cudaMemcpyHostToDevice,
-                                   st));
+        } else {  // the stress entry of the pair kernel (p, T per rhs), directly or through the treecode
+            const int sv = stress_variant(nrhs);
+            if (sv < 0) {
+                ctx->last_error = "no stress kernel for this nrhs";
+                return MFS_ERR_INVALID_ARG;
             }
-            if (ctx->ff.ready) {  // through the treecode
-                CKS(ff_stress_points(ctx, et, traction != nullptr, nrhs, ps_d, ts_d, st));
+            CK(ctx->alloc(&o4_d, (size_t)nrhs * np * 4));
+            const double scale = 1.0 / (4.0 * MFS_PI);
+            if (ctx->ff.ready) {
+                CKS(ff_points(ctx, sv, et, traction ? et.nrm32.data() : nullptr, nrhs, 4, scale, o4_d, st));
             } else {
-                // scalar-format records: position then the strengths of every rhs
+                CK(ctx->alloc(&t4_d, np));
+                CK(cudaMemcpyAsync(t4_d, et.t4.data(), sizeof(float4) * np, cudaMemcpyHostToDevice, st));
+                if (traction) {
+                    CK(ctx->alloc(&n32_d, 3 * (size_t)np));
+                    CK(cudaMemcpyAsync(n32_d, et.nrm32.data(), sizeof(float) * et.nrm32.size(),
+                                       cudaMemcpyHostToDevice, st));
+                }
+                CKS(build_plan_for(ctx, sv, 1, et.toff, et.tbody, ctx->blk_off, np, splan));
                 CK(pack_sources(3, nrhs, 0, ctx->src_pos_d, ctx->rec_pt_d, ctx->lam_d, ctx->sumN, ctx->nrec,
                                 ctx->rec_d, st));
-                CK(stress_f32(nrhs, t4_d, n32_d, np, ctx->rec_d, pair_record_floats(3, nrhs, 0), ctx->rec_off_d,
-                              sb0_d, sb1_d, ctx->centres_d, ps_d, ts_d, st));
+                PairGeom g = geom_of(ctx);
+                g.tgt = t4_d;
+                g.ntargets = np;
+                g.tgt_w = n32_d;
+                const PairWork w = work_of(splan);
+                if (w.total_units > 0) CK(pair_launch(sv, g, w, ctx->err_d, st));
+                CK(pair_epilogue(4, nrhs, w, nullptr, 0.0, scale, o4_d, np, st));
             }
+            const size_t n = (size_t)nrhs * np;
+            split_stress_kernel<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, st>>>(o4_d, n, ps_d,
+                                                                                                  ts_d);
+            CK(cudaGetLastError());
         }
         if (pressure) {
             const size_t n = (size_t)nrhs * np;

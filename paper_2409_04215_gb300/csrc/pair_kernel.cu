@@ -744,6 +744,110 @@ struct GradStokes : PolicyBase {
     }
 };
 
+// Pressure and surface traction of the Stokeslet representation at evaluation points (Eq. traction),
+// as a pair-kernel policy: for a target x with unit normal n (geo.tgt_w, FP32 [ntargets][3]; zero:
+// pressure only) and a source y of strength lambda, r = x - y,
+//   p   = (r . lambda) / r^3                  (x 1/(4 pi) in the epilogue)
+//   T   = r (r . n)(r . lambda) / r^5         (x -3/(4 pi) afterwards),
+// both independent of the viscosity; four outputs per right-hand side (p, T_x, T_y, T_z).  T targets
+// per thread, sources as the pair sums' plain records; all pairs of the suspension (self included).
+template <int NRHS, int T, int NT>
+struct StressStokes : PolicyBase {
+    static constexpr int D = 4;
+    static constexpr int C = 4 * NRHS;
+    static constexpr int REC = rec_floats(3, NRHS, false);
+    static constexpr int TPT = T;
+    static constexpr int PSM = 0;
+    float3 tp[T];
+    int tb[T];
+    float nv[T][3];
+    float hi[T][C], lo[T][C], bsum[T][C];
+
+    __device__ __forceinline__ void init(float *, int) {}
+    __device__ __forceinline__ void set_target(int j, float4 p) {
+        tp[j] = make_float3(p.x, p.y, p.z);
+        tb[j] = __float_as_int(p.w);
+    }
+    __device__ __forceinline__ void load_extra(int j, int idx, bool valid, const PairGeom &geo) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) nv[j][c] = (valid && geo.tgt_w) ? geo.tgt_w[(size_t)idx * 3 + c] : 0.f;
+    }
+    __device__ __forceinline__ void reset() {
+#pragma unroll
+        for (int j = 0; j < T; ++j)
+#pragma unroll
+            for (int c = 0; c < C; ++c) hi[j][c] = lo[j][c] = bsum[j][c] = 0.f;
+    }
+    __device__ __forceinline__ void compute(const float *sb, int nrec, const float (*dc)[3], const float (*)[3],
+                                            int kb0) {
+        float3 xt[T];
+#pragma unroll
+        for (int j = 0; j < T; ++j) {
+            const int r = tb[j] - kb0;
+            xt[j] = make_float3(dc[r][0] + tp[j].x, dc[r][1] + tp[j].y, dc[r][2] + tp[j].z);
+        }
+        for (int s0 = 0; s0 < nrec; s0 += MFS_BS) {
+            const int s1 = min(s0 + MFS_BS, nrec);
+            float blk[T][C];
+#pragma unroll
+            for (int j = 0; j < T; ++j)
+#pragma unroll
+                for (int c = 0; c < C; ++c) blk[j][c] = 0.f;
+            for (int s = s0; s < s1; ++s) {
+                float rec[REC];
+#pragma unroll
+                for (int v = 0; v < REC / 4; ++v) {
+                    const float4 f = reinterpret_cast<const float4 *>(sb + s * REC)[v];
+                    rec[4 * v + 0] = f.x;
+                    rec[4 * v + 1] = f.y;
+                    rec[4 * v + 2] = f.z;
+                    rec[4 * v + 3] = f.w;
+                }
+#pragma unroll
+                for (int j = 0; j < T; ++j) {
+                    const float rx = xt[j].x - rec[0], ry = xt[j].y - rec[1], rz = xt[j].z - rec[2];
+                    const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                    const float ir = rsqrt_ftz(r2);
+                    const float ir2 = ir * ir, ir3 = ir2 * ir;
+                    const float rn = fmaf(rx, nv[j][0], fmaf(ry, nv[j][1], rz * nv[j][2]));
+                    const float q5 = rn * ir3 * ir2;
+#pragma unroll
+                    for (int h = 0; h < NRHS; ++h) {
+                        const float rl = fmaf(rx, rec[3 + 3 * h], fmaf(ry, rec[4 + 3 * h], rz * rec[5 + 3 * h]));
+                        const float q = rl * q5;
+                        blk[j][4 * h] = fmaf(rl, ir3, blk[j][4 * h]);
+                        blk[j][4 * h + 1] = fmaf(rx, q, blk[j][4 * h + 1]);
+                        blk[j][4 * h + 2] = fmaf(ry, q, blk[j][4 * h + 2]);
+                        blk[j][4 * h + 3] = fmaf(rz, q, blk[j][4 * h + 3]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < T; ++j)
+#pragma unroll
+                for (int c = 0; c < C; ++c) bsum[j][c] += blk[j][c];
+        }
+    }
+    __device__ __forceinline__ void end_body(int body, bool include_self) {
+#pragma unroll
+        for (int j = 0; j < T; ++j) {
+            const bool keep = include_self || (tb[j] != body);
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                float s, e;
+                two_sum(hi[j][c], keep ? bsum[j][c] : 0.f, s, e);
+                hi[j][c] = s;
+                lo[j][c] += e;
+                bsum[j][c] = 0.f;
+            }
+        }
+    }
+    __device__ __forceinline__ float result(int j, int c, float &l) const {
+        l = lo[j][c];
+        return hi[j][c];
+    }
+};
+
 // ---------------------------------------------------------------------------
 // Compensated (double-FP32) pair sums: every pair term is carried as an unevaluated FP32 sum
 // hi + lo, accurate to about 2^-28 of its size instead of FP32's 2^-24, and summed per target with
@@ -1289,7 +1393,7 @@ static int occupancy_variant() {
 // Scalar S(D, nrhs, targets per thread, threads); packed Stokes P(nrhs, target pairs per thread, threads)
 // Scalar S(D, nrhs, T, NT); packed Stokes P(policy, nrhs, target pairs per thread, NT);
 // centre-gradient G(nrhs, T, NT) for the adjoint; compensated X(policy, nrhs, T, NT) (precision = 3)
-#define MFS_VARIANTS(S, P, G, X)  \
+#define MFS_VARIANTS(S, P, G, X, Q)  \
     S(3, 1, 4, 128)         \
     S(3, 1, 2, 128)         \
     S(3, 1, 4, 256)         \
@@ -1354,7 +1458,11 @@ static int occupancy_variant() {
     X(CompLaplace, 1, 2, 128)     \
     X(CompLaplace, 2, 2, 128)     \
     X(CompLaplace, 3, 2, 128)     \
-    X(CompLaplace, 4, 2, 128)
+    X(CompLaplace, 4, 2, 128)     \
+    Q(1, 4, 128)                  \
+    Q(2, 2, 128)                  \
+    Q(3, 2, 128)                  \
+    Q(4, 2, 128)
 
 static const PairVariant kVariants[] = {
 #define S(D_, R_, T_, N_) {D_, R_, T_, N_, N_ * T_, 0, 0, 0, "Scalar<" #D_ "," #R_ "," #T_ "," #N_ ">"},
@@ -1363,11 +1471,13 @@ static const PairVariant kVariants[] = {
 #define G(R_, T_, N_) {3, R_, T_, N_, N_ * T_, 0, 1, 0, "GradStokes<" #R_ "," #T_ "," #N_ ">"},
 #define X(POL_, R_, T_, N_) \
     {POL_<R_, T_, N_>::DIM, R_, T_, N_, N_ * T_, 0, 0, 1, #POL_ "<" #R_ "," #T_ "," #N_ ">"},
-    MFS_VARIANTS(S, P, G, X)
+#define Q(R_, T_, N_) {4, R_, T_, N_, N_ * T_, 0, 2, 0, "StressStokes<" #R_ "," #T_ "," #N_ ">"},
+    MFS_VARIANTS(S, P, G, X, Q)
 #undef S
 #undef P
 #undef G
 #undef X
+#undef Q
 };
 
 const PairVariant *pair_variants(int *count) {
@@ -1390,11 +1500,14 @@ int pair_occupancy(int vi) {
     if (vi == i++) return occupancy_variant<GradStokes<R_, T_, N_>, N_>();
 #define X(POL_, R_, T_, N_) \
     if (vi == i++) return occupancy_variant<POL_<R_, T_, N_>, N_>();
-    MFS_VARIANTS(S, P, G, X)
+#define Q(R_, T_, N_) \
+    if (vi == i++) return occupancy_variant<StressStokes<R_, T_, N_>, N_>();
+    MFS_VARIANTS(S, P, G, X, Q)
 #undef S
 #undef P
 #undef G
 #undef X
+#undef Q
     return 0;
 }
 
@@ -1408,11 +1521,14 @@ cudaError_t pair_launch(int vi, const PairGeom &geo, const PairWork &work, int *
     if (vi == i++) return launch_variant<GradStokes<R_, T_, N_>, N_>(geo, work, err, st);
 #define X(POL_, R_, T_, N_) \
     if (vi == i++) return launch_variant<POL_<R_, T_, N_>, N_>(geo, work, err, st);
-    MFS_VARIANTS(S, P, G, X)
+#define Q(R_, T_, N_) \
+    if (vi == i++) return launch_variant<StressStokes<R_, T_, N_>, N_>(geo, work, err, st);
+    MFS_VARIANTS(S, P, G, X, Q)
 #undef S
 #undef P
 #undef G
 #undef X
+#undef Q
     return cudaErrorInvalidValue;
 }
 
@@ -1432,6 +1548,7 @@ cudaError_t pair_epilogue(int D, int nrhs, const PairWork &work, const double *b
         return cudaGetLastError();                                                                     \
     }
     E(3, 1) E(3, 2) E(3, 3) E(3, 4) E(1, 1) E(1, 2) E(1, 3) E(1, 4)
+    E(4, 1) E(4, 2) E(4, 3) E(4, 4)  // pressure and traction
 #undef E
     return cudaErrorInvalidValue;
 }
