@@ -259,6 +259,21 @@ def resistance_two_way(args):
 
     res_resistance = residual(ctx, U_ref, W_ref)
     res_mobility = residual(mob, U, W)
+
+    # traction (Eq. traction) of the resistance solution on the same lattice (unit spheres: the normal
+    # is the lattice point), and its force balance: on an equal-area lattice the traction summed with
+    # weight 4 pi / 4800 per point is minus the body's resistance force
+    nrm = torch.tensor(np.tile(fine, (wl.num_bodies, 1)), device=dev)
+    ctx.evaluate_stress(pts, normals=nrm, owner=own)  # warm-up
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    torch.cuda.nvtx.range_push("bench_stress")  # profilers select the timed stress evaluation by this range
+    _, tr = ctx.evaluate_stress(pts, normals=nrm, owner=own, pressure=False)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    stress_ms = 1e3 * (time.perf_counter() - t1)
+    fsum = tr[0].reshape(wl.num_bodies, -1, 3).sum(1) * (4.0 * np.pi / fine.shape[0])
+    balance = float(torch.linalg.norm(fsum + F[0]) / torch.linalg.norm(F[0]))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = 2 * 128 * sms * 2070e6 / 1e12
     tflops = FLOPS_PER_PAIR * infos[-1].pairs / (pair_ms / 1e3) / 1e12 if pair_ms > 0 else None
@@ -285,6 +300,9 @@ def resistance_two_way(args):
         "surface_residual": {"points": int(pts.shape[0]), "lattice": "4800-point Fibonacci lattice per sphere",
                              "resistance": res_resistance, "mobility": res_mobility,
                              "definition": "|u(x) - g(x)| / |g(x)|, g the rigid motion (Eq. residual)"},
+        "traction": {"points": int(pts.shape[0]), "evaluate_ms": stress_ms, "kernel": "pair_sum_kernel<StressStokes>",
+                     "force_balance_rel": balance,
+                     "definition": "|sum of traction x 4 pi / 4800 per body + F| / |F| (Eq. traction, force_def)"},
         "gpu_launches": infos[-1].launches,
         "clocks": ck,
     }
